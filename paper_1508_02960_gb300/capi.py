@@ -1,0 +1,440 @@
+"""ctypes binding of the C ABI in ``include/lbm_gb300.h`` (argument marshalling only).
+
+Every computation runs in the CUDA library ``_build/liblbm_gb300.so``; this module
+declares the structures and prototypes, converts numpy arrays to pointers and turns
+non-zero status codes into :class:`LBMError`.  There is no fallback: if the library is
+missing or cannot be loaded, :func:`lib` raises.
+
+Device memory is owned by the library.  A CUDA stream handle (``int`` or a
+``torch.cuda.Stream``) may be passed at creation; work is queued on it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+Q = 19
+SRT, TRT, MRT = 0, 1, 2
+SBB, CLI = 0, 1
+F64, F32, F16DEV, BF16DEV = 0, 1, 2, 3
+LAYOUT_AB, LAYOUT_AA = 0, 1
+DEV_SCALE_AUTO = -1000
+
+STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_NO_MEMORY", -3: "LBM_ERR_CUDA",
+          -4: "LBM_ERR_DIVERGED", -5: "LBM_ERR_NOT_CONVERGED", -6: "LBM_ERR_TIMEOUT",
+          -7: "LBM_ERR_STATE", -8: "LBM_ERR_IO"}
+OK, ERR_ARG, ERR_NO_MEMORY, ERR_CUDA, ERR_DIVERGED, ERR_NOT_CONVERGED, ERR_TIMEOUT, \
+    ERR_STATE, ERR_IO = 0, -1, -2, -3, -4, -5, -6, -7, -8
+
+STORAGE_BYTES = {F64: 8, F32: 4, F16DEV: 2, BF16DEV: 2}
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Sphere(ctypes.Structure):
+    _fields_ = [("cx", ctypes.c_double), ("cy", ctypes.c_double), ("cz", ctypes.c_double),
+                ("r", ctypes.c_double)]
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("n_spheres", ctypes.c_int32),
+        ("spheres", ctypes.POINTER(Sphere)),
+        ("flags", ctypes.POINTER(ctypes.c_uint8)),
+        ("q", ctypes.POINTER(ctypes.c_double)),
+        ("tau", ctypes.c_double), ("delta_rho", ctypes.c_double), ("rho0", ctypes.c_double),
+        ("magic_lambda", ctypes.c_double), ("mrt_energy_ratio", ctypes.c_double),
+        ("mrt_rates", ctypes.POINTER(ctypes.c_double)),
+        ("collision", ctypes.c_int32), ("wall", ctypes.c_int32), ("storage", ctypes.c_int32),
+        ("layout", ctypes.c_int32), ("dev_scale_log2", ctypes.c_int32),
+        ("block_cells", ctypes.c_int32),
+        ("d_p", ctypes.c_double), ("perturb_u", ctypes.c_double), ("seed", ctypes.c_uint64),
+    ]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("U_sup", "U_int", "mass", "porosity", "K", "K_app", "Re_p", "Re_K", "beta",
+                 "C_F", "F_K", "u_max")] + [("steps", ctypes.c_int64), ("n_fluid", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class Info(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in
+                ("n_cells", "n_fluid", "n_boundary", "n_links", "n_links_cli",
+                 "bytes_populations", "bytes_geometry", "kernel_launches")] + \
+               [(n, ctypes.c_int32) for n in
+                ("block_cells", "storage", "layout", "collision", "wall", "dev_scale_log2")] + \
+               [("steps", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("check_interval", ctypes.c_int32),
+                ("max_resident", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "resident", "queued")] + \
+               [(n, ctypes.c_double) for n in ("fluid_updates", "busy_seconds", "mlups")] + \
+               [("kernel_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_st = ctypes.c_int
+
+PROTOTYPES = {
+    "lbm_last_error": (ctypes.c_char_p, []),
+    "lbm_version": (ctypes.c_char_p, []),
+    "lbm_create": (_st, [ctypes.POINTER(Desc), _vp, ctypes.POINTER(_vp)]),
+    "lbm_destroy": (None, [_vp]),
+    "lbm_init_equilibrium": (_st, [_vp]),
+    "lbm_step": (_st, [_vp, ctypes.c_int64]),
+    "lbm_run_to_convergence": (_st, [_vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int64,
+                                     ctypes.POINTER(ctypes.c_int64)]),
+    "lbm_observables": (_st, [_vp, ctypes.c_double, ctypes.POINTER(Obs)]),
+    "lbm_moment_sums": (_st, [_vp, _dp]),
+    "lbm_get_populations_f64": (_st, [_vp, _dp]),
+    "lbm_set_populations_f64": (_st, [_vp, _dp]),
+    "lbm_get_velocity_f64": (_st, [_vp, _dp]),
+    "lbm_get_flags": (_st, [_vp, ctypes.POINTER(ctypes.c_uint8)]),
+    "lbm_get_wall_distances": (_st, [_vp, _dp]),
+    "lbm_get_info": (_st, [_vp, ctypes.POINTER(Info)]),
+    "lbm_synchronize": (_st, [_vp]),
+    "lbm_save": (_st, [_vp, ctypes.c_char_p]),
+    "lbm_load": (_st, [_vp, ctypes.c_char_p]),
+    "lbm_delta_rho_for_re_p": (ctypes.c_double, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                 ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                                 ctypes.c_double]),
+    "lbm_batch_create": (_st, [ctypes.POINTER(Desc), ctypes.c_int32, _vp, ctypes.POINTER(_vp)]),
+    "lbm_batch_destroy": (None, [_vp]),
+    "lbm_batch_init_equilibrium": (_st, [_vp]),
+    "lbm_batch_step": (_st, [_vp, ctypes.c_int64]),
+    "lbm_batch_observables": (_st, [_vp, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(Obs)]),
+    "lbm_batch_get_populations_f64": (_st, [_vp, ctypes.c_int32, _dp]),
+    "lbm_batch_set_populations_f64": (_st, [_vp, ctypes.c_int32, _dp]),
+    "lbm_batch_get_info": (_st, [_vp, ctypes.POINTER(Info)]),
+    "lbm_server_create": (_st, [ctypes.POINTER(ServerOpts), ctypes.POINTER(_vp)]),
+    "lbm_server_submit": (_st, [_vp, ctypes.POINTER(Desc), ctypes.c_double, ctypes.c_int64,
+                                ctypes.POINTER(ctypes.c_int64)]),
+    "lbm_server_poll": (_st, [_vp, ctypes.c_int64, ctypes.POINTER(Obs), _dp]),
+    "lbm_server_drain": (_st, [_vp, ctypes.c_double]),
+    "lbm_server_get_stats": (_st, [_vp, ctypes.POINTER(ServerStats)]),
+    "lbm_server_destroy": (None, [_vp]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = False):
+    """Load the CUDA library (raises if it is missing and build_if_missing is False)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                if not build_if_missing:
+                    raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+                _build.build()
+            L = ctypes.CDLL(path)
+            for name, (res, args) in PROTOTYPES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().lbm_last_error().decode()
+
+
+def check(status: int, where: str) -> int:
+    if status != OK:
+        raise LBMError(status, where, last_error())
+    return status
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def make_desc(shape=None, *, nx=None, ny=None, nz=None, spheres=None, flags=None, q=None, tau=0.8,
+              delta_rho=0.0, rho0=1.0, magic_lambda=3.0 / 16.0, mrt_energy_ratio=4.6, mrt_rates=None,
+              collision=TRT, wall=SBB, storage=F64, layout=LAYOUT_AB, dev_scale_log2=DEV_SCALE_AUTO,
+              block_cells=0, d_p=0.0, perturb_u=0.0, seed=0):
+    """Build a Desc.  Returns (desc, keepalive): keep both alive until the call returns.
+
+    shape = (nz, ny, nx) or nx/ny/nz keywords; spheres (n, 4) array of (cx, cy, cz, r);
+    flags uint8 [nz, ny, nx]; q [19, nz, ny, nx] float64."""
+    if shape is not None:
+        nz, ny, nx = shape
+    keep = []
+    d = Desc(nx=nx, ny=ny, nz=nz, tau=tau, delta_rho=delta_rho, rho0=rho0, magic_lambda=magic_lambda,
+             mrt_energy_ratio=mrt_energy_ratio, collision=collision, wall=wall, storage=storage,
+             layout=layout, dev_scale_log2=dev_scale_log2, block_cells=block_cells, d_p=d_p,
+             perturb_u=perturb_u, seed=seed)
+    if spheres is not None and len(spheres):
+        sp = np.ascontiguousarray(np.asarray(spheres, dtype=np.float64).reshape(-1, 4))
+        keep.append(sp)
+        d.n_spheres = sp.shape[0]
+        d.spheres = sp.ctypes.data_as(ctypes.POINTER(Sphere))
+    if flags is not None:
+        fl = np.ascontiguousarray(flags, dtype=np.uint8)
+        assert fl.size == nx * ny * nz
+        keep.append(fl)
+        d.flags = fl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    if q is not None:
+        qq = np.ascontiguousarray(q, dtype=np.float64)
+        assert qq.size == Q * nx * ny * nz
+        keep.append(qq)
+        d.q = qq.ctypes.data_as(_dp)
+    if mrt_rates is not None:
+        mr = np.ascontiguousarray(mrt_rates, dtype=np.float64)
+        assert mr.size == Q
+        keep.append(mr)
+        d.mrt_rates = mr.ctypes.data_as(_dp)
+    return d, keep
+
+
+def _f64(a):
+    return a.ctypes.data_as(_dp)
+
+
+class Context:
+    """One periodic cell on the GPU (wraps lbm_ctx)."""
+
+    def __init__(self, desc: Desc | None = None, stream=None, **kw):
+        keep = None
+        if desc is None:
+            desc, keep = make_desc(**kw)
+        self._keep = keep
+        self.shape = (desc.nz, desc.ny, desc.nx)
+        self.storage = desc.storage
+        h = _vp()
+        check(lib().lbm_create(ctypes.byref(desc), _stream_handle(stream), ctypes.byref(h)), "lbm_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def n_cells(self):
+        nz, ny, nx = self.shape
+        return nx * ny * nz
+
+    def init_equilibrium(self):
+        check(lib().lbm_init_equilibrium(self._h), "lbm_init_equilibrium")
+
+    def step(self, n: int):
+        check(lib().lbm_step(self._h, int(n)), "lbm_step")
+
+    def run_to_convergence(self, tol: float, check_interval: int, max_steps: int):
+        done = ctypes.c_int64(0)
+        st = lib().lbm_run_to_convergence(self._h, float(tol), int(check_interval), int(max_steps),
+                                          ctypes.byref(done))
+        if st not in (OK, ERR_NOT_CONVERGED):
+            check(st, "lbm_run_to_convergence")
+        return st, int(done.value)
+
+    def observables(self, K_darcy: float = 0.0) -> dict:
+        o = Obs()
+        st = lib().lbm_observables(self._h, float(K_darcy), ctypes.byref(o))
+        if st not in (OK, ERR_DIVERGED):
+            check(st, "lbm_observables")
+        d = o.as_dict()
+        d["status"] = st
+        return d
+
+    def moment_sums(self) -> np.ndarray:
+        s = np.zeros(4)
+        check(lib().lbm_moment_sums(self._h, _f64(s)), "lbm_moment_sums")
+        return s
+
+    def get_populations(self, out=None) -> np.ndarray:
+        f = out if out is not None else np.empty((Q,) + self.shape)
+        assert f.dtype == np.float64 and f.flags.c_contiguous and f.size == Q * self.n_cells
+        check(lib().lbm_get_populations_f64(self._h, _f64(f)), "lbm_get_populations_f64")
+        return f
+
+    def set_populations(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.size == Q * self.n_cells
+        check(lib().lbm_set_populations_f64(self._h, _f64(f)), "lbm_set_populations_f64")
+
+    def get_velocity(self) -> np.ndarray:
+        u = np.empty((3,) + self.shape)
+        check(lib().lbm_get_velocity_f64(self._h, _f64(u)), "lbm_get_velocity_f64")
+        return u
+
+    def get_flags(self) -> np.ndarray:
+        fl = np.empty(self.shape, dtype=np.uint8)
+        check(lib().lbm_get_flags(self._h, fl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))), "lbm_get_flags")
+        return fl
+
+    def get_wall_distances(self) -> np.ndarray:
+        q = np.empty((Q,) + self.shape)
+        check(lib().lbm_get_wall_distances(self._h, _f64(q)), "lbm_get_wall_distances")
+        return q
+
+    def info(self) -> dict:
+        i = Info()
+        check(lib().lbm_get_info(self._h, ctypes.byref(i)), "lbm_get_info")
+        return i.as_dict()
+
+    def synchronize(self):
+        check(lib().lbm_synchronize(self._h), "lbm_synchronize")
+
+    def save(self, path: str):
+        check(lib().lbm_save(self._h, path.encode()), "lbm_save")
+
+    def load(self, path: str):
+        check(lib().lbm_load(self._h, path.encode()), "lbm_load")
+
+
+class Batch:
+    """Many independent periodic cells advanced by one launch per step (wraps lbm_batch)."""
+
+    def __init__(self, descs, stream=None):
+        arr = (Desc * len(descs))(*descs)
+        self.shapes = [(d.nz, d.ny, d.nx) for d in descs]
+        h = _vp()
+        check(lib().lbm_batch_create(arr, len(descs), _stream_handle(stream), ctypes.byref(h)),
+              "lbm_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_equilibrium(self):
+        check(lib().lbm_batch_init_equilibrium(self._h), "lbm_batch_init_equilibrium")
+
+    def step(self, n: int):
+        check(lib().lbm_batch_step(self._h, int(n)), "lbm_batch_step")
+
+    def observables(self, i: int, K_darcy: float = 0.0) -> dict:
+        o = Obs()
+        st = lib().lbm_batch_observables(self._h, int(i), float(K_darcy), ctypes.byref(o))
+        if st not in (OK, ERR_DIVERGED):
+            check(st, "lbm_batch_observables")
+        d = o.as_dict()
+        d["status"] = st
+        return d
+
+    def get_populations(self, i: int) -> np.ndarray:
+        f = np.empty((Q,) + self.shapes[i])
+        check(lib().lbm_batch_get_populations_f64(self._h, int(i), _f64(f)), "lbm_batch_get_populations_f64")
+        return f
+
+    def set_populations(self, i: int, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        check(lib().lbm_batch_set_populations_f64(self._h, int(i), _f64(f)), "lbm_batch_set_populations_f64")
+
+    def info(self) -> dict:
+        x = Info()
+        check(lib().lbm_batch_get_info(self._h, ctypes.byref(x)), "lbm_batch_get_info")
+        return x.as_dict()
+
+
+class Server:
+    """Memory-admitted continuous-batching request loop (wraps lbm_server)."""
+
+    def __init__(self, hbm_budget_bytes: int, check_interval: int = 200, max_resident: int = 256):
+        o = ServerOpts(hbm_budget_bytes=int(hbm_budget_bytes), check_interval=check_interval,
+                       max_resident=max_resident)
+        h = _vp()
+        check(lib().lbm_server_create(ctypes.byref(o), ctypes.byref(h)), "lbm_server_create")
+        self._h = h
+
+    def submit(self, desc: Desc, tol: float, max_steps: int) -> int:
+        rid = ctypes.c_int64(0)
+        check(lib().lbm_server_submit(self._h, ctypes.byref(desc), float(tol), int(max_steps),
+                                      ctypes.byref(rid)), "lbm_server_submit")
+        return int(rid.value)
+
+    def poll(self, rid: int):
+        """Returns None while running, else (status, obs dict, latency_s)."""
+        o = Obs()
+        lat = ctypes.c_double(0.0)
+        st = lib().lbm_server_poll(self._h, int(rid), ctypes.byref(o), ctypes.byref(lat))
+        if st == ERR_STATE:
+            return None
+        if st == ERR_ARG:
+            check(st, "lbm_server_poll")
+        return st, o.as_dict(), lat.value
+
+    def drain(self, timeout_s: float = 0.0):
+        check(lib().lbm_server_drain(self._h, float(timeout_s)), "lbm_server_drain")
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        check(lib().lbm_server_get_stats(self._h, ctypes.byref(s)), "lbm_server_get_stats")
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().lbm_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def delta_rho_for_re_p(re_p, tau, d_p, lx, K_D, C_F=0.0, rho0=1.0) -> float:
+    return float(lib().lbm_delta_rho_for_re_p(float(re_p), float(tau), float(d_p), int(lx), float(K_D),
+                                              float(C_F), float(rho0)))

@@ -1,0 +1,725 @@
+// batch.cu -- runtime of a set of independent periodic cells advanced together.
+//
+// One time step of every instance is one launch of the fused step kernel over a tile
+// list (tiles never span two instances, so each instance's reduction order is the
+// same alone or in a mix).  Repeated step sequences are captured once as CUDA graphs
+// (n steps + the final FP64 reduction) and replayed on the caller's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "batch.h"
+
+namespace lbm {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+const char *last_error_cstr() { return g_last_error.c_str(); }
+
+lbm_status fail(lbm_status st, const std::string &msg)
+{
+    set_error(msg);
+    return st;
+}
+
+lbm_status cuda_fail(cudaError_t e, const char *what)
+{
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? LBM_ERR_NO_MEMORY : LBM_ERR_CUDA;
+}
+
+const FormatOps &format_ops(int storage)
+{
+    switch (storage) {
+    case ST_F64: return ops_f64;
+    case ST_F32: return ops_f32;
+    case ST_F16: return ops_f16;
+    default: return ops_bf16;
+    }
+}
+
+#define CK(x)                                                 \
+    do {                                                      \
+        cudaError_t e_ = (x);                                 \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #x);      \
+    } while (0)
+
+// ------------------------------------------------------------------------------------
+// Descriptor validation and defaults
+// ------------------------------------------------------------------------------------
+lbm_status validate_desc(const lbm_desc &d)
+{
+    if (d.nx < 1 || d.ny < 1 || d.nz < 1) return fail(LBM_ERR_ARG, "nx, ny, nz must be >= 1");
+    const long long n = (long long)d.nx * d.ny * d.nz;
+    if (n > (1ll << 36)) return fail(LBM_ERR_ARG, "box too large");
+    if (!(d.tau > 0.5) || !std::isfinite(d.tau)) return fail(LBM_ERR_ARG, "tau must be a finite value > 1/2");
+    if (!std::isfinite(d.delta_rho)) return fail(LBM_ERR_ARG, "delta_rho must be finite");
+    if (d.rho0 < 0 || !std::isfinite(d.rho0)) return fail(LBM_ERR_ARG, "rho0 must be >= 0 (0 = 1)");
+    if (d.collision < LBM_SRT || d.collision > LBM_MRT) return fail(LBM_ERR_ARG, "unknown collision operator");
+    if (d.wall < LBM_SBB || d.wall > LBM_CLI) return fail(LBM_ERR_ARG, "unknown wall rule");
+    if (d.storage < LBM_F64 || d.storage > LBM_BF16DEV) return fail(LBM_ERR_ARG, "unknown storage format");
+    if (d.layout < LBM_LAYOUT_AB || d.layout > LBM_LAYOUT_AA) return fail(LBM_ERR_ARG, "unknown layout");
+    if (d.n_spheres < 0) return fail(LBM_ERR_ARG, "n_spheres < 0");
+    if (d.n_spheres > 0 && !d.spheres) return fail(LBM_ERR_ARG, "n_spheres > 0 but spheres is NULL");
+    for (int i = 0; i < d.n_spheres; ++i) {
+        const lbm_sphere &s = d.spheres[i];
+        if (!std::isfinite(s.cx) || !std::isfinite(s.cy) || !std::isfinite(s.cz) || !(s.r > 0) || !std::isfinite(s.r))
+            return fail(LBM_ERR_ARG, "sphere " + std::to_string(i) + " has a non-finite centre or radius <= 0");
+    }
+    if (d.magic_lambda < 0 || !std::isfinite(d.magic_lambda)) return fail(LBM_ERR_ARG, "magic_lambda must be >= 0");
+    if (d.mrt_energy_ratio < 0 || !std::isfinite(d.mrt_energy_ratio))
+        return fail(LBM_ERR_ARG, "mrt_energy_ratio must be >= 0");
+    if (d.block_cells != 0 && (d.block_cells < 64 || d.block_cells > 1024 || d.block_cells % 32))
+        return fail(LBM_ERR_ARG, "block_cells must be 0 or a multiple of 32 in [64, 1024]");
+    if (d.dev_scale_log2 != LBM_DEV_SCALE_AUTO && (d.dev_scale_log2 < -60 || d.dev_scale_log2 > 60))
+        return fail(LBM_ERR_ARG, "dev_scale_log2 out of [-60, 60]");
+    if (!std::isfinite(d.perturb_u) || std::fabs(d.perturb_u) > 0.3) return fail(LBM_ERR_ARG, "|perturb_u| > 0.3");
+    if (d.d_p < 0 || !std::isfinite(d.d_p)) return fail(LBM_ERR_ARG, "d_p must be >= 0");
+    return LBM_OK;
+}
+
+static int auto_dev_scale(const lbm_desc &d)
+{
+    if (d.storage != LBM_F16DEV) return 0;
+    if (d.dev_scale_log2 != LBM_DEV_SCALE_AUTO) return d.dev_scale_log2;
+    // the largest deviations are of the order of the density drop; map it near 2^12
+    const double dr = std::max(std::fabs(d.delta_rho), 1e-12);
+    int s = (int)std::floor(std::log2(4096.0 / dr));
+    return std::min(40, std::max(0, s));
+}
+
+size_t Batch::footprint(const lbm_desc &d)
+{
+    const size_t n = (size_t)d.nx * d.ny * d.nz;
+    const size_t es = storage_bytes(d.storage);
+    const size_t bufs = d.layout == LBM_LAYOUT_AA ? 1 : 2;
+    // populations + solid flags + segment table + partials + a boundary-table allowance
+    return bufs * Q * n * es + n + (n / 32 + 64) * (16 + 16) + n / 8 + (1u << 20);
+}
+
+lbm_status Batch::make_instance(const lbm_desc &d0, cudaStream_t s, std::unique_ptr<Instance> *out)
+{
+    lbm_status st = validate_desc(d0);
+    if (st != LBM_OK) return st;
+    std::unique_ptr<Instance> in(new Instance());
+    in->desc = d0;
+    lbm_desc &d = in->desc;
+    if (d.rho0 == 0) d.rho0 = 1.0;
+    if (d.magic_lambda == 0) d.magic_lambda = 3.0 / 16.0;
+    if (d.mrt_energy_ratio == 0) d.mrt_energy_ratio = 4.6;
+    if (d0.mrt_rates) in->mrt_rates.assign(d0.mrt_rates, d0.mrt_rates + Q);
+    in->dev_scale_log2 = auto_dev_scale(d0);
+    d.dev_scale_log2 = in->dev_scale_log2;
+    if (d.d_p > 0) {
+        in->d_p = d.d_p;
+    } else if (d0.n_spheres > 0) {
+        double m3 = 0;
+        for (int i = 0; i < d0.n_spheres; ++i) m3 += std::pow(d0.spheres[i].r, 3.0);
+        in->d_p = 2.0 * std::cbrt(m3 / d0.n_spheres);
+    }
+    std::vector<double> sph;
+    for (int i = 0; i < d0.n_spheres; ++i) {
+        sph.push_back(d0.spheres[i].cx);
+        sph.push_back(d0.spheres[i].cy);
+        sph.push_back(d0.spheres[i].cz);
+        sph.push_back(d0.spheres[i].r);
+    }
+    std::string err;
+    cudaError_t e = build_geometry(d.nx, d.ny, d.nz, sph.empty() ? nullptr : sph.data(), d0.n_spheres,
+                                   d0.n_spheres > 0 ? nullptr : d0.flags, d0.q, d.storage == LBM_F64, s, &in->geo,
+                                   &err);
+    d.spheres = nullptr;
+    d.flags = nullptr;
+    d.q = nullptr;
+    d.mrt_rates = nullptr;
+    if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? LBM_ERR_NO_MEMORY : LBM_ERR_CUDA, err);
+
+    const long long n = in->geo.ncells;
+    const size_t es = storage_bytes(d.storage);
+    const size_t pop = (size_t)Q * n * es;
+    auto cleanup = [&](cudaError_t ce, const char *what) {
+        cudaFree(in->f0);
+        cudaFree(in->f1);
+        cudaFree(in->linkB);
+        cudaFree(in->partials);
+        free_geometry(&in->geo);
+        return cuda_fail(ce, what);
+    };
+    if ((e = cudaMalloc(&in->f0, pop)) != cudaSuccess) return cleanup(e, "cudaMalloc(populations)");
+    if ((e = cudaMemsetAsync(in->f0, 0, pop, s)) != cudaSuccess) return cleanup(e, "cudaMemset");
+    if (d.layout == LBM_LAYOUT_AB) {
+        if ((e = cudaMalloc(&in->f1, pop)) != cudaSuccess) return cleanup(e, "cudaMalloc(populations)");
+        if ((e = cudaMemsetAsync(in->f1, 0, pop, s)) != cudaSuccess) return cleanup(e, "cudaMemset");
+    }
+    if (d.layout == LBM_LAYOUT_AA && d.wall == LBM_CLI && in->geo.n_links > 0) {
+        if ((e = cudaMalloc(&in->linkB, es * in->geo.n_links)) != cudaSuccess) return cleanup(e, "cudaMalloc(linkB)");
+        if ((e = cudaMemsetAsync(in->linkB, 0, es * in->geo.n_links, s)) != cudaSuccess)
+            return cleanup(e, "cudaMemset");
+    }
+    // partial sums: one slot of 4 doubles per tile at the smallest tile (2 segments)
+    in->partial_capacity = in->geo.nseg_padded / 2;
+    if ((e = cudaMalloc(&in->partials, sizeof(double) * 4 * in->partial_capacity)) != cudaSuccess)
+        return cleanup(e, "cudaMalloc(partials)");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cleanup(e, "cudaStreamSynchronize");
+    in->bytes_pop = pop * (d.layout == LBM_LAYOUT_AB ? 2 : 1);
+    *out = std::move(in);
+    return LBM_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// Batch
+// ------------------------------------------------------------------------------------
+Batch::~Batch()
+{
+    if (stream_ || cap_) cudaStreamSynchronize(stream_);
+    for (auto &kv : graphs_) cudaGraphExecDestroy(kv.second);
+    for (auto &p : inst_) {
+        cudaFree(p->f0);
+        cudaFree(p->f1);
+        cudaFree(p->linkB);
+        cudaFree(p->partials);
+        free_geometry(&p->geo);
+    }
+    cudaFree(d_table_);
+    cudaFree(d_tiles_);
+    cudaFree(d_tile_begin_);
+    cudaFree(d_tile_count_);
+    cudaFree(d_sums_);
+    cudaFree(d_status_);
+    cudaFree(d_stage_);
+    if (h_sums_) cudaFreeHost(h_sums_);
+    if (h_status_) cudaFreeHost(h_status_);
+    if (cap_) cudaStreamDestroy(cap_);
+}
+
+lbm_status Batch::init(cudaStream_t user_stream, int storage, int collision, int layout)
+{
+    stream_ = user_stream;
+    storage_ = storage;
+    collision_ = collision;
+    layout_ = layout;
+    CK(cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking));
+    return LBM_OK;
+}
+
+lbm_status Batch::add(std::unique_ptr<Instance> in)
+{
+    const lbm_desc &d = in->desc;
+    if (d.storage != storage_ || d.collision != collision_ || d.layout != layout_)
+        return fail(LBM_ERR_ARG, "instances of a batch must share storage, collision and layout");
+    if (layout_ == LBM_LAYOUT_AA && !inst_.empty()) return fail(LBM_ERR_ARG, "AA layout supports one instance");
+    in->phase = 0;
+    inst_.push_back(std::move(in));
+    dirty_ = true;
+    return LBM_OK;
+}
+
+lbm_status Batch::remove(int i)
+{
+    if (i < 0 || i >= size()) return fail(LBM_ERR_ARG, "instance index out of range");
+    CK(cudaStreamSynchronize(stream_));
+    Instance &p = *inst_[i];
+    cudaFree(p.f0);
+    cudaFree(p.f1);
+    cudaFree(p.linkB);
+    cudaFree(p.partials);
+    free_geometry(&p.geo);
+    inst_.erase(inst_.begin() + i);
+    dirty_ = true;
+    return LBM_OK;
+}
+
+lbm_status Batch::set_block(int block_cells)
+{
+    if (block_cells < 64 || block_cells > 1024 || block_cells % 32) return fail(LBM_ERR_ARG, "bad block size");
+    if (block_cells != block_) {
+        block_ = block_cells;
+        dirty_ = true;
+    }
+    return LBM_OK;
+}
+
+long long Batch::fluid_cells() const
+{
+    long long s = 0;
+    for (auto &p : inst_) s += p->geo.n_fluid;
+    return s;
+}
+
+static void fill_dev(const Instance &in, InstanceDev &D)
+{
+    const lbm_desc &d = in.desc;
+    std::memset(&D, 0, sizeof(D));
+    D.f0 = in.f0;
+    D.f1 = in.f1;
+    D.seg = in.geo.seg;
+    D.bmask = in.geo.bmask;
+    D.boff = in.geo.boff;
+    D.linkc = in.geo.linkc;
+    D.linkB = in.linkB;
+    D.partials = in.partials;
+    D.ncells = in.geo.ncells;
+    D.nx = d.nx;
+    D.ny = d.ny;
+    D.nz = d.nz;
+    D.wall = d.wall;
+    D.phase = in.phase;
+    D.scale = std::ldexp(1.0f, in.dev_scale_log2);
+    D.inv_scale = std::ldexp(1.0f, -in.dev_scale_log2);
+    const double tau = d.tau;
+    D.omega = 1.0 / tau;
+    D.omega_m = 1.0 / (0.5 + d.magic_lambda / (tau - 0.5));
+    if (!in.mrt_rates.empty()) {
+        for (int i = 0; i < Q; ++i) D.s[i] = in.mrt_rates[i];
+    } else {
+        // Sec. 2.1: s_nu = 1/tau on the viscous modes, s_zeta = 8(2-s_nu)/(8-s_nu) on the
+        // kinetic modes, energy modes by the ratio rule, conserved modes 0.
+        const double snu = 1.0 / tau;
+        const double sz = 8.0 * (2.0 - snu) / (8.0 - snu);
+        const double se = 1.0 / (0.5 + (tau - 0.5) / d.mrt_energy_ratio);
+        for (int i = 0; i < Q; ++i) D.s[i] = sz;
+        D.s[0] = D.s[3] = D.s[5] = D.s[7] = 0.0;
+        D.s[9] = D.s[11] = D.s[13] = D.s[14] = D.s[15] = snu;
+        D.s[1] = D.s[2] = se;
+    }
+    D.delta_rho = d.delta_rho;
+    D.rho0 = d.rho0;
+}
+
+lbm_status Batch::rebuild()
+{
+    CK(cudaStreamSynchronize(stream_));
+    for (auto &kv : graphs_) cudaGraphExecDestroy(kv.second);
+    graphs_.clear();
+    const int n = size();
+    const int W = block_ / 32;
+    std::vector<InstanceDev> table(std::max(n, 1));
+    std::vector<TileDev> tiles;
+    std::vector<int> tb(std::max(n, 1)), tc(std::max(n, 1));
+    for (int i = 0; i < n; ++i) {
+        Instance &in = *inst_[i];
+        fill_dev(in, table[i]);
+        const long long nt = in.geo.nseg_padded / W;
+        if (nt > in.partial_capacity) return fail(LBM_ERR_STATE, "partials too small");
+        tb[i] = (int)tiles.size();
+        tc[i] = (int)nt;
+        for (long long t = 0; t < nt; ++t) tiles.push_back(TileDev{i, (int)t, t * W});
+    }
+    if (tiles.size() > (size_t)INT32_MAX) return fail(LBM_ERR_ARG, "too many tiles");
+    ntiles_ = (int)tiles.size();
+    cudaFree(d_table_);
+    cudaFree(d_tiles_);
+    cudaFree(d_tile_begin_);
+    cudaFree(d_tile_count_);
+    d_table_ = nullptr;
+    d_tiles_ = nullptr;
+    d_tile_begin_ = d_tile_count_ = nullptr;
+    CK(cudaMalloc(&d_table_, sizeof(InstanceDev) * table.size()));
+    CK(cudaMemcpy(d_table_, table.data(), sizeof(InstanceDev) * table.size(), cudaMemcpyHostToDevice));
+    if (ntiles_ > 0) {
+        CK(cudaMalloc(&d_tiles_, sizeof(TileDev) * tiles.size()));
+        CK(cudaMemcpy(d_tiles_, tiles.data(), sizeof(TileDev) * tiles.size(), cudaMemcpyHostToDevice));
+    }
+    CK(cudaMalloc(&d_tile_begin_, sizeof(int) * tb.size()));
+    CK(cudaMalloc(&d_tile_count_, sizeof(int) * tc.size()));
+    CK(cudaMemcpy(d_tile_begin_, tb.data(), sizeof(int) * tb.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_tile_count_, tc.data(), sizeof(int) * tc.size(), cudaMemcpyHostToDevice));
+    if (n > capacity_) {
+        cudaFree(d_sums_);
+        cudaFree(d_status_);
+        if (h_sums_) cudaFreeHost(h_sums_);
+        if (h_status_) cudaFreeHost(h_status_);
+        d_sums_ = nullptr;
+        d_status_ = nullptr;
+        h_sums_ = nullptr;
+        h_status_ = nullptr;
+        capacity_ = std::max(n, 2 * capacity_);
+        CK(cudaMalloc(&d_sums_, sizeof(double) * 4 * capacity_));
+        CK(cudaMalloc(&d_status_, sizeof(unsigned) * capacity_));
+        CK(cudaMemset(d_status_, 0, sizeof(unsigned) * capacity_));
+        CK(cudaMallocHost(&h_sums_, sizeof(double) * 4 * capacity_));
+        CK(cudaMallocHost(&h_status_, sizeof(unsigned) * capacity_));
+    }
+    // one tile per block: the hardware block scheduler balances the tiles
+    grid_ = std::max(1, ntiles_);
+    dirty_ = false;
+    return LBM_OK;
+}
+
+lbm_status Batch::init_equilibrium(int i)
+{
+    if (dirty_) {
+        lbm_status st = rebuild();
+        if (st != LBM_OK) return st;
+    }
+    for (int j = 0; j < size(); ++j) {
+        if (i >= 0 && j != i) continue;
+        Instance &in = *inst_[j];
+        CK(ops().init(d_table_, j, in.geo.ncells, layout_, cur_of(in), in.desc.perturb_u,
+                      (unsigned long long)in.desc.seed, stream_));
+        ++launches_;
+        in.have_sums = false;
+        in.sums_pending = false;
+        in.steps = 0;
+    }
+    if (layout_ == LBM_LAYOUT_AA) aa_phase_ = 0;
+    return LBM_OK;
+}
+
+struct StepQueue {
+    const FormatOps *ops;
+    Launch L;
+    int collision, layout;
+    unsigned *status;
+    int n_status;
+    const int *tile_begin, *tile_count;
+    double *sums;
+    int n_inst;
+};
+
+// Queue n steps on stream s starting from (flip, aa); returns launches queued.
+static cudaError_t queue_steps(const StepQueue &q, cudaStream_t s, long long n, bool reduce_last, int &flip,
+                               int &aa, long long &launches)
+{
+    Launch L = q.L;
+    L.stream = s;
+    for (long long i = 0; i < n; ++i) {
+        const bool red = reduce_last && i == n - 1;
+        if (red) {
+            cudaError_t e = cudaMemsetAsync(q.status, 0, sizeof(unsigned) * q.n_status, s);
+            if (e != cudaSuccess) return e;
+        }
+        const int kind = q.layout == LBM_LAYOUT_AB ? KIND_AB : (aa == 0 ? KIND_AA_PULL : KIND_AA_LOCAL);
+        cudaError_t e = q.ops->step(q.collision, kind, L, flip, red ? 1 : 0, q.status);
+        if (e != cudaSuccess) return e;
+        ++launches;
+        if (q.layout == LBM_LAYOUT_AB) flip ^= 1;
+        else aa ^= 1;
+    }
+    if (reduce_last && n > 0) {
+        cudaError_t e = launch_final_reduce(q.L.table, q.tile_begin, q.tile_count, q.n_inst, q.sums, s);
+        if (e != cudaSuccess) return e;
+        ++launches;
+    }
+    return cudaSuccess;
+}
+
+lbm_status Batch::step(long long n)
+{
+    if (n < 0) return fail(LBM_ERR_ARG, "n_steps < 0");
+    if (n == 0 || size() == 0) return LBM_OK;
+    if (dirty_) {
+        lbm_status st = rebuild();
+        if (st != LBM_OK) return st;
+    }
+    StepQueue q{&ops(), Launch{d_table_, d_tiles_, ntiles_, grid_, block_, stream_}, collision_, layout_, d_status_,
+                size(), d_tile_begin_, d_tile_count_, d_sums_, size()};
+    const long long kChunk = 1000;
+    long long left = n;
+    while (left > 0) {
+        const long long m = left > 2 * kChunk ? kChunk : left;
+        const bool red = (m == left);
+        const auto key = std::make_tuple(m * 2 + (red ? 1 : 0), flip_, aa_phase_);
+        auto it = graphs_.find(key);
+        cudaGraphExec_t exec = nullptr;
+        if (it == graphs_.end()) {
+            int f = flip_, a = aa_phase_;
+            long long dummy = 0;
+            cudaGraph_t graph = nullptr;
+            CK(cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = queue_steps(q, cap_, m, red, f, a, dummy);
+            cudaError_t e2 = cudaStreamEndCapture(cap_, &graph);
+            if (e != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return cuda_fail(e, "capture of step kernels");
+            }
+            if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+            graphs_[key] = exec;
+        } else {
+            exec = it->second;
+        }
+        CK(cudaGraphLaunch(exec, stream_));
+        launches_ += m + (red ? 1 : 0);
+        if (layout_ == LBM_LAYOUT_AB) flip_ ^= (int)(m & 1);
+        else aa_phase_ ^= (int)(m & 1);
+        left -= m;
+    }
+    for (auto &p : inst_) {
+        p->steps += n;
+        p->have_sums = false;
+        p->sums_pending = true;
+    }
+    return LBM_OK;
+}
+
+lbm_status Batch::fetch_sums()
+{
+    const int n = size();
+    if (n == 0) return LBM_OK;
+    CK(cudaMemcpyAsync(h_sums_, d_sums_, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, stream_));
+    CK(cudaMemcpyAsync(h_status_, d_status_, sizeof(unsigned) * n, cudaMemcpyDeviceToHost, stream_));
+    CK(cudaStreamSynchronize(stream_));
+    for (int i = 0; i < n; ++i) {
+        Instance &in = *inst_[i];
+        for (int d = 0; d < 4; ++d) in.sums[d] = h_sums_[4 * i + d];
+        in.status = h_status_[i];
+        if (in.sums_pending) in.have_sums = true;
+        in.sums_pending = false;
+    }
+    return LBM_OK;
+}
+
+lbm_status Batch::moment_sums_now(int i, double *sums)
+{
+    if (i < 0 || i >= size()) return fail(LBM_ERR_ARG, "instance index out of range");
+    if (dirty_) {
+        lbm_status st = rebuild();
+        if (st != LBM_OK) return st;
+    }
+    Instance &in = *inst_[i];
+    std::vector<int> tb(size());
+    {
+        int acc = 0;
+        for (int j = 0; j < size(); ++j) {
+            tb[j] = acc;
+            acc += (int)(inst_[j]->geo.nseg_padded / (block_ / 32));
+        }
+    }
+    const int nt = (int)(in.geo.nseg_padded / (block_ / 32));
+    Launch L{d_table_, d_tiles_ + tb[i], nt, std::max(1, nt), block_, stream_};
+    CK(ops().moments(L, layout_, cur_of(in), aa_phase_, 1, 0, nullptr));
+    CK(launch_final_reduce(d_table_ + i, d_tile_begin_ + i, d_tile_count_ + i, 1, d_sums_ + 4 * i, stream_));
+    launches_ += 2;
+    CK(cudaMemcpyAsync(h_sums_ + 4 * i, d_sums_ + 4 * i, sizeof(double) * 4, cudaMemcpyDeviceToHost, stream_));
+    CK(cudaStreamSynchronize(stream_));
+    for (int d = 0; d < 4; ++d) sums[d] = h_sums_[4 * i + d];
+    return LBM_OK;
+}
+
+static cudaError_t ensure_stage(double **buf, long long *cap, long long n)
+{
+    if (*cap >= n) return cudaSuccess;
+    cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(buf, sizeof(double) * n);
+    if (e == cudaSuccess) *cap = n;
+    return e;
+}
+
+lbm_status Batch::get_f64(int i, double *host)
+{
+    if (i < 0 || i >= size() || !host) return fail(LBM_ERR_ARG, "bad instance index or NULL buffer");
+    if (dirty_) {
+        lbm_status st = rebuild();
+        if (st != LBM_OK) return st;
+    }
+    Instance &in = *inst_[i];
+    const long long n = in.geo.ncells;
+    CK(ensure_stage(&d_stage_, &stage_cells_, n));
+    for (int k = 0; k < Q; ++k) {
+        CK(ops().export_dir(d_table_, i, n, layout_, cur_of(in), aa_phase_, k, d_stage_, stream_));
+        ++launches_;
+        CK(cudaMemcpyAsync(host + (long long)k * n, d_stage_, sizeof(double) * n, cudaMemcpyDeviceToHost, stream_));
+    }
+    CK(cudaStreamSynchronize(stream_));
+    return LBM_OK;
+}
+
+lbm_status Batch::set_f64(int i, const double *host)
+{
+    if (i < 0 || i >= size() || !host) return fail(LBM_ERR_ARG, "bad instance index or NULL buffer");
+    if (dirty_) {
+        lbm_status st = rebuild();
+        if (st != LBM_OK) return st;
+    }
+    if (layout_ == LBM_LAYOUT_AA) aa_phase_ = 0;
+    Instance &in = *inst_[i];
+    const long long n = in.geo.ncells;
+    CK(ensure_stage(&d_stage_, &stage_cells_, n));
+    for (int k = 0; k < Q; ++k) {
+        CK(cudaMemcpyAsync(d_stage_, host + (long long)k * n, sizeof(double) * n, cudaMemcpyHostToDevice, stream_));
+        CK(ops().import_dir(d_table_, i, n, layout_, cur_of(in), k, d_stage_, stream_));
+        ++launches_;
+    }
+    in.have_sums = false;
+    in.sums_pending = false;
+    CK(cudaStreamSynchronize(stream_));
+    return LBM_OK;
+}
+
+lbm_status Batch::get_velocity(int i, double *host)
+{
+    if (i < 0 || i >= size() || !host) return fail(LBM_ERR_ARG, "bad instance index or NULL buffer");
+    if (dirty_) {
+        lbm_status st = rebuild();
+        if (st != LBM_OK) return st;
+    }
+    Instance &in = *inst_[i];
+    const long long n = in.geo.ncells;
+    CK(ensure_stage(&d_stage_, &stage_cells_, n));
+    std::vector<int> tb(size());
+    int acc = 0;
+    for (int j = 0; j < size(); ++j) {
+        tb[j] = acc;
+        acc += (int)(inst_[j]->geo.nseg_padded / (block_ / 32));
+    }
+    const int nt = (int)(in.geo.nseg_padded / (block_ / 32));
+    Launch L{d_table_, d_tiles_ + tb[i], nt, std::max(1, nt), block_, stream_};
+    for (int c = 0; c < 3; ++c) {
+        CK(ops().moments(L, layout_, cur_of(in), aa_phase_, 0, c, d_stage_));
+        ++launches_;
+        CK(cudaMemcpyAsync(host + (long long)c * n, d_stage_, sizeof(double) * n, cudaMemcpyDeviceToHost, stream_));
+    }
+    CK(cudaStreamSynchronize(stream_));
+    return LBM_OK;
+}
+
+lbm_status Batch::get_flags(int i, uint8_t *host)
+{
+    if (i < 0 || i >= size() || !host) return fail(LBM_ERR_ARG, "bad instance index or NULL buffer");
+    Instance &in = *inst_[i];
+    CK(cudaMemcpyAsync(host, in.geo.solid, in.geo.ncells, cudaMemcpyDeviceToHost, stream_));
+    CK(cudaStreamSynchronize(stream_));
+    return LBM_OK;
+}
+
+lbm_status Batch::get_q(int i, double *host)
+{
+    if (i < 0 || i >= size() || !host) return fail(LBM_ERR_ARG, "bad instance index or NULL buffer");
+    Instance &in = *inst_[i];
+    const long long n = in.geo.ncells;
+    CK(ensure_stage(&d_stage_, &stage_cells_, n));
+    for (int k = 0; k < Q; ++k) {
+        CK(export_wall_distances(in.geo, k, d_stage_, stream_));
+        launches_ += 2;
+        CK(cudaMemcpyAsync(host + (long long)k * n, d_stage_, sizeof(double) * n, cudaMemcpyDeviceToHost, stream_));
+    }
+    CK(cudaStreamSynchronize(stream_));
+    return LBM_OK;
+}
+
+lbm_status Batch::sync()
+{
+    CK(cudaStreamSynchronize(stream_));
+    return LBM_OK;
+}
+
+void Batch::fill_info(int i, lbm_info *out) const
+{
+    std::memset(out, 0, sizeof(*out));
+    for (int j = 0; j < size(); ++j) {
+        if (i >= 0 && j != i) continue;
+        const Instance &in = *inst_[j];
+        out->n_cells += in.geo.ncells;
+        out->n_fluid += in.geo.n_fluid;
+        out->n_boundary += in.geo.n_boundary;
+        out->n_links += in.geo.n_links;
+        out->n_links_cli += in.geo.n_links_cli;
+        out->bytes_populations += (int64_t)in.bytes_pop;
+        out->bytes_geometry += (int64_t)in.geo.bytes;
+        out->steps = in.steps;
+        out->dev_scale_log2 = in.dev_scale_log2;
+        out->wall = in.desc.wall;
+    }
+    out->kernel_launches = launches_;
+    out->block_cells = block_;
+    out->storage = storage_;
+    out->layout = layout_;
+    out->collision = collision_;
+}
+
+// ------------------------------------------------------------------------------------
+// Checkpoint: native-format state of one instance.
+// ------------------------------------------------------------------------------------
+struct CkptHeader {
+    char magic[8];
+    int32_t version, nx, ny, nz, storage, layout, collision, wall, aa_phase, dev_scale_log2;
+    int64_t steps, n_links, elem_bytes;
+};
+
+lbm_status Batch::save(int i, const char *path)
+{
+    if (i < 0 || i >= size() || !path) return fail(LBM_ERR_ARG, "bad instance index or NULL path");
+    Instance &in = *inst_[i];
+    CK(cudaStreamSynchronize(stream_));
+    const size_t es = storage_bytes(storage_);
+    const size_t pop = (size_t)Q * in.geo.ncells * es;
+    std::vector<char> buf(pop);
+    const void *src = (layout_ == LBM_LAYOUT_AB) ? (cur_of(in) ? in.f1 : in.f0) : in.f0;
+    CK(cudaMemcpy(buf.data(), src, pop, cudaMemcpyDeviceToHost));
+    std::vector<char> lb;
+    if (in.linkB) {
+        lb.resize(es * in.geo.n_links);
+        CK(cudaMemcpy(lb.data(), in.linkB, lb.size(), cudaMemcpyDeviceToHost));
+    }
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, "LBMGB300", 8);
+    h.version = 1;
+    h.nx = in.desc.nx;
+    h.ny = in.desc.ny;
+    h.nz = in.desc.nz;
+    h.storage = storage_;
+    h.layout = layout_;
+    h.collision = collision_;
+    h.wall = in.desc.wall;
+    h.aa_phase = aa_phase_;
+    h.dev_scale_log2 = in.dev_scale_log2;
+    h.steps = in.steps;
+    h.n_links = in.linkB ? in.geo.n_links : 0;
+    h.elem_bytes = (int64_t)es;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(LBM_ERR_IO, std::string("cannot open ") + path);
+    bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 && std::fwrite(buf.data(), 1, buf.size(), f) == buf.size() &&
+              (lb.empty() || std::fwrite(lb.data(), 1, lb.size(), f) == lb.size());
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(LBM_ERR_IO, std::string("write failed: ") + path);
+    return LBM_OK;
+}
+
+lbm_status Batch::load(int i, const char *path)
+{
+    if (i < 0 || i >= size() || !path) return fail(LBM_ERR_ARG, "bad instance index or NULL path");
+    if (dirty_) {
+        lbm_status st = rebuild();
+        if (st != LBM_OK) return st;
+    }
+    Instance &in = *inst_[i];
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(LBM_ERR_IO, std::string("cannot open ") + path);
+    CkptHeader h;
+    if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 1) {
+        std::fclose(f);
+        return fail(LBM_ERR_IO, "not a checkpoint of this library");
+    }
+    const size_t es = storage_bytes(storage_);
+    if (h.nx != in.desc.nx || h.ny != in.desc.ny || h.nz != in.desc.nz || h.storage != storage_ ||
+        h.layout != layout_ || h.collision != collision_ || h.wall != in.desc.wall || h.elem_bytes != (int64_t)es ||
+        h.dev_scale_log2 != in.dev_scale_log2 || h.n_links != (in.linkB ? in.geo.n_links : 0)) {
+        std::fclose(f);
+        return fail(LBM_ERR_ARG, "checkpoint does not match this context's descriptor");
+    }
+    const size_t pop = (size_t)Q * in.geo.ncells * es;
+    std::vector<char> buf(pop), lb(h.n_links * es);
+    bool ok = std::fread(buf.data(), 1, pop, f) == pop && (lb.empty() || std::fread(lb.data(), 1, lb.size(), f) == lb.size());
+    std::fclose(f);
+    if (!ok) return fail(LBM_ERR_IO, "checkpoint truncated");
+    CK(cudaStreamSynchronize(stream_));
+    if (layout_ == LBM_LAYOUT_AA) aa_phase_ = h.aa_phase;
+    void *dst = (layout_ == LBM_LAYOUT_AB) ? (cur_of(in) ? in.f1 : in.f0) : in.f0;
+    CK(cudaMemcpy(dst, buf.data(), pop, cudaMemcpyHostToDevice));
+    if (!lb.empty()) CK(cudaMemcpy(in.linkB, lb.data(), lb.size(), cudaMemcpyHostToDevice));
+    in.steps = h.steps;
+    in.have_sums = false;
+    in.sums_pending = false;
+    return LBM_OK;
+}
+
+}  // namespace lbm

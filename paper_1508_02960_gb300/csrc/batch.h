@@ -1,0 +1,106 @@
+// batch.h -- host runtime object behind contexts, batches and the server: a set of
+// independent periodic cells that share storage format, collision operator and layout
+// and advance together, one persistent kernel launch per time step.
+#pragma once
+
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+struct Instance {
+    lbm_desc desc{};               // copy; pointer members cleared
+    std::vector<double> mrt_rates; // explicit MRT rates when given
+    GeometryDev geo;
+    void *f0 = nullptr, *f1 = nullptr;
+    void *linkB = nullptr;
+    double *partials = nullptr;
+    long long partial_capacity = 0;  // tiles
+    int phase = 0;                   // A-B buffer holding the state when the batch flip is 0
+    int dev_scale_log2 = 0;
+    double d_p = 0.0;
+    long long steps = 0;
+    // results of the last reduction
+    double sums[4] = {0, 0, 0, 0};
+    unsigned status = 0;
+    bool have_sums = false;
+    bool sums_pending = false;       // the last queued step reduced the moments
+    size_t bytes_pop = 0;
+};
+
+class Batch {
+public:
+    ~Batch();
+    // Validates and builds one instance (geometry + memory).  Does not initialise state.
+    static lbm_status make_instance(const lbm_desc &d, cudaStream_t s, std::unique_ptr<Instance> *out);
+    // Footprint estimate (bytes) of an instance before building it.
+    static size_t footprint(const lbm_desc &d);
+
+    lbm_status init(cudaStream_t user_stream, int storage, int collision, int layout);
+    lbm_status add(std::unique_ptr<Instance> inst);    // A-B batches only when stepping has begun
+    lbm_status remove(int i);                          // releases device memory of instance i
+    int size() const { return (int)inst_.size(); }
+    Instance &at(int i) { return *inst_[i]; }
+
+    lbm_status init_equilibrium(int i);                // i < 0: all
+    lbm_status step(long long n);                      // queue n steps (+ final reduction)
+    lbm_status moment_sums_now(int i, double *sums);   // reduce the stored state (synchronises)
+    lbm_status fetch_sums();                           // copy last reduction to host (synchronises)
+    lbm_status get_f64(int i, double *host);
+    lbm_status set_f64(int i, const double *host);
+    lbm_status get_velocity(int i, double *host);
+    lbm_status get_flags(int i, uint8_t *host);
+    lbm_status get_q(int i, double *host);
+    lbm_status save(int i, const char *path);
+    lbm_status load(int i, const char *path);
+    lbm_status sync();
+    void fill_info(int i, lbm_info *out) const;
+    long long launches() const { return launches_; }
+    int block_cells() const { return block_; }
+    int aa_phase() const { return aa_phase_; }
+    cudaStream_t stream() const { return stream_; }
+    long long fluid_cells() const;
+    lbm_status set_block(int block_cells);
+
+private:
+    lbm_status rebuild();          // upload table and tiles, drop graphs
+    int cur_of(const Instance &in) const { return in.phase ^ flip_; }
+    const FormatOps &ops() const { return format_ops(storage_); }
+
+    std::vector<std::unique_ptr<Instance>> inst_;
+    int storage_ = 0, collision_ = 0, layout_ = 0;
+    cudaStream_t stream_ = nullptr;   // user stream (launches)
+    cudaStream_t cap_ = nullptr;      // private stream for graph capture
+    InstanceDev *d_table_ = nullptr;
+    TileDev *d_tiles_ = nullptr;
+    int *d_tile_begin_ = nullptr, *d_tile_count_ = nullptr;
+    double *d_sums_ = nullptr;        // [n][4]
+    unsigned *d_status_ = nullptr;    // [n]
+    double *h_sums_ = nullptr;        // pinned [n][4]
+    unsigned *h_status_ = nullptr;    // pinned [n]
+    int capacity_ = 0;
+    int ntiles_ = 0;
+    int block_ = 256;
+    int grid_ = 0;
+    int flip_ = 0;
+    int aa_phase_ = 0;
+    bool dirty_ = true;
+    long long launches_ = 0;
+    std::map<std::tuple<long long, int, int>, cudaGraphExec_t> graphs_;
+    double *d_stage_ = nullptr;       // FP64 staging for import/export (one direction)
+    long long stage_cells_ = 0;
+};
+
+lbm_status fail(lbm_status st, const std::string &msg);
+// Checks a descriptor without touching the GPU.
+lbm_status validate_desc(const lbm_desc &d);
+// Observables of an instance's last reduction (Eqs. Darcy, Forchheimer, frictionFactor).
+void compute_obs(const Instance &in, double K_D, lbm_obs *out);
+lbm_status cuda_fail(cudaError_t e, const char *what);
+
+}  // namespace lbm

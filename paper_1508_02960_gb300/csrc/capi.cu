@@ -1,0 +1,323 @@
+// capi.cu -- extern "C" entry points for contexts and batches, and the host arithmetic
+// of the observables (Eqs. Darcy, Forchheimer, frictionFactor) and the convergence test.
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <new>
+
+#include "batch.h"
+
+using namespace lbm;
+
+namespace lbm {
+const char *last_error_cstr();
+}
+
+struct lbm_ctx {
+    Batch b;
+};
+struct lbm_batch {
+    Batch b;
+};
+
+namespace lbm {
+
+// Observables in lattice units with rho = rho0: mu = rho0 (tau - 1/2)/3, nu = (tau - 1/2)/3,
+// delta_p = delta_rho / 3 (p = rho c_s^2), gradP = delta_p / L_x, K = mu U / gradP
+// (Eq. Darcy), Re_p = U d_p / nu, and with K_D: beta = (gradP - mu U / K_D)/(rho U^2)
+// (Eq. Forchheimer), C_F = beta sqrt(K_D), F_K = gradP sqrt(K_D)/(rho U^2),
+// Re_K = rho U sqrt(K_D)/mu (Eq. frictionFactor).
+void compute_obs(const Instance &in, double K_D, lbm_obs *o)
+{
+    const lbm_desc &d = in.desc;
+    const double nan = std::numeric_limits<double>::quiet_NaN();
+    const double ncell = (double)in.geo.ncells, nf = (double)in.geo.n_fluid;
+    std::memset(o, 0, sizeof(*o));
+    o->U_sup = in.sums[1] / ncell;
+    o->U_int = nf > 0 ? in.sums[1] / nf : nan;
+    o->mass = nf * d.rho0 + in.sums[0];
+    o->porosity = nf / ncell;
+    const double mu = d.rho0 * (d.tau - 0.5) / 3.0, nu = (d.tau - 0.5) / 3.0;
+    const double gradP = (d.delta_rho / 3.0) / d.nx;
+    const double U = o->U_sup;
+    o->K = gradP != 0 ? mu * U / gradP : nan;
+    o->K_app = o->K;
+    o->Re_p = in.d_p > 0 ? U * in.d_p / nu : nan;
+    if (K_D > 0) {
+        const double sk = std::sqrt(K_D);
+        o->beta = (gradP - mu * U / K_D) / (d.rho0 * U * U);
+        o->C_F = o->beta * sk;
+        o->F_K = gradP * sk / (d.rho0 * U * U);
+        o->Re_K = d.rho0 * U * sk / mu;
+    } else {
+        o->beta = o->C_F = o->F_K = o->Re_K = nan;
+    }
+    o->u_max = 0.0;
+    o->steps = in.steps;
+    o->n_fluid = in.geo.n_fluid;
+}
+
+}  // namespace lbm
+
+namespace {
+
+lbm_status create_batch(Batch &b, const lbm_desc *descs, int n, cudaStream_t s)
+{
+    for (int i = 0; i < n; ++i) {
+        lbm_status v = validate_desc(descs[i]);
+        if (v != LBM_OK) return v;
+        if (descs[i].storage != descs[0].storage || descs[i].collision != descs[0].collision ||
+            descs[i].layout != descs[0].layout)
+            return fail(LBM_ERR_ARG, "instances of a batch must share storage, collision and layout");
+    }
+    lbm_status st = b.init(s, descs[0].storage, descs[0].collision, descs[0].layout);
+    if (st != LBM_OK) return st;
+    int block = 0;
+    for (int i = 0; i < n; ++i) {
+        std::unique_ptr<Instance> in;
+        st = Batch::make_instance(descs[i], s, &in);
+        if (st != LBM_OK) return st;
+        if (descs[i].block_cells) block = descs[i].block_cells;
+        st = b.add(std::move(in));
+        if (st != LBM_OK) return st;
+    }
+    if (block) return b.set_block(block);
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lbm_last_error(void) { return last_error_cstr(); }
+const char *lbm_version(void) { return "lbm_gb300 0.1 (sm_103a)"; }
+
+lbm_status lbm_create(const lbm_desc *desc, void *cuda_stream, lbm_ctx **out)
+{
+    if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!desc) return fail(LBM_ERR_ARG, "desc is NULL");
+    lbm_ctx *c = new (std::nothrow) lbm_ctx();
+    if (!c) return fail(LBM_ERR_NO_MEMORY, "host allocation failed");
+    lbm_status st = create_batch(c->b, desc, 1, (cudaStream_t)cuda_stream);
+    if (st != LBM_OK) {
+        delete c;
+        return st;
+    }
+    *out = c;
+    set_error("");
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx *ctx) { delete ctx; }
+
+lbm_status lbm_init_equilibrium(lbm_ctx *ctx)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "ctx is NULL");
+    return ctx->b.init_equilibrium(-1);
+}
+
+lbm_status lbm_step(lbm_ctx *ctx, int64_t n_steps)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "ctx is NULL");
+    return ctx->b.step(n_steps);
+}
+
+lbm_status lbm_observables(lbm_ctx *ctx, double K_darcy, lbm_obs *out)
+{
+    if (!ctx || !out) return fail(LBM_ERR_ARG, "NULL argument");
+    Instance &in = ctx->b.at(0);
+    if (!in.have_sums) {
+        lbm_status st;
+        if (in.sums_pending) {
+            st = ctx->b.fetch_sums();
+        } else {  // no step since the state was set: reduce the stored state
+            st = ctx->b.moment_sums_now(0, in.sums);
+            in.status = 0;
+            in.have_sums = (st == LBM_OK);
+        }
+        if (st != LBM_OK) return st;
+    }
+    compute_obs(in, K_darcy, out);
+    if (in.status & STATUS_DIVERGED) return fail(LBM_ERR_DIVERGED, "the last reduction saw a diverged cell");
+    return LBM_OK;
+}
+
+lbm_status lbm_run_to_convergence(lbm_ctx *ctx, double tol, int64_t check_interval, int64_t max_steps,
+                                  int64_t *steps_done)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "ctx is NULL");
+    if (!(tol > 0) || check_interval < 1 || max_steps < 0) return fail(LBM_ERR_ARG, "bad tol/check_interval/max_steps");
+    Instance &in = ctx->b.at(0);
+    int64_t done = 0;
+    double U_old = std::numeric_limits<double>::quiet_NaN();
+    lbm_status result = LBM_ERR_NOT_CONVERGED;
+    while (done < max_steps) {
+        const int64_t m = std::min<int64_t>(check_interval, max_steps - done);
+        lbm_status st = ctx->b.step(m);
+        if (st != LBM_OK) return st;
+        done += m;
+        st = ctx->b.fetch_sums();
+        if (st != LBM_OK) return st;
+        if (in.status & STATUS_DIVERGED) {
+            result = fail(LBM_ERR_DIVERGED, "diverged (non-finite moments or |u| > 0.3)");
+            break;
+        }
+        const double U = in.sums[1] / (double)in.geo.ncells;
+        if (!std::isnan(U_old) && std::fabs(U - U_old) < tol * std::fabs(U)) {
+            result = LBM_OK;
+            break;
+        }
+        U_old = U;
+    }
+    if (steps_done) *steps_done = done;
+    if (result == LBM_ERR_NOT_CONVERGED) set_error("max_steps reached before convergence");
+    return result;
+}
+
+lbm_status lbm_moment_sums(lbm_ctx *ctx, double *sums)
+{
+    if (!ctx || !sums) return fail(LBM_ERR_ARG, "NULL argument");
+    return ctx->b.moment_sums_now(0, sums);
+}
+
+lbm_status lbm_get_populations_f64(lbm_ctx *ctx, double *host_out)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "ctx is NULL");
+    return ctx->b.get_f64(0, host_out);
+}
+
+lbm_status lbm_set_populations_f64(lbm_ctx *ctx, const double *host_in)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "ctx is NULL");
+    return ctx->b.set_f64(0, host_in);
+}
+
+lbm_status lbm_get_velocity_f64(lbm_ctx *ctx, double *host_out)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "ctx is NULL");
+    return ctx->b.get_velocity(0, host_out);
+}
+
+lbm_status lbm_get_flags(lbm_ctx *ctx, uint8_t *host_out)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "ctx is NULL");
+    return ctx->b.get_flags(0, host_out);
+}
+
+lbm_status lbm_get_wall_distances(lbm_ctx *ctx, double *host_out)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "ctx is NULL");
+    return ctx->b.get_q(0, host_out);
+}
+
+lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *out)
+{
+    if (!ctx || !out) return fail(LBM_ERR_ARG, "NULL argument");
+    ctx->b.fill_info(0, out);
+    return LBM_OK;
+}
+
+lbm_status lbm_synchronize(lbm_ctx *ctx)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "ctx is NULL");
+    return ctx->b.sync();
+}
+
+lbm_status lbm_save(lbm_ctx *ctx, const char *path)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "ctx is NULL");
+    return ctx->b.save(0, path);
+}
+
+lbm_status lbm_load(lbm_ctx *ctx, const char *path)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "ctx is NULL");
+    return ctx->b.load(0, path);
+}
+
+// Solve gradP = mu U / K_D + (C_F / sqrt(K_D)) rho U^2 for the U of the target Re_p
+// (U = Re_p nu / d_p) and return delta_rho = 3 L gradP.
+double lbm_delta_rho_for_re_p(double re_p, double tau, double d_p, int32_t lx, double K_D, double C_F, double rho0)
+{
+    if (rho0 <= 0) rho0 = 1.0;
+    const double nu = (tau - 0.5) / 3.0, mu = rho0 * nu;
+    const double U = re_p * nu / d_p;
+    const double gradP = mu * U / K_D + (K_D > 0 ? C_F / std::sqrt(K_D) : 0.0) * rho0 * U * U;
+    return 3.0 * lx * gradP;
+}
+
+// ---- batches ---------------------------------------------------------------------------
+lbm_status lbm_batch_create(const lbm_desc *descs, int32_t n, void *cuda_stream, lbm_batch **out)
+{
+    if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!descs || n < 1) return fail(LBM_ERR_ARG, "need at least one descriptor");
+    for (int i = 0; i < n; ++i)
+        if (descs[i].layout != LBM_LAYOUT_AB) return fail(LBM_ERR_ARG, "batches use the A-B layout");
+    lbm_batch *b = new (std::nothrow) lbm_batch();
+    if (!b) return fail(LBM_ERR_NO_MEMORY, "host allocation failed");
+    lbm_status st = create_batch(b->b, descs, n, (cudaStream_t)cuda_stream);
+    if (st != LBM_OK) {
+        delete b;
+        return st;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch *b) { delete b; }
+
+lbm_status lbm_batch_init_equilibrium(lbm_batch *b)
+{
+    if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
+    return b->b.init_equilibrium(-1);
+}
+
+lbm_status lbm_batch_step(lbm_batch *b, int64_t n_steps)
+{
+    if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
+    return b->b.step(n_steps);
+}
+
+lbm_status lbm_batch_observables(lbm_batch *b, int32_t i, double K_darcy, lbm_obs *out)
+{
+    if (!b || !out) return fail(LBM_ERR_ARG, "NULL argument");
+    if (i < 0 || i >= b->b.size()) return fail(LBM_ERR_ARG, "instance index out of range");
+    Instance &in = b->b.at(i);
+    if (!in.have_sums) {
+        lbm_status st;
+        if (in.sums_pending) {
+            st = b->b.fetch_sums();
+        } else {
+            st = b->b.moment_sums_now(i, in.sums);
+            in.status = 0;
+            in.have_sums = (st == LBM_OK);
+        }
+        if (st != LBM_OK) return st;
+    }
+    compute_obs(in, K_darcy, out);
+    if (in.status & STATUS_DIVERGED) return fail(LBM_ERR_DIVERGED, "the last reduction saw a diverged cell");
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_get_populations_f64(lbm_batch *b, int32_t i, double *host_out)
+{
+    if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
+    return b->b.get_f64(i, host_out);
+}
+
+lbm_status lbm_batch_set_populations_f64(lbm_batch *b, int32_t i, const double *host_in)
+{
+    if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
+    return b->b.set_f64(i, host_in);
+}
+
+lbm_status lbm_batch_get_info(lbm_batch *b, lbm_info *out)
+{
+    if (!b || !out) return fail(LBM_ERR_ARG, "NULL argument");
+    b->b.fill_info(-1, out);
+    return LBM_OK;
+}
+
+}  // extern "C"

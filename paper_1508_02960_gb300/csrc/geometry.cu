@@ -1,0 +1,467 @@
+// geometry.cu -- device construction of the solid flags, the per-segment cell tables,
+// the boundary-cell table and the wall distance q of every cut link (Sec. 2.2.1 and
+// Sec. 3: for a non-deforming medium they are computed once before time stepping).
+//
+// Steps (all on the device, deterministic):
+//   1. solid[cell]: a cell is solid when its centre (i+1/2, j+1/2, k+1/2) lies within r
+//      of the nearest periodic image of a sphere centre (or copied from a flag field);
+//   2. wm[cell]: bit k set when the fluid cell's pull source x - e_k is solid;
+//   3. per 32-cell segment: solid/out-of-range bits, boundary bits, boundary count;
+//   4. exclusive scan of the counts -> first boundary index of every segment;
+//   5. boundary table (mask, cell) and link counts; scan -> first link of every cell;
+//   6. per link: q from the ray x_f1 + t e_kbar against the spheres (nearest crossing),
+//      or from a caller-supplied q field, and the CLI coefficient (1-2q)/(1+2q), set
+//      to 0 (simple bounce-back) when x_f2 = x + e_k is solid.
+#include <cmath>
+#include <string>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace {
+
+// Nearest periodic image of a displacement along an axis of length n.
+__device__ double min_image(double d, int n)
+{
+    const double h = 0.5 * n;
+    while (d > h) d = __dsub_rn(d, (double)n);
+    while (d < -h) d = __dadd_rn(d, (double)n);
+    return d;
+}
+
+__device__ double dist2_rn(double a, double b, double c)
+{
+    return __dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(c, c));
+}
+
+__global__ void voxelize_kernel(int nx, int ny, int nz, const double4 *__restrict__ sph, int ns,
+                                uint8_t *__restrict__ solid)
+{
+    const long long n = (long long)nx * ny * nz;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % nx);
+        const long long yz = c / nx;
+        const int y = (int)(yz % ny), z = (int)(yz / ny);
+        uint8_t s = 0;
+        for (int i = 0; i < ns; ++i) {
+            const double4 sp = sph[i];
+            const double dx = min_image(__dsub_rn(x + 0.5, sp.x), nx);
+            const double dy = min_image(__dsub_rn(y + 0.5, sp.y), ny);
+            const double dz = min_image(__dsub_rn(z + 0.5, sp.z), nz);
+            if (dist2_rn(dx, dy, dz) <= __dmul_rn(sp.w, sp.w)) s = 1;
+        }
+        solid[c] = s;
+    }
+}
+
+__global__ void wallmask_kernel(int nx, int ny, int nz, const uint8_t *__restrict__ solid,
+                                uint32_t *__restrict__ wm)
+{
+    const long long n = (long long)nx * ny * nz;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        uint32_t m = 0u;
+        if (!solid[c]) {
+            const int x = (int)(c % nx);
+            const long long yz = c / nx;
+            const int y = (int)(yz % ny), z = (int)(yz / ny);
+#pragma unroll
+            for (int k = 1; k < Q; ++k) {
+                const int xs = (x - ex(k) + nx) % nx, ys = (y - ey(k) + ny) % ny, zs = (z - ez(k) + nz) % nz;
+                if (solid[xs + (long long)nx * (ys + (long long)ny * zs)]) m |= 1u << k;
+            }
+        }
+        wm[c] = m;
+    }
+}
+
+// One warp per segment.  count[s] = boundary cells; fluid count accumulated atomically.
+__global__ void segment_kernel(long long n, long long nseg_padded, const uint8_t *__restrict__ solid,
+                               const uint32_t *__restrict__ wm, uint4 *__restrict__ seg,
+                               unsigned long long *__restrict__ count, unsigned long long *__restrict__ nfluid)
+{
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long s = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < nseg_padded;
+         s += warps) {
+        const long long c = s * 32 + lane;
+        const bool in = c < n;
+        const bool sol = !in || solid[c];
+        const bool bnd = in && !sol && wm[c] != 0u;
+        const unsigned sb = __ballot_sync(0xffffffffu, sol);
+        const unsigned bb = __ballot_sync(0xffffffffu, bnd);
+        if (lane == 0) {
+            seg[s] = make_uint4(sb, bb, 0u, 0u);
+            count[s] = __popc(bb);
+            const int nf = 32 - __popc(sb);
+            if (nf) atomicAdd(nfluid, (unsigned long long)nf);
+        }
+    }
+}
+
+__global__ void seg_base_kernel(long long nseg, uint4 *__restrict__ seg, const unsigned long long *__restrict__ base)
+{
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < nseg;
+         s += (long long)gridDim.x * blockDim.x)
+        seg[s].z = (uint32_t)base[s];
+}
+
+__global__ void boundary_kernel(long long n, const uint4 *__restrict__ seg, const uint32_t *__restrict__ wm,
+                                uint32_t *__restrict__ bmask, long long *__restrict__ bcell,
+                                unsigned long long *__restrict__ nlink)
+{
+    const int lane = threadIdx.x & 31;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        const uint4 m = seg[c >> 5];
+        if ((m.y >> lane) & 1u) {
+            const uint32_t b = m.z + __popc(m.y & ((1u << lane) - 1u));
+            bmask[b] = wm[c];
+            bcell[b] = c;
+            nlink[b] = __popc(wm[c]);
+        }
+    }
+}
+
+__global__ void to_u32_kernel(long long n, const unsigned long long *__restrict__ in, uint32_t *__restrict__ out)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = (uint32_t)in[i];
+}
+
+template <typename R>
+__global__ void link_kernel(long long nb, int nx, int ny, int nz, const double4 *__restrict__ sph, int ns,
+                            const double *__restrict__ qfield, const uint8_t *__restrict__ solid,
+                            const uint32_t *__restrict__ bmask, const uint32_t *__restrict__ boff,
+                            const long long *__restrict__ bcell, double *__restrict__ linkq, R *__restrict__ linkc,
+                            unsigned long long *__restrict__ ncli)
+{
+    const long long n = (long long)nx * ny * nz;
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
+         b += (long long)gridDim.x * blockDim.x) {
+        const long long c = bcell[b];
+        const uint32_t m = bmask[b];
+        const int x = (int)(c % nx);
+        const long long yz = c / nx;
+        const int y = (int)(yz % ny), z = (int)(yz / ny);
+        uint32_t l = boff[b];
+        int cli = 0;
+        for (int k = 1; k < Q; ++k) {
+            if (!((m >> k) & 1u)) continue;
+            const int kd = opp(k);  // link direction from x_f1 into the wall
+            double q = 0.5;
+            if (sph) {
+                // solid end point x_b = x + e_kd; nearest crossing of the segment x_f1 -> x_b
+                const double bx = x + ex(kd) + 0.5, by = y + ey(kd) + 0.5, bz = z + ez(kd) + 0.5;
+                double best = INFINITY;
+                for (int i = 0; i < ns; ++i) {
+                    const double4 sp = sph[i];
+                    const double cx = __dsub_rn(bx, min_image(__dsub_rn(bx, sp.x), nx));
+                    const double cy = __dsub_rn(by, min_image(__dsub_rn(by, sp.y), ny));
+                    const double cz = __dsub_rn(bz, min_image(__dsub_rn(bz, sp.z), nz));
+                    if (dist2_rn(__dsub_rn(bx, cx), __dsub_rn(by, cy), __dsub_rn(bz, cz)) > __dmul_rn(sp.w, sp.w))
+                        continue;
+                    const double px = __dsub_rn(x + 0.5, cx), py = __dsub_rn(y + 0.5, cy), pz = __dsub_rn(z + 0.5, cz);
+                    const double a = (double)speed2(kd);
+                    const double hb = __dadd_rn(__dadd_rn(__dmul_rn(px, (double)ex(kd)), __dmul_rn(py, (double)ey(kd))),
+                                                __dmul_rn(pz, (double)ez(kd)));
+                    const double cc = __dsub_rn(dist2_rn(px, py, pz), __dmul_rn(sp.w, sp.w));
+                    double disc = __dsub_rn(__dmul_rn(hb, hb), __dmul_rn(a, cc));
+                    if (disc < 0.0) disc = 0.0;
+                    const double t = __ddiv_rn(__dsub_rn(-hb, __dsqrt_rn(disc)), a);
+                    if (t < best) best = t;
+                }
+                if (best < INFINITY) q = best;
+            } else if (qfield) {
+                q = qfield[(long long)kd * n + c];
+                if (!(q == q)) q = 0.5;
+            }
+            if (q < 1e-6) q = 1e-6;
+            if (q > 1.0) q = 1.0;
+            // x_f2 = x_f1 - e_kd = x + e_k must be fluid for CLI (else simple bounce-back)
+            const int x2 = (x + ex(k) + nx) % nx, y2 = (y + ey(k) + ny) % ny, z2 = (z + ez(k) + nz) % nz;
+            const bool f2 = !solid[x2 + (long long)nx * (y2 + (long long)ny * z2)];
+            const double cq = f2 ? __ddiv_rn(__dsub_rn(1.0, 2.0 * q), __dadd_rn(1.0, 2.0 * q)) : 0.0;
+            linkq[l] = q;
+            linkc[l] = (R)cq;
+            cli += f2;
+            ++l;
+        }
+        if (cli) atomicAdd(ncli, (unsigned long long)cli);
+    }
+}
+
+__global__ void scatter_q_kernel(long long nb, int kdir, const uint32_t *__restrict__ bmask,
+                                 const uint32_t *__restrict__ boff, const long long *__restrict__ bcell,
+                                 const double *__restrict__ linkq, double *__restrict__ qk)
+{
+    const int k = opp(kdir);  // pull direction whose source is the wall
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
+         b += (long long)gridDim.x * blockDim.x) {
+        const uint32_t m = bmask[b];
+        if ((m >> k) & 1u) qk[bcell[b]] = linkq[boff[b] + __popc(m & ((1u << k) - 1u))];
+    }
+}
+
+__global__ void fill_kernel(long long n, double v, double *__restrict__ out)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = v;
+}
+
+// ---- exclusive scan of unsigned 64-bit counts (deterministic, recursive) ----------------
+__global__ void scan_block_kernel(const unsigned long long *__restrict__ in, unsigned long long *__restrict__ out,
+                                  unsigned long long *__restrict__ bsum, long long n)
+{
+    __shared__ unsigned long long ws[32];
+    const long long i = (long long)blockIdx.x * 1024 + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned long long v = i < n ? in[i] : 0ull;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = ws[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        ws[lane] = w;
+    }
+    __syncthreads();
+    const unsigned long long excl = x - v + (warp ? ws[warp - 1] : 0ull);
+    if (i < n) out[i] = excl;
+    if (threadIdx.x == 1023) bsum[blockIdx.x] = excl + v;
+}
+
+__global__ void scan_add_kernel(unsigned long long *__restrict__ out, const unsigned long long *__restrict__ boff,
+                                long long n)
+{
+    const long long i = (long long)blockIdx.x * 1024 + threadIdx.x;
+    if (i < n) out[i] += boff[blockIdx.x];
+}
+
+cudaError_t exclusive_scan(const unsigned long long *in, unsigned long long *out, long long n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const long long nb = (n + 1023) / 1024;
+    unsigned long long *bsum = nullptr, *bscan = nullptr;
+    cudaError_t e = cudaMalloc(&bsum, sizeof(unsigned long long) * nb);
+    if (e != cudaSuccess) return e;
+    scan_block_kernel<<<(unsigned)nb, 1024, 0, s>>>(in, out, bsum, n);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && nb > 1) {
+        e = cudaMalloc(&bscan, sizeof(unsigned long long) * nb);
+        if (e == cudaSuccess) e = exclusive_scan(bsum, bscan, nb, s);
+        if (e == cudaSuccess) {
+            scan_add_kernel<<<(unsigned)nb, 1024, 0, s>>>(out, bscan, n);
+            e = cudaGetLastError();
+        }
+    }
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = e2;
+    cudaFree(bsum);
+    if (bscan) cudaFree(bscan);
+    return e;
+}
+
+int grid_for(long long n, int block)
+{
+    long long g = (n + block - 1) / block;
+    if (g > 152 * 32) g = 152 * 32;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+void free_geometry(GeometryDev *g)
+{
+    cudaFree(g->solid);
+    cudaFree(g->seg);
+    cudaFree(g->bmask);
+    cudaFree(g->boff);
+    cudaFree(g->bcell);
+    cudaFree(g->linkq);
+    cudaFree(g->linkc);
+    *g = GeometryDev();
+}
+
+#define GEO_CHECK(x)                                                                  \
+    do {                                                                              \
+        e = (x);                                                                      \
+        if (e != cudaSuccess) {                                                       \
+            *err = std::string("geometry: ") + #x + ": " + cudaGetErrorString(e);     \
+            goto fail;                                                                \
+        }                                                                             \
+    } while (0)
+
+cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_spheres, const uint8_t *flags,
+                           const double *q_host, bool c_double, cudaStream_t s, GeometryDev *g, std::string *err)
+{
+    cudaError_t e = cudaSuccess;
+    const long long n = (long long)nx * ny * nz;
+    double4 *d_sph = nullptr;
+    double *d_q = nullptr;
+    uint32_t *d_wm = nullptr;
+    unsigned long long *d_cnt = nullptr, *d_base = nullptr, *d_nl = nullptr, *d_lbase = nullptr, *d_ctr = nullptr;
+    unsigned long long h_ctr[2] = {0ull, 0ull};
+    unsigned long long h_last[2];
+    *g = GeometryDev();
+    g->ncells = n;
+    g->nseg = (n + 31) / 32;
+    g->nseg_padded = (g->nseg + kMaxWarpsPerBlock - 1) / kMaxWarpsPerBlock * kMaxWarpsPerBlock;
+
+    GEO_CHECK(cudaMalloc(&g->solid, n));
+    GEO_CHECK(cudaMalloc(&g->seg, sizeof(uint4) * g->nseg_padded));
+    GEO_CHECK(cudaMalloc(&d_wm, sizeof(uint32_t) * n));
+    GEO_CHECK(cudaMalloc(&d_cnt, sizeof(unsigned long long) * g->nseg_padded));
+    GEO_CHECK(cudaMalloc(&d_base, sizeof(unsigned long long) * g->nseg_padded));
+    GEO_CHECK(cudaMalloc(&d_ctr, sizeof(unsigned long long) * 2));
+    GEO_CHECK(cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long) * 2, s));
+
+    if (spheres && n_spheres > 0) {
+        GEO_CHECK(cudaMalloc(&d_sph, sizeof(double4) * n_spheres));
+        GEO_CHECK(cudaMemcpyAsync(d_sph, spheres, sizeof(double4) * n_spheres, cudaMemcpyHostToDevice, s));
+        voxelize_kernel<<<grid_for(n, 256), 256, 0, s>>>(nx, ny, nz, d_sph, n_spheres, g->solid);
+        GEO_CHECK(cudaGetLastError());
+    } else if (flags) {
+        GEO_CHECK(cudaMemcpyAsync(g->solid, flags, n, cudaMemcpyHostToDevice, s));
+    } else {
+        GEO_CHECK(cudaMemsetAsync(g->solid, 0, n, s));
+    }
+    wallmask_kernel<<<grid_for(n, 256), 256, 0, s>>>(nx, ny, nz, g->solid, d_wm);
+    GEO_CHECK(cudaGetLastError());
+    segment_kernel<<<grid_for(g->nseg_padded * 32, 256), 256, 0, s>>>(n, g->nseg_padded, g->solid, d_wm, g->seg,
+                                                                       d_cnt, d_ctr);
+    GEO_CHECK(cudaGetLastError());
+    GEO_CHECK(exclusive_scan(d_cnt, d_base, g->nseg_padded, s));
+    GEO_CHECK(cudaMemcpy(&h_last[0], d_base + g->nseg_padded - 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    GEO_CHECK(cudaMemcpy(&h_last[1], d_cnt + g->nseg_padded - 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    g->n_boundary = (long long)(h_last[0] + h_last[1]);
+    if (g->n_boundary >= (1ll << 32)) {
+        *err = "geometry: too many boundary cells for 32-bit indices";
+        e = cudaErrorInvalidValue;
+        goto fail;
+    }
+    seg_base_kernel<<<grid_for(g->nseg_padded, 256), 256, 0, s>>>(g->nseg_padded, g->seg, d_base);
+    GEO_CHECK(cudaGetLastError());
+
+    if (g->n_boundary > 0) {
+        const long long nb = g->n_boundary;
+        GEO_CHECK(cudaMalloc(&g->bmask, sizeof(uint32_t) * nb));
+        GEO_CHECK(cudaMalloc(&g->boff, sizeof(uint32_t) * nb));
+        GEO_CHECK(cudaMalloc(&g->bcell, sizeof(long long) * nb));
+        GEO_CHECK(cudaMalloc(&d_nl, sizeof(unsigned long long) * nb));
+        GEO_CHECK(cudaMalloc(&d_lbase, sizeof(unsigned long long) * nb));
+        boundary_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, g->seg, d_wm, g->bmask, g->bcell, d_nl);
+        GEO_CHECK(cudaGetLastError());
+        GEO_CHECK(exclusive_scan(d_nl, d_lbase, nb, s));
+        GEO_CHECK(cudaMemcpy(&h_last[0], d_lbase + nb - 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+        GEO_CHECK(cudaMemcpy(&h_last[1], d_nl + nb - 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+        g->n_links = (long long)(h_last[0] + h_last[1]);
+        if (g->n_links >= (1ll << 32)) {
+            *err = "geometry: too many cut links for 32-bit indices";
+            e = cudaErrorInvalidValue;
+            goto fail;
+        }
+        to_u32_kernel<<<grid_for(nb, 256), 256, 0, s>>>(nb, d_lbase, g->boff);
+        GEO_CHECK(cudaGetLastError());
+        if (g->n_links > 0) {
+            GEO_CHECK(cudaMalloc(&g->linkq, sizeof(double) * g->n_links));
+            GEO_CHECK(cudaMalloc(&g->linkc, (c_double ? 8 : 4) * g->n_links));
+            if (q_host && !(spheres && n_spheres > 0)) {
+                GEO_CHECK(cudaMalloc(&d_q, sizeof(double) * Q * n));
+                GEO_CHECK(cudaMemcpyAsync(d_q, q_host, sizeof(double) * Q * n, cudaMemcpyHostToDevice, s));
+            }
+            const double4 *sp = (spheres && n_spheres > 0) ? d_sph : nullptr;
+            if (c_double)
+                link_kernel<double><<<grid_for(nb, 128), 128, 0, s>>>(nb, nx, ny, nz, sp, n_spheres, d_q, g->solid,
+                                                                      g->bmask, g->boff, g->bcell, g->linkq,
+                                                                      (double *)g->linkc, d_ctr + 1);
+            else
+                link_kernel<float><<<grid_for(nb, 128), 128, 0, s>>>(nb, nx, ny, nz, sp, n_spheres, d_q, g->solid,
+                                                                     g->bmask, g->boff, g->bcell, g->linkq,
+                                                                     (float *)g->linkc, d_ctr + 1);
+            GEO_CHECK(cudaGetLastError());
+        }
+    }
+    GEO_CHECK(cudaMemcpyAsync(h_ctr, d_ctr, sizeof(h_ctr), cudaMemcpyDeviceToHost, s));
+    GEO_CHECK(cudaStreamSynchronize(s));
+    g->n_fluid = (long long)h_ctr[0];
+    g->n_links_cli = (long long)h_ctr[1];
+    g->bytes = n + sizeof(uint4) * g->nseg_padded +
+               (sizeof(uint32_t) * 2 + sizeof(long long)) * g->n_boundary +
+               (sizeof(double) + (c_double ? 8 : 4)) * g->n_links;
+
+    cudaFree(d_sph);
+    cudaFree(d_q);
+    cudaFree(d_wm);
+    cudaFree(d_cnt);
+    cudaFree(d_base);
+    cudaFree(d_nl);
+    cudaFree(d_lbase);
+    cudaFree(d_ctr);
+    return cudaSuccess;
+fail:
+    cudaStreamSynchronize(s);
+    cudaFree(d_sph);
+    cudaFree(d_q);
+    cudaFree(d_wm);
+    cudaFree(d_cnt);
+    cudaFree(d_base);
+    cudaFree(d_nl);
+    cudaFree(d_lbase);
+    cudaFree(d_ctr);
+    free_geometry(g);
+    return e == cudaSuccess ? cudaErrorUnknown : e;
+}
+
+cudaError_t export_wall_distances(const GeometryDev &g, int kdir, double *qk, cudaStream_t s)
+{
+    fill_kernel<<<grid_for(g.ncells, 256), 256, 0, s>>>(g.ncells, NAN, qk);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || g.n_links == 0 || kdir == 0) return e;
+    scatter_q_kernel<<<grid_for(g.n_boundary, 256), 256, 0, s>>>(g.n_boundary, kdir, g.bmask, g.boff, g.bcell,
+                                                                  g.linkq, qk);
+    return cudaGetLastError();
+}
+
+// ---- deterministic final reduction of tile partials ---------------------------------------
+__global__ void final_reduce_kernel(const InstanceDev *__restrict__ table, const int *__restrict__ tile_begin,
+                                    const int *__restrict__ tile_count, double *__restrict__ out)
+{
+    __shared__ double sm[256][4];
+    const int inst = blockIdx.x;
+    const double *p = table[inst].partials;
+    const int nt = tile_count[inst];
+    (void)tile_begin;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int t = threadIdx.x; t < nt; t += blockDim.x)
+        for (int d = 0; d < 4; ++d) a[d] += p[(long long)t * 4 + d];
+    for (int d = 0; d < 4; ++d) sm[threadIdx.x][d] = a[d];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int d = 0; d < 4; ++d) sm[threadIdx.x][d] += sm[threadIdx.x + w][d];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) out[(long long)inst * 4 + threadIdx.x] = sm[0][threadIdx.x];
+}
+
+cudaError_t launch_final_reduce(const InstanceDev *table, const int *tile_begin, const int *tile_count, int n_inst,
+                                double *out, cudaStream_t s)
+{
+    final_reduce_kernel<<<n_inst, 256, 0, s>>>(table, tile_begin, tile_count, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

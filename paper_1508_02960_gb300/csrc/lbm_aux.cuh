@@ -1,0 +1,241 @@
+// lbm_aux.cuh -- kernels around the time step: initial state, import/export of the
+// populations as FP64, velocity field and moment sums of the stored state.  All of
+// them see the state through canonical(): the post-collision population g~_k(x) in
+// either layout.
+#pragma once
+
+#include "lbm_device.cuh"
+#include "lbm_step.cuh"
+
+namespace lbm {
+
+// Where g~_k(x) of a fluid cell lives.  A-B: slot k of the current buffer.  AA after a
+// LOCAL step (or import): own slot kbar.  AA after a PULL step: slot k of x + e_k, or
+// the own slot kbar when x + e_k is solid (bounce-back redirect).
+template <int STORE>
+__device__ __forceinline__ long long canonical_index(const InstanceDev &I, int layout, int aa_phase,
+                                                     int cur, long long cell, int k, uint32_t wm,
+                                                     const long long (&X)[3], const long long (&Y)[3],
+                                                     const long long (&Z)[3], int &buf)
+{
+    const long long N = I.ncells;
+    if (layout == 0) {
+        buf = cur;
+        return (long long)k * N + cell;
+    }
+    buf = 0;
+    const int kb = opp(k);
+    if (aa_phase == 0 || ((wm >> kb) & 1u)) return (long long)kb * N + cell;
+    return (long long)k * N + X[1 + ex(k)] + Y[1 + ey(k)] + Z[1 + ez(k)];
+}
+
+struct CellGeom {
+    long long cell;
+    int x, y, z;
+    long long X[3], Y[3], Z[3];
+    uint32_t wm, off;
+};
+
+__device__ __forceinline__ void cell_geom(const InstanceDev &I, long long cell, uint4 meta, int lane,
+                                          CellGeom &c)
+{
+    const int nx = I.nx, ny = I.ny, nz = I.nz;
+    c.cell = cell;
+    c.x = (int)(cell % nx);
+    const long long yz = cell / nx;
+    c.y = (int)(yz % ny);
+    c.z = (int)(yz / ny);
+    const long long nxy = (long long)nx * ny;
+    c.X[0] = c.x == 0 ? nx - 1 : c.x - 1;
+    c.X[1] = c.x;
+    c.X[2] = c.x == nx - 1 ? 0 : c.x + 1;
+    c.Y[0] = (long long)(c.y == 0 ? ny - 1 : c.y - 1) * nx;
+    c.Y[1] = (long long)c.y * nx;
+    c.Y[2] = (long long)(c.y == ny - 1 ? 0 : c.y + 1) * nx;
+    c.Z[0] = (long long)(c.z == 0 ? nz - 1 : c.z - 1) * nxy;
+    c.Z[1] = (long long)c.z * nxy;
+    c.Z[2] = (long long)(c.z == nz - 1 ? 0 : c.z + 1) * nxy;
+    c.wm = 0u;
+    c.off = 0u;
+    if ((meta.y >> lane) & 1u) {
+        const uint32_t b = meta.z + __popc(meta.y & ((1u << lane) - 1u));
+        c.wm = I.bmask[b];
+        c.off = I.boff[b];
+    }
+}
+
+// SplitMix64 finaliser (Steele, Lea & Flood 2014) as a counter-based hash.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ double hash_uniform_pm1(unsigned long long seed, long long cell, int comp)
+{
+    const unsigned long long h = mix64(seed ^ mix64((unsigned long long)cell * 3ull + (unsigned long long)comp));
+    return ((double)(h >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0;
+}
+
+// Equilibrium initial state g_k = f^eq_k(rho0, u) - w_k rho0 for fluid cells (u = 0 or a
+// seeded perturbation of amplitude amp), 0 in solid cells.  Writes the layout's
+// post-collision form (A-B buffer `cur`, or AA phase 0) and the AA side buffer.
+template <int STORE>
+__global__ void init_kernel(const InstanceDev *__restrict__ table, int inst, int layout, int cur,
+                            double amp, unsigned long long seed)
+{
+    using S = Store<STORE>;
+    using T = typename S::T;
+    const InstanceDev &I = table[inst];
+    const long long N = I.ncells;
+    const int lane = threadIdx.x & 31;
+    for (long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x; cell < N;
+         cell += (long long)gridDim.x * blockDim.x) {
+        const uint4 meta = I.seg[cell >> 5];
+        T *f = reinterpret_cast<T *>(layout == 0 ? (cur ? I.f1 : I.f0) : I.f0);
+        if ((meta.x >> lane) & 1u) {
+#pragma unroll
+            for (int k = 0; k < Q; ++k) f[(long long)k * N + cell] = S::pack(0.0f, I.scale);
+            continue;
+        }
+        double u[3] = {0.0, 0.0, 0.0};
+        if (amp != 0.0)
+            for (int a = 0; a < 3; ++a) u[a] = amp * hash_uniform_pm1(seed, cell, a);
+        const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        uint32_t wm = 0u, off = 0u;
+        if ((meta.y >> lane) & 1u) {
+            const uint32_t b = meta.z + __popc(meta.y & ((1u << lane) - 1u));
+            wm = I.bmask[b];
+            off = I.boff[b];
+        }
+        T *linkB = reinterpret_cast<T *>(I.linkB);
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const double eu = ex(k) * u[0] + ey(k) * u[1] + ez(k) * u[2];
+            const double g = weight(k) * I.rho0 * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+            const T v = S::pack((typename S::R)g, I.scale);
+            f[(long long)(layout == 0 ? k : opp(k)) * N + cell] = v;
+            if (layout == 1 && linkB && ((wm >> k) & 1u)) linkB[off + __popc(wm & ((1u << k) - 1u))] = v;
+        }
+    }
+}
+
+// Import direction k from FP64 f (cells of one direction): g = f - w rho0.
+template <int STORE>
+__global__ void import_kernel(const InstanceDev *__restrict__ table, int inst, int layout, int cur, int k,
+                              const double *__restrict__ fk)
+{
+    using S = Store<STORE>;
+    using T = typename S::T;
+    const InstanceDev &I = table[inst];
+    const long long N = I.ncells;
+    const int lane = threadIdx.x & 31;
+    const double wr = weight(k) * I.rho0;
+    for (long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x; cell < N;
+         cell += (long long)gridDim.x * blockDim.x) {
+        const uint4 meta = I.seg[cell >> 5];
+        T *f = reinterpret_cast<T *>(layout == 0 ? (cur ? I.f1 : I.f0) : I.f0);
+        const long long slot = (long long)(layout == 0 ? k : opp(k)) * N + cell;
+        if ((meta.x >> lane) & 1u) {
+            f[slot] = S::pack(0.0f, I.scale);
+            continue;
+        }
+        const T v = S::pack((typename S::R)(fk[cell] - wr), I.scale);
+        f[slot] = v;
+        if (layout == 1 && ((meta.y >> lane) & 1u) && I.linkB) {
+            const uint32_t b = meta.z + __popc(meta.y & ((1u << lane) - 1u));
+            const uint32_t wm = I.bmask[b];
+            if ((wm >> k) & 1u)
+                reinterpret_cast<T *>(I.linkB)[I.boff[b] + __popc(wm & ((1u << k) - 1u))] = v;
+        }
+    }
+}
+
+// Export direction k as FP64 f = w rho0 + g~ (0 in solid cells).
+template <int STORE>
+__global__ void export_kernel(const InstanceDev *__restrict__ table, int inst, int layout, int cur,
+                              int aa_phase, int k, double *__restrict__ fk)
+{
+    using S = Store<STORE>;
+    using T = typename S::T;
+    const InstanceDev &I = table[inst];
+    const long long N = I.ncells;
+    const int lane = threadIdx.x & 31;
+    const double wr = weight(k) * I.rho0;
+    for (long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x; cell < N;
+         cell += (long long)gridDim.x * blockDim.x) {
+        const uint4 meta = I.seg[cell >> 5];
+        if ((meta.x >> lane) & 1u) {
+            fk[cell] = 0.0;
+            continue;
+        }
+        CellGeom c;
+        cell_geom(I, cell, meta, lane, c);
+        int buf;
+        const long long idx = canonical_index<STORE>(I, layout, aa_phase, cur, cell, k, c.wm, c.X, c.Y, c.Z, buf);
+        const T *f = reinterpret_cast<const T *>(buf ? I.f1 : I.f0);
+        fk[cell] = wr + (double)S::load(f + idx, I.inv_scale);
+    }
+}
+
+// Moments of the stored post-collision state of every fluid cell.  mode 0: write the
+// velocity component `comp` to out[cell] (0 in solid cells).  mode 1: tile partial sums
+// (drho, u_x, u_y, u_z) into I.partials, one block per tile of blockDim/32 segments.
+template <int STORE>
+__global__ void __launch_bounds__(256) moments_kernel(const InstanceDev *__restrict__ table,
+                                                      const TileDev *__restrict__ tiles, int ntiles,
+                                                      int layout, int cur, int aa_phase, int mode, int comp,
+                                                      double *__restrict__ out)
+{
+    using S = Store<STORE>;
+    using T = typename S::T;
+    __shared__ double red[32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const TileDev tile = tiles[t];
+        const InstanceDev &I = table[tile.inst];
+        const long long seg = tile.seg0 + warp;
+        const uint4 meta = I.seg[seg];
+        const long long cell = seg * 32 + lane;
+        double a[4] = {0.0, 0.0, 0.0, 0.0};
+        if (!((meta.x >> lane) & 1u)) {
+            CellGeom c;
+            cell_geom(I, cell, meta, lane, c);
+            double drho = 0.0, j[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                int buf;
+                const long long idx =
+                    canonical_index<STORE>(I, layout, aa_phase, cur, cell, k, c.wm, c.X, c.Y, c.Z, buf);
+                const T *f = reinterpret_cast<const T *>(buf ? I.f1 : I.f0);
+                const double g = (double)S::load(f + idx, I.inv_scale);
+                drho += g;
+                j[0] += ex(k) * g;
+                j[1] += ey(k) * g;
+                j[2] += ez(k) * g;
+            }
+            a[0] = drho;
+            for (int d = 0; d < 3; ++d) a[1 + d] = j[d] / I.rho0;
+        } else if (mode == 0 && cell < I.ncells) {
+            out[cell] = 0.0;
+        }
+        if (mode == 0) {
+            if (!((meta.x >> lane) & 1u)) out[cell] = a[1 + comp];
+            continue;
+        }
+#pragma unroll
+        for (int d = 0; d < 4; ++d) a[d] = warp_sum(a[d]);
+        if (lane == 0)
+            for (int d = 0; d < 4; ++d) red[warp][d] = a[d];
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            double s = 0.0;
+            for (int w = 0; w < nwarps; ++w) s += red[w][threadIdx.x];
+            I.partials[(long long)tile.local * 4 + threadIdx.x] = s;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace lbm

@@ -1,0 +1,156 @@
+// lbm_device.cuh -- device-side definitions shared by the kernels of the GB300 D3Q19
+// sphere-pack library: the D3Q19 lattice (Sec. 2), population storage formats, the
+// per-instance parameter table and the tile work list.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+constexpr int Q = 19;
+
+// D3Q19 velocities: rest, six axis links, twelve face diagonals, opposites adjacent.
+__host__ __device__ constexpr int ex(int k)
+{
+    constexpr int v[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return v[k];
+}
+__host__ __device__ constexpr int ey(int k)
+{
+    constexpr int v[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return v[k];
+}
+__host__ __device__ constexpr int ez(int k)
+{
+    constexpr int v[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return v[k];
+}
+// Opposite direction k-bar (e_kbar = -e_k).
+__host__ __device__ constexpr int opp(int k) { return k == 0 ? 0 : ((k & 1) ? k + 1 : k - 1); }
+// Squared speed and lattice weight (c_s^2 = 1/3 isotropic set).
+__host__ __device__ constexpr int speed2(int k) { return ex(k) * ex(k) + ey(k) * ey(k) + ez(k) * ez(k); }
+__host__ __device__ constexpr double weight(int k)
+{
+    return speed2(k) == 0 ? 1.0 / 3.0 : (speed2(k) == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// MRT moment basis (Sec. 2.1, Eq. MRT): d'Humieres' integer polynomials in e_k, which
+// are already mutually orthogonal over the 19 velocities (the Gram-Schmidt result up
+// to row scaling).  Row order: rho, e, eps, j_x, q_x, j_y, q_y, j_z, q_z, 3p_xx,
+// 3pi_xx, p_ww, pi_ww, p_xy, p_yz, p_xz, m_x, m_y, m_z.
+__host__ __device__ constexpr int mrt_m(int i, int k)
+{
+    const int x = ex(k), y = ey(k), z = ez(k), n2 = speed2(k);
+    switch (i) {
+    case 0: return 1;
+    case 1: return 19 * n2 - 30;
+    case 2: return (21 * n2 * n2 - 53 * n2 + 24) / 2;
+    case 3: return x;
+    case 4: return (5 * n2 - 9) * x;
+    case 5: return y;
+    case 6: return (5 * n2 - 9) * y;
+    case 7: return z;
+    case 8: return (5 * n2 - 9) * z;
+    case 9: return 3 * x * x - n2;
+    case 10: return (3 * n2 - 5) * (3 * x * x - n2);
+    case 11: return y * y - z * z;
+    case 12: return (3 * n2 - 5) * (y * y - z * z);
+    case 13: return x * y;
+    case 14: return y * z;
+    case 15: return x * z;
+    case 16: return (y * y - z * z) * x;
+    case 17: return (z * z - x * x) * y;
+    default: return (x * x - y * y) * z;
+    }
+}
+__host__ __device__ constexpr int mrt_norm2(int i)
+{
+    int s = 0;
+    for (int k = 0; k < Q; ++k) s += mrt_m(i, k) * mrt_m(i, k);
+    return s;
+}
+
+// ------------------------------------------------------------------------------------
+// Storage formats.  Every format stores the deviation g_k = f_k - w_k rho0; R is the
+// arithmetic type of the collision.
+// ------------------------------------------------------------------------------------
+enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
+
+template <int S> struct Store;
+template <> struct Store<ST_F64> {
+    using T = double;
+    using R = double;
+    __device__ static R load(const T *p, float) { return __ldg(p); }
+    __device__ static T pack(R v, float) { return v; }
+};
+template <> struct Store<ST_F32> {
+    using T = float;
+    using R = float;
+    __device__ static R load(const T *p, float) { return __ldg(p); }
+    __device__ static T pack(R v, float) { return v; }
+};
+// FP16 deviation with a power-of-two scale 2^s: stored = g * 2^s (exact scaling).
+template <> struct Store<ST_F16> {
+    using T = __half;
+    using R = float;
+    __device__ static R load(const T *p, float inv_scale) { return __half2float(__ldg(p)) * inv_scale; }
+    __device__ static T pack(R v, float scale) { return __float2half_rn(v * scale); }
+};
+template <> struct Store<ST_BF16> {
+    using T = __nv_bfloat16;
+    using R = float;
+    __device__ static R load(const T *p, float) { return __bfloat162float(__ldg(p)); }
+    __device__ static T pack(R v, float) { return __float2bfloat16_rn(v); }
+};
+
+inline size_t storage_bytes(int s) { return s == ST_F64 ? 8 : (s == ST_F32 ? 4 : 2); }
+
+// ------------------------------------------------------------------------------------
+// Per-instance parameters, read by every kernel from a device table so that one launch
+// can advance many independent cells (the batched sweep) or just one.
+//
+// Geometry is described per 32-cell segment (cells 32s .. 32s+31 of the linear index):
+//   seg[s].x  bit l set: cell 32s+l is solid or beyond the box (no work)
+//   seg[s].y  bit l set: cell 32s+l is fluid with at least one solid pull source
+//   seg[s].z  index of the first such boundary cell of the segment in the boundary table
+// Boundary cell b: bmask[b] bit k set when x - e_k is solid (the pull of direction k hits
+// the wall), boff[b] the index of its first link; its links are ordered by k.  Link l:
+// linkc[l] = CLI coefficient (1-2q)/(1+2q) (0 where CLI falls back to SBB), linkB[l] =
+// the cell's own post-collision population of the link (AA layout only).
+// ------------------------------------------------------------------------------------
+struct InstanceDev {
+    void *f0, *f1;           // populations [19][ncells]; AA uses f0 only
+    const uint4 *seg;        // [nseg]
+    const uint32_t *bmask;   // [n_boundary]
+    const uint32_t *boff;    // [n_boundary]
+    const void *linkc;       // [n_links], type R
+    void *linkB;             // [n_links], type T (AA layout)
+    double *partials;        // [n_tiles of this instance][4]
+    long long ncells;
+    int nx, ny, nz;
+    int wall;                // 0 = SBB, 1 = CLI
+    int phase;               // A-B: buffer holding the current state when flip == 0
+    float scale, inv_scale;  // FP16 deviation scaling
+    double omega;            // SRT omega = 1/tau; TRT omega+
+    double omega_m;          // TRT omega-
+    double s[Q];             // MRT relaxation rates
+    double delta_rho, rho0;
+};
+
+// A tile: nseg consecutive segments of one instance, processed by one thread block.
+struct TileDev {
+    int inst;
+    int local;       // tile index within its instance (partials slot)
+    long long seg0;  // first segment
+};
+
+enum { KIND_AB = 0, KIND_AA_PULL = 1, KIND_AA_LOCAL = 2 };
+enum { COLL_SRT = 0, COLL_TRT = 1, COLL_MRT = 2 };
+
+// Divergence flag bits in the status word.
+enum { STATUS_DIVERGED = 1u };
+
+}  // namespace lbm

@@ -1,0 +1,77 @@
+// lbm_internal.h -- host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lbm_gb300.h"
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// Arguments of one persistent launch over a tile list.
+struct Launch {
+    const InstanceDev *table;
+    const TileDev *tiles;
+    int ntiles;
+    int grid, block;
+    cudaStream_t stream;
+};
+
+// Per-storage-format kernel entry points (one translation unit per format).
+struct FormatOps {
+    cudaError_t (*step)(int coll, int kind, const Launch &L, int flip, int reduce, unsigned *status);
+    cudaError_t (*init)(const InstanceDev *table, int inst, long long ncells, int layout, int cur,
+                        double amp, unsigned long long seed, cudaStream_t s);
+    cudaError_t (*import_dir)(const InstanceDev *table, int inst, long long ncells, int layout, int cur,
+                              int k, const double *fk, cudaStream_t s);
+    cudaError_t (*export_dir)(const InstanceDev *table, int inst, long long ncells, int layout, int cur,
+                              int aa_phase, int k, double *fk, cudaStream_t s);
+    cudaError_t (*moments)(const Launch &L, int layout, int cur, int aa_phase, int mode, int comp,
+                           double *out);
+    const void *(*step_kernel_ptr)(int coll, int kind);  // for occupancy queries
+};
+
+const FormatOps &format_ops(int storage);
+extern const FormatOps ops_f64, ops_f32, ops_f16, ops_bf16;
+
+// Geometry built on the device for one instance (Sec. 3: flags and wall distances are
+// computed once before time stepping).
+struct GeometryDev {
+    long long ncells = 0, nseg = 0, nseg_padded = 0;
+    long long n_fluid = 0, n_boundary = 0, n_links = 0, n_links_cli = 0;
+    uint8_t *solid = nullptr;      // [ncells]
+    uint4 *seg = nullptr;          // [nseg_padded]
+    uint32_t *bmask = nullptr;     // [n_boundary]
+    uint32_t *boff = nullptr;      // [n_boundary]
+    long long *bcell = nullptr;    // [n_boundary] cell index of each boundary cell
+    double *linkq = nullptr;       // [n_links] wall distance q (FP64)
+    void *linkc = nullptr;         // [n_links] CLI coefficient, compute type
+    size_t bytes = 0;
+};
+
+// Builds the geometry tables.  spheres (host, n*4 doubles) or flags (host [ncells]);
+// q_host optional [19][ncells] wall distances indexed by link direction.  linkc is
+// written as double when c_double, else float.  Returns a CUDA error or cudaSuccess;
+// *err receives a message on failure.
+cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_spheres,
+                           const uint8_t *flags, const double *q_host, bool c_double, cudaStream_t s,
+                           GeometryDev *g, std::string *err);
+void free_geometry(GeometryDev *g);
+// Scatter link q values into qk[ncells] for link direction kdir (NaN elsewhere).
+cudaError_t export_wall_distances(const GeometryDev &g, int kdir, double *qk, cudaStream_t s);
+
+// Deterministic final sum of an instance's tile partials: out[4] = sum over tiles
+// t0 .. t0+nt-1 of partials[t][0..3], in a fixed order.  One block per instance.
+cudaError_t launch_final_reduce(const InstanceDev *table, const int *tile_begin, const int *tile_count,
+                                int n_inst, double *out, cudaStream_t s);
+
+// Error helpers
+void set_error(const std::string &msg);
+
+constexpr int kMaxWarpsPerBlock = 32;
+
+}  // namespace lbm

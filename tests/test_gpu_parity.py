@@ -1,0 +1,291 @@
+"""GPU path vs FP64 CPU oracle, element by element, on the same seeded inputs.
+
+Every call goes through the C ABI (ctypes binding).  Tolerances: FP64 storage 1e-12
+relative per population, FP32 storage 1e-5 relative per population; FP16/BF16
+deviation storage one unit in the last place of the stored format per step (the FP32
+collision error is far below that unit).
+"""
+import numpy as np
+import pytest
+
+from paper_1508_02960_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1508_02960_gb300 import capi as C
+    C.lib(build_if_missing=True)
+    return C
+
+
+def _fluid(solid):
+    return solid == 0
+
+
+def rel_err(a, b, solid):
+    m = _fluid(solid)
+    return float(np.max(np.abs(a[:, m] - b[:, m]) / np.abs(b[:, m])))
+
+
+RAGGED = I.Geometry(24, 20, 18, np.array([[11.3, 9.6, 8.7, 6.2]]))   # 8640 cells: partial tiles
+
+
+# ---------------------------------------------------------------------------------------
+# Geometry: flags bit-exact, q to 1e-12
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("geom", [
+    I.centred_sphere(32, 12.0),
+    RAGGED,
+    I.Geometry(20, 16, 12, np.array([[0.3, 15.2, 6.0, 5.1], [10.0, 8.0, 6.0, 3.3]])),  # periodic images
+    I.random_pack(48, 6, 4.0, 7.0, 7),
+])
+def test_geometry_parity(capi, orc, geom):
+    with capi.Context(spheres=geom.spheres, shape=geom.shape, wall=capi.CLI) as ctx:
+        flags = ctx.get_flags()
+        q = ctx.get_wall_distances()
+        info = ctx.info()
+    solid = orc.voxelize(geom.shape, geom.spheres)
+    qref = orc.wall_distances(solid, geom.spheres)
+    assert np.array_equal(flags, solid)
+    assert np.array_equal(np.isfinite(q), np.isfinite(qref))
+    fin = np.isfinite(qref)
+    assert np.abs(q[fin] - qref[fin]).max() <= 1e-12
+    assert info["n_fluid"] == int((solid == 0).sum())
+    assert info["n_links"] == int(fin.sum())
+
+
+def test_geometry_from_flags_and_q(capi, orc):
+    geom = RAGGED
+    solid = orc.voxelize(geom.shape, geom.spheres)
+    qref = orc.wall_distances(solid, geom.spheres)
+    with capi.Context(flags=solid, q=np.nan_to_num(qref, nan=0.5), shape=geom.shape, wall=capi.CLI) as ctx:
+        assert np.array_equal(ctx.get_flags(), solid)
+        q = ctx.get_wall_distances()
+    fin = np.isfinite(qref)
+    assert np.array_equal(np.isfinite(q), fin)
+    assert np.abs(q[fin] - qref[fin]).max() == 0.0
+
+
+# ---------------------------------------------------------------------------------------
+# The reference workload: 32^3, r = 12, TRT Lambda 3/16, SBB, FP64, 2000 steps
+# ---------------------------------------------------------------------------------------
+def test_reference_32_fp64_2000_steps(capi, orc):
+    cfg = I.config_reference_32()
+    g = cfg["geometry"]
+    kw = dict(tau=cfg["tau"], delta_rho=cfg["delta_rho"], magic_lambda=cfg["magic_lambda"],
+              collision=capi.TRT, wall=capi.SBB)
+    with capi.Context(spheres=g.spheres, shape=g.shape, storage=capi.F64, **kw) as ctx:
+        ctx.init_equilibrium()
+        ctx.step(cfg["steps"])
+        f = ctx.get_populations()
+        obs = ctx.observables()
+    solid = orc.voxelize(g.shape, g.spheres)
+    fref, sums, _ = orc.run(solid, orc.init_rest(solid), cfg["steps"], **kw)
+    assert rel_err(f, fref, solid) <= 1e-12
+    U = sums[1] / g.n_cells
+    assert obs["U_sup"] == pytest.approx(U, rel=1e-12)
+    K = orc.observables(U, cfg["tau"], cfg["delta_rho"], g.nx, g.d_p)[1]
+    assert obs["K"] == pytest.approx(K, rel=1e-12)
+    assert obs["mass"] == pytest.approx(sums[0], rel=1e-14)
+    assert np.all(f[:, solid == 1] == 0.0)
+
+
+# ---------------------------------------------------------------------------------------
+# Operator x wall x storage x layout on a ragged box, from a seeded perturbed state
+# ---------------------------------------------------------------------------------------
+def _perturbed_state(orc, solid, amp, seed):
+    _, w, _ = orc.lattice()
+    xi = I.noise((19,) + solid.shape, seed)
+    f = w[:, None, None, None] * (1.0 + amp * xi)
+    f[:, solid == 1] = 0.0
+    return f
+
+
+@pytest.mark.parametrize("layout", ["AB", "AA"])
+@pytest.mark.parametrize("storage", ["F64", "F32"])
+@pytest.mark.parametrize("coll", ["SRT", "TRT", "MRT"])
+@pytest.mark.parametrize("wall", ["SBB", "CLI"])
+def test_step_parity_matrix(capi, orc, layout, storage, coll, wall):
+    g = RAGGED
+    solid = orc.voxelize(g.shape, g.spheres)
+    q = orc.wall_distances(solid, g.spheres)
+    f0 = _perturbed_state(orc, solid, 1e-3, 11)
+    kw = dict(tau=0.62, delta_rho=3e-4, magic_lambda=0.21, collision=getattr(capi, coll),
+              wall=getattr(capi, wall))
+    st = getattr(capi, storage)
+    n = 41
+    with capi.Context(spheres=g.spheres, shape=g.shape, storage=st,
+                      layout=getattr(capi, "LAYOUT_" + layout), **kw) as ctx:
+        ctx.set_populations(f0)
+        ctx.step(n)
+        f = ctx.get_populations()
+        obs = ctx.observables()
+    fref, sums, _ = orc.run(solid, f0, n, q=q, **kw)
+    tol = 1e-12 if storage == "F64" else 1e-5
+    assert rel_err(f, fref, solid) <= tol
+    assert obs["U_sup"] == pytest.approx(sums[1] / g.n_cells, rel=1e-9 if storage == "F64" else 1e-3)
+
+
+@pytest.mark.parametrize("storage", ["F64", "F32"])
+@pytest.mark.parametrize("wall", ["SBB", "CLI"])
+def test_aa_matches_ab_bitwise(capi, orc, storage, wall):
+    g = RAGGED
+    solid = orc.voxelize(g.shape, g.spheres)
+    f0 = _perturbed_state(orc, solid, 1e-3, 5)
+    kw = dict(spheres=g.spheres, shape=g.shape, tau=0.7, delta_rho=2e-4, collision=capi.TRT,
+              wall=getattr(capi, wall), storage=getattr(capi, storage))
+    out = {}
+    for lay in ("AB", "AA"):
+        with capi.Context(layout=getattr(capi, "LAYOUT_" + lay), **kw) as ctx:
+            ctx.set_populations(f0)
+            res = []
+            for n in (1, 1, 5, 12):
+                ctx.step(n)
+                res.append(ctx.get_populations())
+            out[lay] = res
+    for a, b in zip(out["AB"], out["AA"]):
+        assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------------------------------
+# Reduced-precision storage: one step, within one unit in the last place of the format
+# ---------------------------------------------------------------------------------------
+def _round_bf16(x):
+    """Round-to-nearest-even of float64 values to bfloat16 (through float32)."""
+    f = np.asarray(x, dtype=np.float32)
+    b = f.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _ulp_bf16(x):
+    e = np.floor(np.log2(np.maximum(np.abs(x), 1e-38)))
+    return 2.0 ** (e - 7)
+
+
+def _ulp_f16(x):
+    e = np.floor(np.log2(np.maximum(np.abs(x), 2.0 ** -14)))
+    return 2.0 ** (e - 10)
+
+
+@pytest.mark.parametrize("fmt", ["F16DEV", "BF16DEV"])
+@pytest.mark.parametrize("coll", ["TRT", "MRT"])
+@pytest.mark.parametrize("wall", ["SBB", "CLI"])
+def test_half_storage_one_step(capi, orc, fmt, coll, wall):
+    g = RAGGED
+    solid = orc.voxelize(g.shape, g.spheres)
+    q = orc.wall_distances(solid, g.spheres)
+    _, w, _ = orc.lattice()
+    s = 20
+    scale = 2.0 ** s if fmt == "F16DEV" else 1.0
+    xi = I.noise((19,) + solid.shape, 3) * 2e-4
+    if fmt == "F16DEV":
+        dev = np.float16(xi * scale).astype(np.float64) / scale        # exactly storable
+        ulp = lambda v: _ulp_f16(v * scale) / scale
+    else:
+        dev = _round_bf16(xi)
+        ulp = _ulp_bf16
+    f0 = w[:, None, None, None] + dev
+    f0[:, solid == 1] = 0.0
+    kw = dict(tau=0.66, delta_rho=2e-4, collision=getattr(capi, coll), wall=getattr(capi, wall))
+    with capi.Context(spheres=g.spheres, shape=g.shape, storage=getattr(capi, fmt),
+                      dev_scale_log2=s if fmt == "F16DEV" else 0, **kw) as ctx:
+        ctx.set_populations(f0)
+        assert np.abs(ctx.get_populations() - f0).max() < 1e-17       # import is exact
+        ctx.step(1)
+        f = ctx.get_populations()
+    fref, _, _ = orc.run(solid, f0, 1, q=q, **kw)
+    m = solid == 0
+    g_gpu = (f - w[:, None, None, None])[:, m]
+    g_ref = (fref - w[:, None, None, None])[:, m]
+    err = np.abs(g_gpu - g_ref)
+    # FP32 collision error: a few dozen roundings of operands up to max|g| (floor for
+    # results so small that their storage ulp is below it)
+    floor = 64 * 2.0 ** -24 * np.abs(g_ref).max()
+    assert np.all(err <= ulp(g_ref) * 1.0001 + floor)
+
+
+# ---------------------------------------------------------------------------------------
+# Exported fields and reductions
+# ---------------------------------------------------------------------------------------
+def test_velocity_and_moment_sums(capi, orc):
+    g = RAGGED
+    solid = orc.voxelize(g.shape, g.spheres)
+    q = orc.wall_distances(solid, g.spheres)
+    kw = dict(tau=0.7, delta_rho=1e-4, collision=capi.TRT, wall=capi.CLI)
+    with capi.Context(spheres=g.spheres, shape=g.shape, storage=capi.F64, **kw) as ctx:
+        ctx.init_equilibrium()
+        ctx.step(30)
+        u = ctx.get_velocity()
+        sums_state = ctx.moment_sums()
+        obs = ctx.observables()
+    _, sums, uref = orc.run(solid, orc.init_rest(solid), 30, q=q, want_u=True, **kw)
+    scale = np.abs(uref).max()
+    assert np.abs(u - uref).max() <= 1e-10 * scale
+    assert sums_state[1] == pytest.approx(sums[1], rel=1e-10)
+    assert obs["U_sup"] == pytest.approx(sums[1] / g.n_cells, rel=1e-12)
+
+
+def test_mass_conservation_sbb(capi, orc):
+    g = I.centred_sphere(32, 12.0)
+    with capi.Context(spheres=g.spheres, shape=g.shape, storage=capi.F64, tau=0.8, delta_rho=1e-4,
+                      collision=capi.TRT, wall=capi.SBB) as ctx:
+        ctx.init_equilibrium()
+        m0 = ctx.observables()["mass"]
+        ctx.step(500)
+        o = ctx.observables()
+    assert abs(o["mass"] / m0 - 1) < 1e-13
+    assert o["U_sup"] > 0
+
+
+def test_checkpoint_restart_bitwise(capi, orc, tmp_path):
+    g = RAGGED
+    kw = dict(spheres=g.spheres, shape=g.shape, tau=0.7, delta_rho=1e-4, collision=capi.TRT,
+              wall=capi.CLI, storage=capi.F32)
+    for lay in (capi.LAYOUT_AB, capi.LAYOUT_AA):
+        with capi.Context(layout=lay, **kw) as a:
+            a.init_equilibrium()
+            a.step(37)
+            a.save(str(tmp_path / "c.bin"))
+            a.step(20)
+            fa = a.get_populations()
+        with capi.Context(layout=lay, **kw) as b:
+            b.load(str(tmp_path / "c.bin"))
+            assert b.info()["steps"] == 37
+            b.step(20)
+            fb = b.get_populations()
+        assert np.array_equal(fa, fb)
+
+
+def test_divergence_is_reported(capi):
+    g = I.centred_sphere(16, 5.0)
+    with capi.Context(spheres=g.spheres, shape=g.shape, storage=capi.F32, tau=0.5001, delta_rho=0.5,
+                      collision=capi.SRT, wall=capi.SBB) as ctx:
+        ctx.init_equilibrium()
+        st, done = ctx.run_to_convergence(1e-8, 50, 5000)
+        assert st == capi.ERR_DIVERGED
+        assert done < 5000
+
+
+def test_batch_alone_vs_mix_bitwise(capi):
+    geoms = [I.centred_sphere(24, 8.0), RAGGED, I.centred_sphere(40, 15.0)]
+    descs_keep = [capi.make_desc(spheres=gg.spheres, shape=gg.shape, tau=0.6 + 0.05 * i, delta_rho=1e-4 * (i + 1),
+                                 collision=capi.TRT, wall=capi.CLI, storage=capi.F16DEV)
+                  for i, gg in enumerate(geoms)]
+    descs = [d for d, _ in descs_keep]
+    b = capi.Batch(descs)
+    b.init_equilibrium()
+    b.step(60)
+    mix = [(b.get_populations(i), b.observables(i)) for i in range(3)]
+    b.close()
+    for i, d in enumerate(descs):
+        with capi.Context(desc=d) as ctx:
+            ctx.init_equilibrium()
+            ctx.step(60)
+            assert np.array_equal(ctx.get_populations(), mix[i][0])
+            assert ctx.observables()["U_sup"] == mix[i][1]["U_sup"]

@@ -1,0 +1,359 @@
+"""Benchmark of the fused D3Q19 sphere-pack step on GB300.
+
+One benchmark step = one pass of the whole hot path over the workload: CHECK_INTERVAL
+fused stream-collide time steps (pull streaming, periodic pressure shift, CLI walls,
+TRT collision), the FP64 volume-averaged velocity reduction of the last of them, and
+the host convergence/observable evaluation.  The metric is fluid-cell million lattice
+updates per second (MLUPS) and the fraction of the HBM roofline the step kernel
+reaches (19 reads + 19 writes of the stored format per fluid-cell update).
+
+Workload (default): 128^3 periodic simple-cubic cell, sphere radius 60 (porosity
+0.569), TRT with Lambda = 3/16, CLI walls with analytic q, FP32 storage, A-B layout,
+tau = 0.6, pressure drop for Re_p ~ 1.  Synthetic, seeded; inputs (318 MB of
+populations) exceed the 126 MB L2, so no flush is needed between steps.
+
+Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+For N > 1 it runs under torchrun, one independent replica per GPU (the single-cell
+path has no exchange step), barrier + max-over-ranks timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CHECK_INTERVAL = 100
+
+WORKLOADS = {
+    # name: (L, r, storage, layout, collision, wall, tau, delta_rho)
+    "cell128_trt_cli_f32_ab": (128, 60.0, "F32", "AB", "TRT", "CLI", 0.6, 2.0e-5),
+    "cell128_trt_cli_f32_aa": (128, 60.0, "F32", "AA", "TRT", "CLI", 0.6, 2.0e-5),
+    "cell128_srt_cli_f32_ab": (128, 60.0, "F32", "AB", "SRT", "CLI", 0.6, 2.0e-5),
+    "cell128_mrt_cli_f32_ab": (128, 60.0, "F32", "AB", "MRT", "CLI", 0.6, 2.0e-5),
+    "cell256_trt_cli_f16_ab": (256, 120.0, "F16DEV", "AB", "TRT", "CLI", 0.6, 2.0e-5),
+    "cell256_trt_cli_bf16_ab": (256, 120.0, "BF16DEV", "AB", "TRT", "CLI", 0.6, 2.0e-5),
+    "cell512_trt_cli_bf16_aa": (512, 240.0, "BF16DEV", "AA", "TRT", "CLI", 0.505, 1.0e-3),
+    "cell512_trt_cli_f32_aa": (512, 240.0, "F32", "AA", "TRT", "CLI", 0.505, 1.0e-3),
+}
+DEFAULT_WORKLOAD = "cell128_trt_cli_f32_ab"
+BYTES = {"F64": 8, "F32": 4, "F16DEV": 2, "BF16DEV": 2}
+DTYPE = {"F64": "f64", "F32": "f32", "F16DEV": "f32 (f16 storage)", "BF16DEV": "f32 (bf16 storage)"}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples taken during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus: int):
+    import torch
+    rank, world, local = 0, 1, 0
+    if n_gpus > 1 or "RANK" in os.environ:
+        import torch.distributed as dist
+        rank = int(os.environ.get("RANK", 0))
+        world = int(os.environ.get("WORLD_SIZE", 1))
+        local = int(os.environ.get("LOCAL_RANK", 0))
+        if world > 1:
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", init_method="env://")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def cpu_baseline(workload: str, target_s: float = 12.0) -> dict:
+    """The FP64 oracle (as it stands) timed on this host's cores on a bounded sample of the
+    same workload: the same geometry and operators for as many steps as fit ~target_s."""
+    import numpy as np
+
+    import oracle
+    from paper_1508_02960_gb300 import inputs as I
+    L, r, storage, layout, coll, wall, tau, dr = WORKLOADS[workload]
+    g = I.centred_sphere(L, r)
+    solid = oracle.voxelize(g.shape, g.spheres)
+    q = oracle.wall_distances(solid, g.spheres)
+    f = oracle.init_rest(solid)
+    kw = dict(q=q, tau=tau, delta_rho=dr, collision=getattr(oracle, coll), wall=getattr(oracle, wall))
+    nf = int((solid == 0).sum())
+    t0 = time.perf_counter()
+    f, _, _ = oracle.run(solid, f, 1, **kw)
+    t1 = time.perf_counter() - t0
+    steps = max(1, min(200, int(target_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    f, _, _ = oracle.run(solid, f, steps, **kw)
+    dt = time.perf_counter() - t0
+    del f
+    return {"value": nf * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{L}^3 r={r:g} {coll}/{wall} FP64 oracle, {steps} time steps from rest "
+                      f"({nf} fluid cells), OpenMP over z", "seconds": round(dt, 3)}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle on the host cores, each benchmark step a bounded
+    sample (a few time steps) of the same workload."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_1508_02960_gb300 import inputs as I
+    oracle.build()
+    L, r, storage, layout, coll, wall, tau, dr = WORKLOADS[args.workload]
+    g = I.centred_sphere(L, r)
+    solid = oracle.voxelize(g.shape, g.spheres)
+    q = oracle.wall_distances(solid, g.spheres)
+    f = oracle.init_rest(solid)
+    nf = int((solid == 0).sum())
+    kw = dict(q=q, tau=tau, delta_rho=dr, collision=getattr(oracle, coll), wall=getattr(oracle, wall))
+    t0 = time.perf_counter()
+    f, _, _ = oracle.run(solid, f, 1, **kw)
+    t1 = time.perf_counter() - t0
+    # size each sample so that the whole run stays within about two minutes
+    per = max(1, min(CHECK_INTERVAL, int(100.0 / max(args.steps + args.warmup, 1) / max(t1, 1e-3))))
+    for _ in range(args.warmup):
+        f, _, _ = oracle.run(solid, f, per, **kw)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f, sums, _ = oracle.run(solid, f, per, **kw)
+    dt = time.perf_counter() - t0
+    value = nf * per * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": "D3Q19 fluid MLUPS", "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "cells": L ** 3, "fluid_cells": nf,
+                   "time_steps_per_step": per, "note": "FP64 CPU oracle, bounded sample per step"},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": f"{per} time steps of {L}^3 per benchmark step"},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_1508_02960_gb300 import capi
+    from paper_1508_02960_gb300 import inputs as I
+
+    capi.lib()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    L, r, storage, layout, coll, wall, tau, dr = WORKLOADS[args.workload]
+    g = I.centred_sphere(L, r)
+    es = BYTES[storage]
+    ctx = capi.Context(spheres=g.spheres, shape=g.shape, tau=tau, delta_rho=dr, magic_lambda=3 / 16,
+                       collision=getattr(capi, coll), wall=getattr(capi, wall), storage=getattr(capi, storage),
+                       layout=getattr(capi, "LAYOUT_" + layout), block_cells=args.block, stream=stream)
+    info = ctx.info()
+    nf = info["n_fluid"]
+    ctx.init_equilibrium()
+    ctx.step(2 * CHECK_INTERVAL)
+    ctx.observables()
+
+    # ---- device-resident timing -------------------------------------------------------
+    for _ in range(args.warmup):
+        ctx.step(CHECK_INTERVAL)
+        ctx.observables()
+    launches0 = ctx.info()["kernel_launches"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        ctx.step(CHECK_INTERVAL)              # graph: CHECK_INTERVAL fused steps + reduction
+        ev[i][1].record(stream)
+        obs = ctx.observables()               # FP64 sums to host, convergence quantities
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    launches = ctx.info()["kernel_launches"] - launches0
+    total_ms = t_start.elapsed_time(t_end)
+    graph_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(total_ms, world)
+    updates = float(nf) * CHECK_INTERVAL * args.steps
+    value = sum_over_ranks(updates, world) / (total_ms * 1e-3) / 1e6
+
+    # per-launch duration of the step kernel inside the timed region
+    kernel_ms = statistics.mean(graph_ms) / CHECK_INTERVAL
+    alg_bytes = 38.0 * es * nf
+    peak, peak_kind = load_peaks()
+    achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
+
+    # ---- end-to-end through the C ABI with host buffers ---------------------------------
+    f_host = torch.empty((19,) + g.shape, dtype=torch.float64, pin_memory=True).numpy()
+    ctx.get_populations(f_host)
+    for _ in range(2):
+        ctx.set_populations(f_host)
+        ctx.step(CHECK_INTERVAL)
+        ctx.observables()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.set_populations(f_host)           # H2D of the step's input state (FP64 host array)
+        ctx.step(CHECK_INTERVAL)
+        ctx.observables()                     # D2H of the step's result
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_value = sum_over_ranks(updates, world) / e2e_s / 1e6
+
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", f"{args.workload}.traffic.json")
+    if os.path.exists(prof):
+        with open(prof) as fh:
+            traffic = json.load(fh).get("dram_bytes_per_launch")
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline(args.workload)
+        line = {
+            "metric": "D3Q19 fluid MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[storage],
+            "data": "synthetic",
+            "config": {"workload": args.workload, "cells": L ** 3, "fluid_cells": nf, "sphere_radius": r,
+                       "storage": storage, "layout": layout, "collision": coll, "wall": wall, "tau": tau,
+                       "delta_rho": dr, "time_steps_per_step": CHECK_INTERVAL, "block_cells": info["block_cells"],
+                       "l2": "inputs larger than L2 (populations %.0f MB)" % (info["bytes_populations"] / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                         "kernel": "step_kernel", "kernel_ms": kernel_ms,
+                         "alg_bytes_per_launch": alg_bytes},
+            "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": int(19 * g.n_cells * 8),
+                    "d2h_bytes_per_step": 36},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "observables": {"U_sup": obs["U_sup"], "K": obs["K"], "Re_p": obs["Re_p"]},
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--block", type=int, default=0, help="cells per thread block (0 = library default)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", 0))
+        run_reference(args, rank, int(os.environ.get("WORLD_SIZE", 1)))
+        return
+    rank, world, local = dist_setup(args.gpus)
+    run_gpu(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -277,7 +277,7 @@ class Context:
         done = ctypes.c_int64(0)
         st = lib().lbm_run_to_convergence(self._h, float(tol), int(check_interval), int(max_steps),
                                           ctypes.byref(done))
-        if st not in (OK, ERR_NOT_CONVERGED):
+        if st not in (OK, ERR_NOT_CONVERGED, ERR_DIVERGED):
             check(st, "lbm_run_to_convergence")
         return st, int(done.value)
 

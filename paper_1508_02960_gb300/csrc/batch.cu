@@ -54,7 +54,8 @@ lbm_status validate_desc(const lbm_desc &d)
 {
     if (d.nx < 1 || d.ny < 1 || d.nz < 1) return fail(LBM_ERR_ARG, "nx, ny, nz must be >= 1");
     const long long n = (long long)d.nx * d.ny * d.nz;
-    if (n > (1ll << 36)) return fail(LBM_ERR_ARG, "box too large");
+    // the kernels address populations with 32-bit element offsets: 19 n < 2^32
+    if (19 * n >= (1ll << 32)) return fail(LBM_ERR_ARG, "box too large: 19 * nx * ny * nz must be < 2^32");
     if (!(d.tau > 0.5) || !std::isfinite(d.tau)) return fail(LBM_ERR_ARG, "tau must be a finite value > 1/2");
     if (!std::isfinite(d.delta_rho)) return fail(LBM_ERR_ARG, "delta_rho must be finite");
     if (d.rho0 < 0 || !std::isfinite(d.rho0)) return fail(LBM_ERR_ARG, "rho0 must be >= 0 (0 = 1)");
@@ -262,6 +263,9 @@ static void fill_dev(const Instance &in, InstanceDev &D)
     D.linkB = in.linkB;
     D.partials = in.partials;
     D.ncells = in.geo.ncells;
+    D.n32 = (uint32_t)in.geo.ncells;
+    D.div_nx = make_fastdiv((uint32_t)d.nx);
+    D.div_ny = make_fastdiv((uint32_t)d.ny);
     D.nx = d.nx;
     D.ny = d.ny;
     D.nz = d.nz;

@@ -109,6 +109,39 @@ template <> struct Store<ST_BF16> {
 inline size_t storage_bytes(int s) { return s == ST_F64 ? 8 : (s == ST_F32 ? 4 : 2); }
 
 // ------------------------------------------------------------------------------------
+// Unsigned 32-bit division by a run-time invariant divisor d >= 1 with one multiply-high
+// (Granlund & Montgomery, "Division by invariant integers using multiplication", PLDI
+// 1994, the round-up method with an N+1-bit multiplier): l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, t = mulhi(m, n), n / d = (t + ((n - t) >> sh1)) >> sh2
+// with sh1 = min(l, 1), sh2 = max(l - 1, 0).  Exact for every 32-bit n.
+// ------------------------------------------------------------------------------------
+struct FastDiv {
+    uint32_t d, m, sh1, sh2;
+};
+
+inline FastDiv make_fastdiv(uint32_t d)
+{
+    uint32_t l = 0;
+    while ((1ull << l) < d) ++l;
+    FastDiv f;
+    f.d = d;
+    f.m = (uint32_t)((((1ull << l) - d) << 32) / d + 1);
+    f.sh1 = l < 1 ? l : 1;
+    f.sh2 = l > 1 ? l - 1 : 0;
+    return f;
+}
+
+__host__ __device__ __forceinline__ uint32_t fast_div(uint32_t n, const FastDiv &f)
+{
+#ifdef __CUDA_ARCH__
+    const uint32_t t = __umulhi(n, f.m);
+#else
+    const uint32_t t = (uint32_t)(((uint64_t)n * f.m) >> 32);
+#endif
+    return (t + ((n - t) >> f.sh1)) >> f.sh2;
+}
+
+// ------------------------------------------------------------------------------------
 // Per-instance parameters, read by every kernel from a device table so that one launch
 // can advance many independent cells (the batched sweep) or just one.
 //
@@ -130,6 +163,8 @@ struct InstanceDev {
     void *linkB;             // [n_links], type T (AA layout)
     double *partials;        // [n_tiles of this instance][4]
     long long ncells;
+    uint32_t n32;            // ncells (19 * ncells < 2^32 is required)
+    FastDiv div_nx, div_ny;  // division by nx and ny
     int nx, ny, nz;
     int wall;                // 0 = SBB, 1 = CLI
     int phase;               // A-B: buffer holding the current state when flip == 0

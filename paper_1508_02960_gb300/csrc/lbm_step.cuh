@@ -114,30 +114,26 @@ __global__ void __launch_bounds__(256) step_kernel(const InstanceDev *__restrict
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const TileDev tile = tiles[t];
         const InstanceDev &I = table[tile.inst];
-        const long long N = I.ncells;
-        const int nx = I.nx, ny = I.ny, nz = I.nz;
+        const uint32_t N = I.n32;
+        const uint32_t nx = I.nx, ny = I.ny, nz = I.nz;
         const float sc = I.scale, isc = I.inv_scale;
-        const long long seg = tile.seg0 + warp;
+        const uint32_t seg = (uint32_t)tile.seg0 + warp;
         const uint4 meta = I.seg[seg];
         double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
 
         if (!((meta.x >> lane) & 1u)) {
-            const long long cell = seg * 32 + lane;
-            const int x = (int)(cell % nx);
-            const long long yz = cell / nx;
-            const int y = (int)(yz % ny);
-            const int z = (int)(yz / ny);
-            // coordinates of x-1, x, x+1 (periodic) and the row/plane offsets
-            const long long X[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
-            const long long Y[3] = {(long long)(y == 0 ? ny - 1 : y - 1) * nx, (long long)y * nx,
-                                    (long long)(y == ny - 1 ? 0 : y + 1) * nx};
-            const long long nxy = (long long)nx * ny;
-            const long long Z[3] = {(long long)(z == 0 ? nz - 1 : z - 1) * nxy, (long long)z * nxy,
-                                    (long long)(z == nz - 1 ? 0 : z + 1) * nxy};
+            const uint32_t cell = seg * 32u + lane;
+            const uint32_t yz = fast_div(cell, I.div_nx);
+            const uint32_t x = cell - yz * nx;
+            const uint32_t z = fast_div(yz, I.div_ny);
+            const uint32_t y = yz - z * ny;
+            // x-1, x, x+1 (periodic) and the row / plane offsets, all 32-bit element counts
+            const uint32_t nxy = nx * ny;
+            const uint32_t X[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
+            const uint32_t Y[3] = {(y == 0 ? ny - 1 : y - 1) * nx, y * nx, (y == ny - 1 ? 0 : y + 1) * nx};
+            const uint32_t Z[3] = {(z == 0 ? nz - 1 : z - 1) * nxy, z * nxy, (z == nz - 1 ? 0 : z + 1) * nxy};
             // pull source of direction k: x - e_k
-            auto src_of = [&](int k) -> long long {
-                return X[1 - ex(k)] + Y[1 - ey(k)] + Z[1 - ez(k)];
-            };
+            auto src_of = [&](int k) -> uint32_t { return X[1 - ex(k)] + Y[1 - ey(k)] + Z[1 - ez(k)]; };
 
             uint32_t wm = 0u, off = 0u;
             if ((meta.y >> lane) & 1u) {
@@ -164,9 +160,9 @@ __global__ void __launch_bounds__(256) step_kernel(const InstanceDev *__restrict
                     continue;
                 }
                 const T *p;
-                if constexpr (KIND == KIND_AB) p = fs + (long long)k * N + src_of(k);
-                else if constexpr (KIND == KIND_AA_PULL) p = fs + (long long)opp(k) * N + src_of(k);
-                else p = fs + (long long)k * N + cell;
+                if constexpr (KIND == KIND_AB) p = fs + ((uint32_t)k * N + src_of(k));
+                else if constexpr (KIND == KIND_AA_PULL) p = fs + ((uint32_t)opp(k) * N + src_of(k));
+                else p = fs + ((uint32_t)k * N + cell);
                 R v = S::load(p, isc);
                 if (ex(k) == 1 && x == 0) v += R(weight(k)) * dshift;
                 if (ex(k) == -1 && x == nx - 1) v -= R(weight(k)) * dshift;
@@ -181,15 +177,15 @@ __global__ void __launch_bounds__(256) step_kernel(const InstanceDev *__restrict
                     const int kb = opp(k);
                     // own post-collision g~_kbar(x)
                     R C;
-                    if constexpr (KIND == KIND_AB) C = S::load(fs + (long long)kb * N + cell, isc);
-                    else C = S::load(fs + (long long)k * N + cell, isc);
+                    if constexpr (KIND == KIND_AB) C = S::load(fs + ((uint32_t)kb * N + cell), isc);
+                    else C = S::load(fs + ((uint32_t)k * N + cell), isc);
                     R v = C;
                     if (I.wall == 1) {
                         const uint32_t l = off + __popc(wm & ((1u << k) - 1u));
                         const R c = linkc[l];
                         if (c != R(0)) {
                             R B;  // own post-collision g~_k(x)
-                            if constexpr (KIND == KIND_AB) B = S::load(fs + (long long)k * N + cell, isc);
+                            if constexpr (KIND == KIND_AB) B = S::load(fs + ((uint32_t)k * N + cell), isc);
                             else B = S::load(linkB + l, isc);
                             v = c * (g[kb] - B) + C;
                         }
@@ -223,13 +219,13 @@ __global__ void __launch_bounds__(256) step_kernel(const InstanceDev *__restrict
             for (int k = 0; k < Q; ++k) {
                 const T v = S::pack(g[k], sc);
                 if constexpr (KIND == KIND_AB) {
-                    fd[(long long)k * N + cell] = v;
+                    fd[(uint32_t)k * N + cell] = v;
                 } else if constexpr (KIND == KIND_AA_LOCAL) {
-                    fd[(long long)opp(k) * N + cell] = v;
+                    fd[(uint32_t)opp(k) * N + cell] = v;
                 } else {
                     // push to x + e_k = pull source of kbar, or bounce into the own slot
-                    if ((wm >> opp(k)) & 1u) fd[(long long)opp(k) * N + cell] = v;
-                    else fd[(long long)k * N + src_of(opp(k))] = v;
+                    if ((wm >> opp(k)) & 1u) fd[(uint32_t)opp(k) * N + cell] = v;
+                    else fd[(uint32_t)k * N + src_of(opp(k))] = v;
                 }
             }
             if constexpr (KIND != KIND_AB) {

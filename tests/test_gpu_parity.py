@@ -4,6 +4,11 @@ Every call goes through the C ABI (ctypes binding).  Tolerances: FP64 storage 1e
 relative per population, FP32 storage 1e-5 relative per population; FP16/BF16
 deviation storage one unit in the last place of the stored format per step (the FP32
 collision error is far below that unit).
+
+Velocity sums: u is a difference of populations ~0.05 that cancel to ~1e-5, so a
+population rounding of ~1e-17 is ~1e-12 of u on either side (the oracle works on full
+f, the GPU on deviations f - w).  U and K are therefore compared at 1e-9 relative in
+FP64 (the permeability requirement is 1e-3).
 """
 import numpy as np
 import pytest
@@ -88,10 +93,11 @@ def test_reference_32_fp64_2000_steps(capi, orc):
     fref, sums, _ = orc.run(solid, orc.init_rest(solid), cfg["steps"], **kw)
     assert rel_err(f, fref, solid) <= 1e-12
     U = sums[1] / g.n_cells
-    assert obs["U_sup"] == pytest.approx(U, rel=1e-12)
+    assert obs["U_sup"] == pytest.approx(U, rel=1e-9, abs=0)
     K = orc.observables(U, cfg["tau"], cfg["delta_rho"], g.nx, g.d_p)[1]
-    assert obs["K"] == pytest.approx(K, rel=1e-12)
-    assert obs["mass"] == pytest.approx(sums[0], rel=1e-14)
+    assert obs["K"] == pytest.approx(K, rel=1e-9, abs=0)
+    # the oracle sums ~5e5 full populations (its rounding ~1e-13); the GPU sums deviations
+    assert obs["mass"] == pytest.approx(sums[0], rel=1e-11, abs=0)
     assert np.all(f[:, solid == 1] == 0.0)
 
 
@@ -128,7 +134,7 @@ def test_step_parity_matrix(capi, orc, layout, storage, coll, wall):
     fref, sums, _ = orc.run(solid, f0, n, q=q, **kw)
     tol = 1e-12 if storage == "F64" else 1e-5
     assert rel_err(f, fref, solid) <= tol
-    assert obs["U_sup"] == pytest.approx(sums[1] / g.n_cells, rel=1e-9 if storage == "F64" else 1e-3)
+    assert obs["U_sup"] == pytest.approx(sums[1] / g.n_cells, rel=1e-9 if storage == "F64" else 1e-3, abs=0)
 
 
 @pytest.mark.parametrize("storage", ["F64", "F32"])
@@ -227,8 +233,8 @@ def test_velocity_and_moment_sums(capi, orc):
     _, sums, uref = orc.run(solid, orc.init_rest(solid), 30, q=q, want_u=True, **kw)
     scale = np.abs(uref).max()
     assert np.abs(u - uref).max() <= 1e-10 * scale
-    assert sums_state[1] == pytest.approx(sums[1], rel=1e-10)
-    assert obs["U_sup"] == pytest.approx(sums[1] / g.n_cells, rel=1e-12)
+    assert sums_state[1] == pytest.approx(sums[1], rel=1e-9, abs=0)
+    assert obs["U_sup"] == pytest.approx(sums[1] / g.n_cells, rel=1e-9, abs=0)
 
 
 def test_mass_conservation_sbb(capi, orc):

@@ -98,7 +98,7 @@ typedef struct {
     int32_t storage;            /* LBM_F64 / LBM_F32 / LBM_F16DEV / LBM_BF16DEV */
     int32_t layout;             /* LBM_LAYOUT_AB / LBM_LAYOUT_AA */
     int32_t dev_scale_log2;     /* FP16DEV scale exponent; LBM_DEV_SCALE_AUTO = from delta_rho */
-    int32_t block_cells;        /* cells per thread block: 0 = default, else 64..1024, /32 */
+    int32_t block_cells;        /* cells per thread block: 0 = default, else 64..256, /32 */
     double d_p;                 /* particle diameter of Re_p; 0 = volume-mean sphere diameter */
     double perturb_u;           /* lbm_init_equilibrium: amplitude of a seeded random initial
                                    velocity (0 = fluid at rest) */

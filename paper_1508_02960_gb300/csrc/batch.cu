@@ -73,8 +73,8 @@ lbm_status validate_desc(const lbm_desc &d)
     if (d.magic_lambda < 0 || !std::isfinite(d.magic_lambda)) return fail(LBM_ERR_ARG, "magic_lambda must be >= 0");
     if (d.mrt_energy_ratio < 0 || !std::isfinite(d.mrt_energy_ratio))
         return fail(LBM_ERR_ARG, "mrt_energy_ratio must be >= 0");
-    if (d.block_cells != 0 && (d.block_cells < 64 || d.block_cells > 1024 || d.block_cells % 32))
-        return fail(LBM_ERR_ARG, "block_cells must be 0 or a multiple of 32 in [64, 1024]");
+    if (d.block_cells != 0 && (d.block_cells < 64 || d.block_cells > 256 || d.block_cells % 32))
+        return fail(LBM_ERR_ARG, "block_cells must be 0 or a multiple of 32 in [64, 256]");
     if (d.dev_scale_log2 != LBM_DEV_SCALE_AUTO && (d.dev_scale_log2 < -60 || d.dev_scale_log2 > 60))
         return fail(LBM_ERR_ARG, "dev_scale_log2 out of [-60, 60]");
     if (!std::isfinite(d.perturb_u) || std::fabs(d.perturb_u) > 0.3) return fail(LBM_ERR_ARG, "|perturb_u| > 0.3");
@@ -161,7 +161,7 @@ lbm_status Batch::make_instance(const lbm_desc &d0, cudaStream_t s, std::unique_
             return cleanup(e, "cudaMemset");
     }
     // partial sums: one slot of 4 doubles per tile at the smallest tile (2 segments)
-    in->partial_capacity = in->geo.nseg_padded / 2;
+    in->partial_capacity = in->geo.n_active_padded / 2;
     if ((e = cudaMalloc(&in->partials, sizeof(double) * 4 * in->partial_capacity)) != cudaSuccess)
         return cleanup(e, "cudaMalloc(partials)");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cleanup(e, "cudaStreamSynchronize");
@@ -235,7 +235,7 @@ lbm_status Batch::remove(int i)
 
 lbm_status Batch::set_block(int block_cells)
 {
-    if (block_cells < 64 || block_cells > 1024 || block_cells % 32) return fail(LBM_ERR_ARG, "bad block size");
+    if (block_cells < 64 || block_cells > 256 || block_cells % 32) return fail(LBM_ERR_ARG, "bad block size");
     if (block_cells != block_) {
         block_ = block_cells;
         dirty_ = true;
@@ -257,6 +257,7 @@ static void fill_dev(const Instance &in, InstanceDev &D)
     D.f0 = in.f0;
     D.f1 = in.f1;
     D.seg = in.geo.seg;
+    D.aseg = in.geo.aseg;
     D.bmask = in.geo.bmask;
     D.boff = in.geo.boff;
     D.linkc = in.geo.linkc;
@@ -306,7 +307,7 @@ lbm_status Batch::rebuild()
     for (int i = 0; i < n; ++i) {
         Instance &in = *inst_[i];
         fill_dev(in, table[i]);
-        const long long nt = in.geo.nseg_padded / W;
+        const long long nt = in.geo.n_active_padded / W;
         if (nt > in.partial_capacity) return fail(LBM_ERR_STATE, "partials too small");
         tb[i] = (int)tiles.size();
         tc[i] = (int)nt;
@@ -492,10 +493,10 @@ lbm_status Batch::moment_sums_now(int i, double *sums)
         int acc = 0;
         for (int j = 0; j < size(); ++j) {
             tb[j] = acc;
-            acc += (int)(inst_[j]->geo.nseg_padded / (block_ / 32));
+            acc += (int)(inst_[j]->geo.n_active_padded / (block_ / 32));
         }
     }
-    const int nt = (int)(in.geo.nseg_padded / (block_ / 32));
+    const int nt = (int)(in.geo.n_active_padded / (block_ / 32));
     Launch L{d_table_, d_tiles_ + tb[i], nt, std::max(1, nt), block_, stream_};
     CK(ops().moments(L, layout_, cur_of(in), aa_phase_, 1, 0, nullptr));
     CK(launch_final_reduce(d_table_ + i, d_tile_begin_ + i, d_tile_count_ + i, 1, d_sums_ + 4 * i, stream_));
@@ -572,11 +573,13 @@ lbm_status Batch::get_velocity(int i, double *host)
     int acc = 0;
     for (int j = 0; j < size(); ++j) {
         tb[j] = acc;
-        acc += (int)(inst_[j]->geo.nseg_padded / (block_ / 32));
+        acc += (int)(inst_[j]->geo.n_active_padded / (block_ / 32));
     }
-    const int nt = (int)(in.geo.nseg_padded / (block_ / 32));
+    const int nt = (int)(in.geo.n_active_padded / (block_ / 32));
     Launch L{d_table_, d_tiles_ + tb[i], nt, std::max(1, nt), block_, stream_};
     for (int c = 0; c < 3; ++c) {
+        // all-solid segments are not in the work list: clear the whole field first
+        CK(cudaMemsetAsync(d_stage_, 0, sizeof(double) * n, stream_));
         CK(ops().moments(L, layout_, cur_of(in), aa_phase_, 0, c, d_stage_));
         ++launches_;
         CK(cudaMemcpyAsync(host + (long long)c * n, d_stage_, sizeof(double) * n, cudaMemcpyDeviceToHost, stream_));

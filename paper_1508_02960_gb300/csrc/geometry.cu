@@ -12,6 +12,7 @@
 //   6. per link: q from the ray x_f1 + t e_kbar against the spheres (nearest crossing),
 //      or from a caller-supplied q field, and the CLI coefficient (1-2q)/(1+2q), set
 //      to 0 (simple bounce-back) when x_f2 = x + e_k is solid.
+#include <algorithm>
 #include <cmath>
 #include <string>
 
@@ -98,6 +99,33 @@ __global__ void segment_kernel(long long n, long long nseg_padded, const uint8_t
             if (nf) atomicAdd(nfluid, (unsigned long long)nf);
         }
     }
+}
+
+__global__ void active_count_kernel(long long nseg, const uint4 *__restrict__ seg,
+                                    unsigned long long *__restrict__ act)
+{
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < nseg;
+         s += (long long)gridDim.x * blockDim.x)
+        act[s] = seg[s].x != 0xFFFFFFFFu ? 1ull : 0ull;
+}
+
+// aseg[i] = segment entry of the i-th segment that holds fluid, with .w = its index;
+// entries past n_active (padding) have every cell marked solid.
+__global__ void active_scatter_kernel(long long nseg, long long n_active_padded, const uint4 *__restrict__ seg,
+                                      const unsigned long long *__restrict__ act,
+                                      const unsigned long long *__restrict__ pos, uint4 *__restrict__ aseg,
+                                      long long n_active)
+{
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < nseg;
+         s += (long long)gridDim.x * blockDim.x)
+        if (act[s]) {
+            uint4 m = seg[s];
+            m.w = (uint32_t)s;
+            aseg[pos[s]] = m;
+        }
+    for (long long i = n_active + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_active_padded;
+         i += (long long)gridDim.x * blockDim.x)
+        aseg[i] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
 }
 
 __global__ void seg_base_kernel(long long nseg, uint4 *__restrict__ seg, const unsigned long long *__restrict__ base)
@@ -287,6 +315,7 @@ void free_geometry(GeometryDev *g)
 {
     cudaFree(g->solid);
     cudaFree(g->seg);
+    cudaFree(g->aseg);
     cudaFree(g->bmask);
     cudaFree(g->boff);
     cudaFree(g->bcell);
@@ -355,6 +384,20 @@ cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_
     seg_base_kernel<<<grid_for(g->nseg_padded, 256), 256, 0, s>>>(g->nseg_padded, g->seg, d_base);
     GEO_CHECK(cudaGetLastError());
 
+    // list of the segments that hold fluid (the kernels' work list), padded to 32 entries
+    active_count_kernel<<<grid_for(g->nseg_padded, 256), 256, 0, s>>>(g->nseg_padded, g->seg, d_cnt);
+    GEO_CHECK(cudaGetLastError());
+    GEO_CHECK(exclusive_scan(d_cnt, d_base, g->nseg_padded, s));
+    GEO_CHECK(cudaMemcpy(&h_last[0], d_base + g->nseg_padded - 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    GEO_CHECK(cudaMemcpy(&h_last[1], d_cnt + g->nseg_padded - 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    g->n_active = (long long)(h_last[0] + h_last[1]);
+    g->n_active_padded = std::max<long long>(kMaxWarpsPerBlock,
+        (g->n_active + kMaxWarpsPerBlock - 1) / kMaxWarpsPerBlock * kMaxWarpsPerBlock);
+    GEO_CHECK(cudaMalloc(&g->aseg, sizeof(uint4) * g->n_active_padded));
+    active_scatter_kernel<<<grid_for(g->nseg_padded, 256), 256, 0, s>>>(g->nseg_padded, g->n_active_padded, g->seg,
+                                                                         d_cnt, d_base, g->aseg, g->n_active);
+    GEO_CHECK(cudaGetLastError());
+
     if (g->n_boundary > 0) {
         const long long nb = g->n_boundary;
         GEO_CHECK(cudaMalloc(&g->bmask, sizeof(uint32_t) * nb));
@@ -398,7 +441,7 @@ cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_
     GEO_CHECK(cudaStreamSynchronize(s));
     g->n_fluid = (long long)h_ctr[0];
     g->n_links_cli = (long long)h_ctr[1];
-    g->bytes = n + sizeof(uint4) * g->nseg_padded +
+    g->bytes = n + sizeof(uint4) * (g->nseg_padded + g->n_active_padded) +
                (sizeof(uint32_t) * 2 + sizeof(long long)) * g->n_boundary +
                (sizeof(double) + (c_double ? 8 : 4)) * g->n_links;
 

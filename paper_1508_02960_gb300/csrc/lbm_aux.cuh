@@ -180,7 +180,7 @@ __global__ void export_kernel(const InstanceDev *__restrict__ table, int inst, i
 }
 
 // Moments of the stored post-collision state of every fluid cell.  mode 0: write the
-// velocity component `comp` to out[cell] (0 in solid cells).  mode 1: tile partial sums
+// velocity component `comp` to out[cell] of fluid cells (the caller clears out first).  mode 1: tile partial sums
 // (drho, u_x, u_y, u_z) into I.partials, one block per tile of blockDim/32 segments.
 template <int STORE>
 __global__ void __launch_bounds__(256) moments_kernel(const InstanceDev *__restrict__ table,
@@ -195,9 +195,8 @@ __global__ void __launch_bounds__(256) moments_kernel(const InstanceDev *__restr
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const TileDev tile = tiles[t];
         const InstanceDev &I = table[tile.inst];
-        const long long seg = tile.seg0 + warp;
-        const uint4 meta = I.seg[seg];
-        const long long cell = seg * 32 + lane;
+        const uint4 meta = I.aseg[tile.seg0 + warp];
+        const long long cell = (long long)meta.w * 32 + lane;
         double a[4] = {0.0, 0.0, 0.0, 0.0};
         if (!((meta.x >> lane) & 1u)) {
             CellGeom c;
@@ -217,8 +216,6 @@ __global__ void __launch_bounds__(256) moments_kernel(const InstanceDev *__restr
             }
             a[0] = drho;
             for (int d = 0; d < 3; ++d) a[1 + d] = j[d] / I.rho0;
-        } else if (mode == 0 && cell < I.ncells) {
-            out[cell] = 0.0;
         }
         if (mode == 0) {
             if (!((meta.x >> lane) & 1u)) out[cell] = a[1 + comp];

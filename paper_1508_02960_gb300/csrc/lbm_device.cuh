@@ -157,6 +157,7 @@ __host__ __device__ __forceinline__ uint32_t fast_div(uint32_t n, const FastDiv 
 struct InstanceDev {
     void *f0, *f1;           // populations [19][ncells]; AA uses f0 only
     const uint4 *seg;        // [nseg]
+    const uint4 *aseg;       // [n_active_padded]: seg entries of segments holding fluid, .w = segment
     const uint32_t *bmask;   // [n_boundary]
     const uint32_t *boff;    // [n_boundary]
     const void *linkc;       // [n_links], type R
@@ -175,11 +176,12 @@ struct InstanceDev {
     double delta_rho, rho0;
 };
 
-// A tile: nseg consecutive segments of one instance, processed by one thread block.
+// A tile: blockDim/32 consecutive entries of an instance's active-segment list (the
+// segments that hold at least one fluid cell), processed by one thread block.
 struct TileDev {
     int inst;
     int local;       // tile index within its instance (partials slot)
-    long long seg0;  // first segment
+    long long seg0;  // first entry of the active-segment list
 };
 
 enum { KIND_AB = 0, KIND_AA_PULL = 1, KIND_AA_LOCAL = 2 };

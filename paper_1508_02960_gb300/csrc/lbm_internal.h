@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/lbm_gb300.h"
+#include "lbm_gb300.h"
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -45,6 +45,8 @@ struct GeometryDev {
     long long n_fluid = 0, n_boundary = 0, n_links = 0, n_links_cli = 0;
     uint8_t *solid = nullptr;      // [ncells]
     uint4 *seg = nullptr;          // [nseg_padded]
+    uint4 *aseg = nullptr;         // [n_active_padded] segments holding fluid: {x, y, z, segment}
+    long long n_active = 0, n_active_padded = 0;
     uint32_t *bmask = nullptr;     // [n_boundary]
     uint32_t *boff = nullptr;      // [n_boundary]
     long long *bcell = nullptr;    // [n_boundary] cell index of each boundary cell

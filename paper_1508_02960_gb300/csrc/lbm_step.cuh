@@ -117,12 +117,11 @@ __global__ void __launch_bounds__(256) step_kernel(const InstanceDev *__restrict
         const uint32_t N = I.n32;
         const uint32_t nx = I.nx, ny = I.ny, nz = I.nz;
         const float sc = I.scale, isc = I.inv_scale;
-        const uint32_t seg = (uint32_t)tile.seg0 + warp;
-        const uint4 meta = I.seg[seg];
+        const uint4 meta = I.aseg[(uint32_t)tile.seg0 + warp];  // {solid, boundary, base, segment}
         double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
 
         if (!((meta.x >> lane) & 1u)) {
-            const uint32_t cell = seg * 32u + lane;
+            const uint32_t cell = meta.w * 32u + lane;
             const uint32_t yz = fast_div(cell, I.div_nx);
             const uint32_t x = cell - yz * nx;
             const uint32_t z = fast_div(yz, I.div_ny);

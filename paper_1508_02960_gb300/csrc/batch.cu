@@ -1,8 +1,8 @@
 // batch.cu -- runtime of a set of independent periodic cells advanced together.
 //
 // One time step of every instance is one launch of the fused step kernel over a tile
-// list (tiles never span two instances, so each instance's reduction order is the
-// same alone or in a mix).  Repeated step sequences are captured once as CUDA graphs
+// list of work chunks (chunks never span two instances and their partial sums are kept
+// per chunk, so each instance's reduction order is the same alone or in a mix).  Repeated step sequences are captured once as CUDA graphs
 // (n steps + the final FP64 reduction) and replayed on the caller's stream.
 #include <algorithm>
 #include <cmath>
@@ -11,6 +11,7 @@
 #include <string>
 
 #include "batch.h"
+#include "lbm_step.cuh"
 
 namespace lbm {
 
@@ -73,8 +74,8 @@ lbm_status validate_desc(const lbm_desc &d)
     if (d.magic_lambda < 0 || !std::isfinite(d.magic_lambda)) return fail(LBM_ERR_ARG, "magic_lambda must be >= 0");
     if (d.mrt_energy_ratio < 0 || !std::isfinite(d.mrt_energy_ratio))
         return fail(LBM_ERR_ARG, "mrt_energy_ratio must be >= 0");
-    if (d.block_cells != 0 && (d.block_cells < 64 || d.block_cells > 256 || d.block_cells % 32))
-        return fail(LBM_ERR_ARG, "block_cells must be 0 or a multiple of 32 in [64, 256]");
+    if (d.block_cells != 0 && (d.block_cells < 32 * kMinChunkSegs || d.block_cells > 1024 || d.block_cells % 32))
+        return fail(LBM_ERR_ARG, "block_cells (cells per work chunk) must be 0 or a multiple of 32 in [128, 1024]");
     if (d.dev_scale_log2 != LBM_DEV_SCALE_AUTO && (d.dev_scale_log2 < -60 || d.dev_scale_log2 > 60))
         return fail(LBM_ERR_ARG, "dev_scale_log2 out of [-60, 60]");
     if (!std::isfinite(d.perturb_u) || std::fabs(d.perturb_u) > 0.3) return fail(LBM_ERR_ARG, "|perturb_u| > 0.3");
@@ -161,7 +162,8 @@ lbm_status Batch::make_instance(const lbm_desc &d0, cudaStream_t s, std::unique_
             return cleanup(e, "cudaMemset");
     }
     // partial sums: one slot of 4 doubles per tile at the smallest tile (2 segments)
-    in->partial_capacity = in->geo.n_active_padded / 2;
+    // partial sums: one slot of 4 doubles per work chunk at the smallest chunk size
+    in->partial_capacity = std::max(1ll, (in->geo.n_active + kMinChunkSegs - 1) / kMinChunkSegs);
     if ((e = cudaMalloc(&in->partials, sizeof(double) * 4 * in->partial_capacity)) != cudaSuccess)
         return cleanup(e, "cudaMalloc(partials)");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cleanup(e, "cudaStreamSynchronize");
@@ -191,6 +193,7 @@ Batch::~Batch()
     cudaFree(d_sums_);
     cudaFree(d_status_);
     cudaFree(d_stage_);
+    cudaFree(d_sched_);
     if (h_sums_) cudaFreeHost(h_sums_);
     if (h_status_) cudaFreeHost(h_status_);
     if (cap_) cudaStreamDestroy(cap_);
@@ -235,7 +238,8 @@ lbm_status Batch::remove(int i)
 
 lbm_status Batch::set_block(int block_cells)
 {
-    if (block_cells < 64 || block_cells > 256 || block_cells % 32) return fail(LBM_ERR_ARG, "bad block size");
+    if (block_cells < 32 * kMinChunkSegs || block_cells > 1024 || block_cells % 32)
+        return fail(LBM_ERR_ARG, "bad work chunk size");
     if (block_cells != block_) {
         block_ = block_cells;
         dirty_ = true;
@@ -258,6 +262,9 @@ static void fill_dev(const Instance &in, InstanceDev &D)
     D.f1 = in.f1;
     D.seg = in.geo.seg;
     D.aseg = in.geo.aseg;
+    D.n_active = (uint32_t)in.geo.n_active;
+    // staged loads need every 32-cell segment inside one row
+    D.staged = (d.nx % 32 == 0) ? 1 : 0;
     D.bmask = in.geo.bmask;
     D.boff = in.geo.boff;
     D.linkc = in.geo.linkc;
@@ -300,18 +307,18 @@ lbm_status Batch::rebuild()
     for (auto &kv : graphs_) cudaGraphExecDestroy(kv.second);
     graphs_.clear();
     const int n = size();
-    const int W = block_ / 32;
+    const int CS = block_ / 32;  // segments per work chunk
     std::vector<InstanceDev> table(std::max(n, 1));
     std::vector<TileDev> tiles;
     std::vector<int> tb(std::max(n, 1)), tc(std::max(n, 1));
     for (int i = 0; i < n; ++i) {
         Instance &in = *inst_[i];
         fill_dev(in, table[i]);
-        const long long nt = in.geo.n_active_padded / W;
+        const long long nt = std::max(1ll, (in.geo.n_active + CS - 1) / CS);
         if (nt > in.partial_capacity) return fail(LBM_ERR_STATE, "partials too small");
         tb[i] = (int)tiles.size();
         tc[i] = (int)nt;
-        for (long long t = 0; t < nt; ++t) tiles.push_back(TileDev{i, (int)t, t * W});
+        for (long long t = 0; t < nt; ++t) tiles.push_back(TileDev{i, (int)t, t * CS});
     }
     if (tiles.size() > (size_t)INT32_MAX) return fail(LBM_ERR_ARG, "too many tiles");
     ntiles_ = (int)tiles.size();
@@ -348,8 +355,28 @@ lbm_status Batch::rebuild()
         CK(cudaMallocHost(&h_sums_, sizeof(double) * 4 * capacity_));
         CK(cudaMallocHost(&h_status_, sizeof(unsigned) * capacity_));
     }
-    // one tile per block: the hardware block scheduler balances the tiles
-    grid_ = std::max(1, ntiles_);
+    // persistent grid: as many step blocks as fit on the device at once
+    if (!d_sched_) {
+        CK(cudaMalloc(&d_sched_, 2 * sizeof(unsigned)));
+        CK(cudaMemset(d_sched_, 0, 2 * sizeof(unsigned)));
+    }
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    smem_ = step_smem_bytes(storage_, kStepBlock / 32);
+    int per_sm = 0;
+    for (int kind = 0; kind < 3; ++kind) {
+        if (layout_ == LBM_LAYOUT_AB && kind != KIND_AB) continue;
+        if (layout_ == LBM_LAYOUT_AA && kind == KIND_AB) continue;
+        const void *fn = ops().step_kernel_ptr(collision_, kind);
+        CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_));
+        int nb = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kStepBlock, smem_));
+        per_sm = per_sm == 0 ? nb : std::min(per_sm, nb);
+    }
+    if (per_sm < 1) return fail(LBM_ERR_CUDA, "step kernel does not fit on a multiprocessor");
+    grid_ = sms * per_sm;
+    aux_grid_ = std::max(1, std::min(sms * 8, (ntiles_ + 7) / 8));
     dirty_ = false;
     return LBM_OK;
 }
@@ -420,7 +447,8 @@ lbm_status Batch::step(long long n)
         lbm_status st = rebuild();
         if (st != LBM_OK) return st;
     }
-    StepQueue q{&ops(), Launch{d_table_, d_tiles_, ntiles_, grid_, block_, stream_}, collision_, layout_, d_status_,
+    StepQueue q{&ops(), Launch{d_table_, d_tiles_, ntiles_, block_ / 32, grid_, kStepBlock, smem_, d_sched_, stream_},
+                collision_, layout_, d_status_,
                 size(), d_tile_begin_, d_tile_count_, d_sums_, size()};
     const long long kChunk = 1000;
     long long left = n;
@@ -493,11 +521,12 @@ lbm_status Batch::moment_sums_now(int i, double *sums)
         int acc = 0;
         for (int j = 0; j < size(); ++j) {
             tb[j] = acc;
-            acc += (int)(inst_[j]->geo.n_active_padded / (block_ / 32));
+            acc += (int)std::max(1ll, (inst_[j]->geo.n_active + block_ / 32 - 1) / (block_ / 32));
         }
     }
-    const int nt = (int)(in.geo.n_active_padded / (block_ / 32));
-    Launch L{d_table_, d_tiles_ + tb[i], nt, std::max(1, nt), block_, stream_};
+    const int nt = (int)std::max(1ll, (in.geo.n_active + block_ / 32 - 1) / (block_ / 32));
+    Launch L{d_table_, d_tiles_ + tb[i], nt, block_ / 32, std::max(1, std::min(aux_grid_, (nt + 7) / 8)), 256, 0,
+             nullptr, stream_};
     CK(ops().moments(L, layout_, cur_of(in), aa_phase_, 1, 0, nullptr));
     CK(launch_final_reduce(d_table_ + i, d_tile_begin_ + i, d_tile_count_ + i, 1, d_sums_ + 4 * i, stream_));
     launches_ += 2;
@@ -573,10 +602,11 @@ lbm_status Batch::get_velocity(int i, double *host)
     int acc = 0;
     for (int j = 0; j < size(); ++j) {
         tb[j] = acc;
-        acc += (int)(inst_[j]->geo.n_active_padded / (block_ / 32));
+        acc += (int)std::max(1ll, (inst_[j]->geo.n_active + block_ / 32 - 1) / (block_ / 32));
     }
-    const int nt = (int)(in.geo.n_active_padded / (block_ / 32));
-    Launch L{d_table_, d_tiles_ + tb[i], nt, std::max(1, nt), block_, stream_};
+    const int nt = (int)std::max(1ll, (in.geo.n_active + block_ / 32 - 1) / (block_ / 32));
+    Launch L{d_table_, d_tiles_ + tb[i], nt, block_ / 32, std::max(1, std::min(aux_grid_, (nt + 7) / 8)), 256, 0,
+             nullptr, stream_};
     for (int c = 0; c < 3; ++c) {
         // all-solid segments are not in the work list: clear the whole field first
         CK(cudaMemsetAsync(d_stage_, 0, sizeof(double) * n, stream_));

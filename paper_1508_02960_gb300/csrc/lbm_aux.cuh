@@ -179,26 +179,30 @@ __global__ void export_kernel(const InstanceDev *__restrict__ table, int inst, i
     }
 }
 
-// Moments of the stored post-collision state of every fluid cell.  mode 0: write the
-// velocity component `comp` to out[cell] of fluid cells (the caller clears out first).  mode 1: tile partial sums
-// (drho, u_x, u_y, u_z) into I.partials, one block per tile of blockDim/32 segments.
+// Moments of the stored post-collision state of every fluid cell, one warp per work
+// chunk.  mode 0: write the velocity component `comp` to out[cell] of fluid cells (the
+// caller clears out first).  mode 1: chunk partial sums (drho, u_x, u_y, u_z) into
+// I.partials, in the same fixed order as the step kernel's.
 template <int STORE>
 __global__ void __launch_bounds__(256) moments_kernel(const InstanceDev *__restrict__ table,
-                                                      const TileDev *__restrict__ tiles, int ntiles,
+                                                      const TileDev *__restrict__ chunks, int nchunks, int chunk_segs,
                                                       int layout, int cur, int aa_phase, int mode, int comp,
                                                       double *__restrict__ out)
 {
     using S = Store<STORE>;
     using T = typename S::T;
-    __shared__ double red[32][4];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const TileDev tile = tiles[t];
-        const InstanceDev &I = table[tile.inst];
-        const uint4 meta = I.aseg[tile.seg0 + warp];
-        const long long cell = (long long)meta.w * 32 + lane;
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    const int nw = (int)((gridDim.x * (long long)blockDim.x) >> 5);
+    for (int c = gw; c < nchunks; c += nw) {
+        const TileDev chunk = chunks[c];
+        const InstanceDev &I = table[chunk.inst];
+        const int n_e = min(chunk_segs, (int)(I.n_active - (uint32_t)chunk.seg0));
         double a[4] = {0.0, 0.0, 0.0, 0.0};
-        if (!((meta.x >> lane) & 1u)) {
+        for (int i = 0; i < n_e; ++i) {
+            const uint4 meta = I.aseg[chunk.seg0 + i];
+            const long long cell = (long long)meta.w * 32 + lane;
+            if ((meta.x >> lane) & 1u) continue;
             CellGeom c;
             cell_geom(I, cell, meta, lane, c);
             double drho = 0.0, j[3] = {0.0, 0.0, 0.0};
@@ -214,24 +218,19 @@ __global__ void __launch_bounds__(256) moments_kernel(const InstanceDev *__restr
                 j[1] += ey(k) * g;
                 j[2] += ez(k) * g;
             }
-            a[0] = drho;
-            for (int d = 0; d < 3; ++d) a[1 + d] = j[d] / I.rho0;
+            if (mode == 0) {
+                out[cell] = j[comp] / I.rho0;
+            } else {
+                a[0] += drho;
+                for (int d = 0; d < 3; ++d) a[1 + d] += j[d] / I.rho0;
+            }
         }
-        if (mode == 0) {
-            if (!((meta.x >> lane) & 1u)) out[cell] = a[1 + comp];
-            continue;
-        }
+        if (mode == 1) {
 #pragma unroll
-        for (int d = 0; d < 4; ++d) a[d] = warp_sum(a[d]);
-        if (lane == 0)
-            for (int d = 0; d < 4; ++d) red[warp][d] = a[d];
-        __syncthreads();
-        if (threadIdx.x < 4) {
-            double s = 0.0;
-            for (int w = 0; w < nwarps; ++w) s += red[w][threadIdx.x];
-            I.partials[(long long)tile.local * 4 + threadIdx.x] = s;
+            for (int d = 0; d < 4; ++d) a[d] = warp_sum(a[d]);
+            if (lane == 0)
+                for (int d = 0; d < 4; ++d) I.partials[(long long)chunk.local * 4 + d] = a[d];
         }
-        __syncthreads();
     }
 }
 

@@ -28,8 +28,21 @@ __host__ __device__ constexpr int ez(int k)
     constexpr int v[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
     return v[k];
 }
-// Opposite direction k-bar (e_kbar = -e_k).
+// Opposite direction k-bar (e_kbar = -e_k); also valid for a run-time k.
 __host__ __device__ constexpr int opp(int k) { return k == 0 ? 0 : ((k & 1) ? k + 1 : k - 1); }
+__host__ __device__ __forceinline__ constexpr int opp_rt(int k) { return opp(k); }
+
+// Velocity components for a run-time k (lane-indexed code): 2 bits per direction.
+__host__ __device__ constexpr unsigned long long pack_component(int a)
+{
+    unsigned long long m = 0ull;
+    for (int k = 0; k < 19; ++k)
+        m |= (unsigned long long)((a == 0 ? ex(k) : a == 1 ? ey(k) : ez(k)) + 1) << (2 * k);
+    return m;
+}
+__device__ __forceinline__ int ex_rt(int k) { return (int)((pack_component(0) >> (2 * k)) & 3ull) - 1; }
+__device__ __forceinline__ int ey_rt(int k) { return (int)((pack_component(1) >> (2 * k)) & 3ull) - 1; }
+__device__ __forceinline__ int ez_rt(int k) { return (int)((pack_component(2) >> (2 * k)) & 3ull) - 1; }
 // Squared speed and lattice weight (c_s^2 = 1/3 isotropic set).
 __host__ __device__ constexpr int speed2(int k) { return ex(k) * ex(k) + ey(k) * ey(k) + ez(k) * ez(k); }
 __host__ __device__ constexpr double weight(int k)
@@ -84,12 +97,14 @@ template <> struct Store<ST_F64> {
     using T = double;
     using R = double;
     __device__ static R load(const T *p, float) { return __ldg(p); }
+    __device__ static R cvt(T v, float) { return v; }
     __device__ static T pack(R v, float) { return v; }
 };
 template <> struct Store<ST_F32> {
     using T = float;
     using R = float;
     __device__ static R load(const T *p, float) { return __ldg(p); }
+    __device__ static R cvt(T v, float) { return v; }
     __device__ static T pack(R v, float) { return v; }
 };
 // FP16 deviation with a power-of-two scale 2^s: stored = g * 2^s (exact scaling).
@@ -97,12 +112,14 @@ template <> struct Store<ST_F16> {
     using T = __half;
     using R = float;
     __device__ static R load(const T *p, float inv_scale) { return __half2float(__ldg(p)) * inv_scale; }
+    __device__ static R cvt(T v, float inv_scale) { return __half2float(v) * inv_scale; }
     __device__ static T pack(R v, float scale) { return __float2half_rn(v * scale); }
 };
 template <> struct Store<ST_BF16> {
     using T = __nv_bfloat16;
     using R = float;
     __device__ static R load(const T *p, float) { return __bfloat162float(__ldg(p)); }
+    __device__ static R cvt(T v, float) { return __bfloat162float(v); }
     __device__ static T pack(R v, float) { return __float2bfloat16_rn(v); }
 };
 
@@ -165,6 +182,8 @@ struct InstanceDev {
     double *partials;        // [n_tiles of this instance][4]
     long long ncells;
     uint32_t n32;            // ncells (19 * ncells < 2^32 is required)
+    uint32_t n_active;       // entries of aseg
+    int staged;              // rows are a multiple of 32 cells: bulk-copy staged loads
     FastDiv div_nx, div_ny;  // division by nx and ny
     int nx, ny, nz;
     int wall;                // 0 = SBB, 1 = CLI
@@ -187,7 +206,7 @@ struct TileDev {
 enum { KIND_AB = 0, KIND_AA_PULL = 1, KIND_AA_LOCAL = 2 };
 enum { COLL_SRT = 0, COLL_TRT = 1, COLL_MRT = 2 };
 
-// Divergence flag bits in the status word.
-enum { STATUS_DIVERGED = 1u };
+// Status word bits: a reduction saw a diverged cell; a bounded wait ran out.
+enum { STATUS_DIVERGED = 1u, STATUS_TIMEOUT = 2u };
 
 }  // namespace lbm

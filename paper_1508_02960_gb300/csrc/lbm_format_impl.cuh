@@ -13,8 +13,8 @@ namespace detail {
 template <int STORE, int COLL, int KIND>
 cudaError_t step_one(const Launch &L, int flip, int reduce, unsigned *status)
 {
-    step_kernel<COLL, STORE, KIND><<<L.grid, L.block, 0, L.stream>>>(L.table, L.tiles, L.ntiles, flip, reduce,
-                                                                     status);
+    step_kernel<COLL, STORE, KIND><<<L.grid, L.block, L.smem, L.stream>>>(L.table, L.tiles, L.ntiles, L.chunk_segs,
+                                                                          flip, reduce, status, L.sched);
     return cudaGetLastError();
 }
 
@@ -86,8 +86,8 @@ cudaError_t export_dir(const InstanceDev *table, int inst, long long n, int layo
 template <int STORE>
 cudaError_t moments(const Launch &L, int layout, int cur, int aa_phase, int mode, int comp, double *out)
 {
-    moments_kernel<STORE><<<L.grid, L.block, 0, L.stream>>>(L.table, L.tiles, L.ntiles, layout, cur, aa_phase,
-                                                            mode, comp, out);
+    moments_kernel<STORE><<<L.grid, L.block, 0, L.stream>>>(L.table, L.tiles, L.ntiles, L.chunk_segs, layout, cur,
+                                                            aa_phase, mode, comp, out);
     return cudaGetLastError();
 }
 

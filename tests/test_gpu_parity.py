@@ -37,7 +37,10 @@ def rel_err(a, b, solid):
     return float(np.max(np.abs(a[:, m] - b[:, m]) / np.abs(b[:, m])))
 
 
-RAGGED = I.Geometry(24, 20, 18, np.array([[11.3, 9.6, 8.7, 6.2]]))   # 8640 cells: partial tiles
+RAGGED = I.Geometry(24, 20, 18, np.array([[11.3, 9.6, 8.7, 6.2]]))   # rows of 24: direct loads
+# rows a multiple of 32 (bulk-copy staged loads), ragged y/z, sphere crossing the periodic faces
+STAGED = I.Geometry(64, 20, 18, np.array([[61.3, 9.6, 8.7, 6.2], [20.0, 3.0, 16.5, 4.1]]))
+GEOMS = {"ragged": RAGGED, "staged": STAGED}
 
 
 # ---------------------------------------------------------------------------------------
@@ -112,12 +115,13 @@ def _perturbed_state(orc, solid, amp, seed):
     return f
 
 
+@pytest.mark.parametrize("geom", ["ragged", "staged"])
 @pytest.mark.parametrize("layout", ["AB", "AA"])
 @pytest.mark.parametrize("storage", ["F64", "F32"])
 @pytest.mark.parametrize("coll", ["SRT", "TRT", "MRT"])
 @pytest.mark.parametrize("wall", ["SBB", "CLI"])
-def test_step_parity_matrix(capi, orc, layout, storage, coll, wall):
-    g = RAGGED
+def test_step_parity_matrix(capi, orc, geom, layout, storage, coll, wall):
+    g = GEOMS[geom]
     solid = orc.voxelize(g.shape, g.spheres)
     q = orc.wall_distances(solid, g.spheres)
     f0 = _perturbed_state(orc, solid, 1e-3, 11)
@@ -137,10 +141,11 @@ def test_step_parity_matrix(capi, orc, layout, storage, coll, wall):
     assert obs["U_sup"] == pytest.approx(sums[1] / g.n_cells, rel=1e-9 if storage == "F64" else 1e-3, abs=0)
 
 
+@pytest.mark.parametrize("geom", ["ragged", "staged"])
 @pytest.mark.parametrize("storage", ["F64", "F32"])
 @pytest.mark.parametrize("wall", ["SBB", "CLI"])
-def test_aa_matches_ab_bitwise(capi, orc, storage, wall):
-    g = RAGGED
+def test_aa_matches_ab_bitwise(capi, orc, geom, storage, wall):
+    g = GEOMS[geom]
     solid = orc.voxelize(g.shape, g.spheres)
     f0 = _perturbed_state(orc, solid, 1e-3, 5)
     kw = dict(spheres=g.spheres, shape=g.shape, tau=0.7, delta_rho=2e-4, collision=capi.TRT,
@@ -179,11 +184,12 @@ def _ulp_f16(x):
     return 2.0 ** (e - 10)
 
 
+@pytest.mark.parametrize("geom", ["ragged", "staged"])
 @pytest.mark.parametrize("fmt", ["F16DEV", "BF16DEV"])
 @pytest.mark.parametrize("coll", ["TRT", "MRT"])
 @pytest.mark.parametrize("wall", ["SBB", "CLI"])
-def test_half_storage_one_step(capi, orc, fmt, coll, wall):
-    g = RAGGED
+def test_half_storage_one_step(capi, orc, geom, fmt, coll, wall):
+    g = GEOMS[geom]
     solid = orc.voxelize(g.shape, g.spheres)
     q = orc.wall_distances(solid, g.spheres)
     _, w, _ = orc.lattice()
@@ -249,8 +255,9 @@ def test_mass_conservation_sbb(capi, orc):
     assert o["U_sup"] > 0
 
 
-def test_checkpoint_restart_bitwise(capi, orc, tmp_path):
-    g = RAGGED
+@pytest.mark.parametrize("geom", ["ragged", "staged"])
+def test_checkpoint_restart_bitwise(capi, orc, tmp_path, geom):
+    g = GEOMS[geom]
     kw = dict(spheres=g.spheres, shape=g.shape, tau=0.7, delta_rho=1e-4, collision=capi.TRT,
               wall=capi.CLI, storage=capi.F32)
     for lay in (capi.LAYOUT_AB, capi.LAYOUT_AA):
@@ -279,7 +286,7 @@ def test_divergence_is_reported(capi):
 
 
 def test_batch_alone_vs_mix_bitwise(capi):
-    geoms = [I.centred_sphere(24, 8.0), RAGGED, I.centred_sphere(40, 15.0)]
+    geoms = [I.centred_sphere(24, 8.0), RAGGED, I.centred_sphere(40, 15.0), STAGED, I.centred_sphere(64, 20.0)]
     descs_keep = [capi.make_desc(spheres=gg.spheres, shape=gg.shape, tau=0.6 + 0.05 * i, delta_rho=1e-4 * (i + 1),
                                  collision=capi.TRT, wall=capi.CLI, storage=capi.F16DEV)
                   for i, gg in enumerate(geoms)]
@@ -287,7 +294,7 @@ def test_batch_alone_vs_mix_bitwise(capi):
     b = capi.Batch(descs)
     b.init_equilibrium()
     b.step(60)
-    mix = [(b.get_populations(i), b.observables(i)) for i in range(3)]
+    mix = [(b.get_populations(i), b.observables(i)) for i in range(len(geoms))]
     b.close()
     for i, d in enumerate(descs):
         with capi.Context(desc=d) as ctx:

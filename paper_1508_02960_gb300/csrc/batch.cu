@@ -141,7 +141,8 @@ lbm_status Batch::make_instance(const lbm_desc &d0, cudaStream_t s, std::unique_
 
     const long long n = in->geo.ncells;
     const size_t es = storage_bytes(d.storage);
-    const size_t pop = (size_t)Q * n * es;
+    // 16 bytes of slack: 16-bit formats copy the aligned 32-bit word holding a population
+    const size_t pop = (size_t)Q * n * es + 16;
     auto cleanup = [&](cudaError_t ce, const char *what) {
         cudaFree(in->f0);
         cudaFree(in->f1);
@@ -263,8 +264,6 @@ static void fill_dev(const Instance &in, InstanceDev &D)
     D.seg = in.geo.seg;
     D.aseg = in.geo.aseg;
     D.n_active = (uint32_t)in.geo.n_active;
-    // staged loads need every 32-cell segment inside one row
-    D.staged = (d.nx % 32 == 0) ? 1 : 0;
     D.bmask = in.geo.bmask;
     D.boff = in.geo.boff;
     D.linkc = in.geo.linkc;

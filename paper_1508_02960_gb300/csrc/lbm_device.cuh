@@ -183,7 +183,6 @@ struct InstanceDev {
     long long ncells;
     uint32_t n32;            // ncells (19 * ncells < 2^32 is required)
     uint32_t n_active;       // entries of aseg
-    int staged;              // rows are a multiple of 32 cells: bulk-copy staged loads
     FastDiv div_nx, div_ny;  // division by nx and ny
     int nx, ny, nz;
     int wall;                // 0 = SBB, 1 = CLI

@@ -16,13 +16,11 @@
 //   collide   SRT, TRT or MRT relaxation towards Eq. equilibrium;
 //   store     A-B: to the other buffer; AA: in place (see below).
 //
-// Staged loads.  When rows are a multiple of 32 cells, every segment lies in one row, and
-// the 32 pull sources of direction k are one contiguous run of the source row (shifted
-// by one cell when e_kx != 0).  Lanes 0..18 then each issue one bulk asynchronous copy
-// (cp.async.bulk, completion counted on an mbarrier) of their direction's run into a
-// shared-memory ring of kStages segments, so the next segments' populations are in flight
-// while the current one is collided, without holding registers.  Only the first and last
-// cell of a row read their x-wrapped source directly.  Other boxes use direct loads.
+// Staged loads.  Each lane copies its cell's 19 pull sources with per-thread asynchronous
+// copies (cp.async) into its own slots of a per-warp shared-memory ring of kStages
+// segments, kStages - 1 segments ahead of the one being collided.  Populations in flight
+// therefore hold no registers, and no lane reads another lane's slots.  16-bit formats
+// copy the aligned 32-bit word holding the population and keep which half it is.
 //
 // AA layout (in-place, one buffer).  PULL steps read g~_k(x - e_k) from slot kbar of
 // x - e_k and push g~_k(x) into slot k of x + e_k; LOCAL steps read slot k and write
@@ -36,8 +34,7 @@
 
 namespace lbm {
 
-constexpr int kStages = 2;                       // segments in flight per warp
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // bounded mbarrier wait: 2 s
+constexpr int kStages = 3;  // segments per warp: kStages - 1 in flight while one is collided
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -46,71 +43,109 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// Shared-memory window layout of one segment: 19 direction slots of W elements; the 32
-// cells of the segment sit at [H, H + 32), H elements (16 bytes) of halo on each side.
-template <int STORE> struct Window {
+// One stage of a warp's ring: [19][32] copied words (8 bytes for FP64, else 4), then for
+// 16-bit formats one 19-bit mask per lane telling which half of each word is wanted.
+template <int STORE> struct Stage {
     using T = typename Store<STORE>::T;
-    static constexpr int H = 16 / (int)sizeof(T);
-    static constexpr int W = 32 + 2 * H;
-    static constexpr int stage_bytes = Q * W * (int)sizeof(T);
-    // bytes copied per segment: e_kx == 0 -> 32 cells, else 32 + 2H cells
-    static constexpr int bytes_pull = (9 * 32 + 10 * W) * (int)sizeof(T);
-    static constexpr int bytes_local = Q * 32 * (int)sizeof(T);
+    static constexpr int word = sizeof(T) == 8 ? 8 : 4;
+    static constexpr bool halves = sizeof(T) == 2;
+    static constexpr int bytes = Q * 32 * word + (halves ? 32 * 4 : 0);
 };
 
 inline size_t step_smem_bytes(int storage, int warps)
 {
-    const int stage = storage == ST_F64 ? Window<ST_F64>::stage_bytes
-                      : storage == ST_F32 ? Window<ST_F32>::stage_bytes
-                                          : Window<ST_F16>::stage_bytes;
-    return (size_t)warps * (kStages * stage + kStages * 8);
+    const int stage = storage == ST_F64 ? Stage<ST_F64>::bytes
+                      : storage == ST_F32 ? Stage<ST_F32>::bytes
+                                          : Stage<ST_F16>::bytes;
+    return (size_t)warps * kStages * stage;
 }
 
-// ---- inline PTX: mbarrier and bulk copies --------------------------------------------
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+template <int BYTES>
+__device__ __forceinline__ void cp_async(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+// Cell coordinates and the periodic x-1/x/x+1 offsets, row offsets y-1/y/y+1 and plane
+// offsets z-1/z/z+1 (32-bit element counts).
+struct Coord {
+    uint32_t x, y, z;
+    uint32_t X[3], Y[3], Z[3];
+    __device__ __forceinline__ uint32_t pull(int k) const { return X[1 - ex(k)] + Y[1 - ey(k)] + Z[1 - ez(k)]; }
+};
+__device__ __forceinline__ Coord coord_of(const InstanceDev &I, uint32_t cell)
 {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+    Coord c;
+    const uint32_t nx = I.nx, ny = I.ny, nz = I.nz, nxy = nx * ny;
+    const uint32_t yz = fast_div(cell, I.div_nx);
+    c.x = cell - yz * nx;
+    c.z = fast_div(yz, I.div_ny);
+    c.y = yz - c.z * ny;
+    c.X[0] = c.x == 0 ? nx - 1 : c.x - 1;
+    c.X[1] = c.x;
+    c.X[2] = c.x == nx - 1 ? 0 : c.x + 1;
+    c.Y[0] = (c.y == 0 ? ny - 1 : c.y - 1) * nx;
+    c.Y[1] = c.y * nx;
+    c.Y[2] = (c.y == ny - 1 ? 0 : c.y + 1) * nx;
+    c.Z[0] = (c.z == 0 ? nz - 1 : c.z - 1) * nxy;
+    c.Z[1] = c.z * nxy;
+    c.Z[2] = (c.z == nz - 1 ? 0 : c.z + 1) * nxy;
+    return c;
 }
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+
+// Element index of the population a cell pulls for direction k: A-B array k at x - e_k;
+// AA pull array kbar at x - e_k; AA local array k at x.
+template <int KIND>
+__device__ __forceinline__ uint32_t pull_index(uint32_t N, uint32_t cell, const Coord &c, int k)
 {
-    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
+    if constexpr (KIND == KIND_AA_LOCAL) return (uint32_t)k * N + cell;
+    else if constexpr (KIND == KIND_AA_PULL) return (uint32_t)opp(k) * N + c.pull(k);
+    else return (uint32_t)k * N + c.pull(k);
 }
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+
+// Queue the asynchronous copies of one lane's 19 pull sources into a stage.
+template <int STORE, int KIND>
+__device__ __forceinline__ void issue_cell(const InstanceDev &I, const typename Store<STORE>::T *fs, uint4 meta,
+                                           int lane, unsigned char *stage)
 {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
+    using St = Stage<STORE>;
+    if ((meta.x >> lane) & 1u) return;
+    const uint32_t cell = meta.w * 32u + lane;
+    const Coord c = coord_of(I, cell);
+    const uint32_t base = smem_addr(stage) + (uint32_t)lane * St::word;
+    uint32_t hmask = 0u;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        const uint32_t idx = pull_index<KIND>(I.n32, cell, c, k);
+        if constexpr (St::halves) {
+            hmask |= (idx & 1u) << k;
+            cp_async<4>(base + (uint32_t)(k * 32 * 4), fs + (idx & ~1u));
+        } else {
+            cp_async<St::word>(base + (uint32_t)(k * 32 * St::word), fs + idx);
+        }
+    }
+    if constexpr (St::halves) reinterpret_cast<uint32_t *>(stage + Q * 32 * 4)[lane] = hmask;
 }
-__device__ __forceinline__ unsigned long long global_ns()
+
+// Read back population k of a lane from a stage.
+template <int STORE>
+__device__ __forceinline__ typename Store<STORE>::R staged_value(const unsigned char *stage, int k, int lane,
+                                                                   uint32_t hmask, float isc)
 {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// Wait for the phase of the given parity, at most kWaitLimitNs; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > kWaitLimitNs) return false;
-    return true;
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
+    using S = Store<STORE>;
+    using T = typename S::T;
+    if constexpr (Stage<STORE>::halves) {
+        const uint32_t w = reinterpret_cast<const uint32_t *>(stage)[k * 32 + lane];
+        const unsigned short h = (unsigned short)(((hmask >> k) & 1u) ? (w >> 16) : (w & 0xFFFFu));
+        T v;
+        memcpy(&v, &h, 2);
+        return S::cvt(v, isc);
+    } else {
+        return S::cvt(reinterpret_cast<const T *>(stage)[k * 32 + lane], isc);
+    }
 }
 
 // Collision of one cell, in place on g[] (deviations).  rho0 enters the equilibrium.
@@ -176,43 +211,6 @@ __device__ __forceinline__ void collide(R (&g)[Q], const InstanceDev &I, R drho,
     }
 }
 
-// Issue the bulk copies of one segment's pull windows into a stage (whole warp calls).
-// Lane k < 19 copies direction k: the 32 sources of the segment's cells (A-B: array k at
-// x - e_k; AA pull: array kbar at x - e_k; AA local: array k at x), widened by H cells on
-// each side when e_kx != 0 so that every copy starts and ends on a 16-byte boundary.
-template <int STORE, int KIND>
-__device__ __forceinline__ void issue_segment(const InstanceDev &I, const typename Store<STORE>::T *fs, uint32_t seg,
-                                              uint32_t stage_smem, uint32_t bar, int lane)
-{
-    using T = typename Store<STORE>::T;
-    using Wn = Window<STORE>;
-    const uint32_t cell0 = seg * 32u;
-    const uint32_t row = fast_div(cell0, I.div_nx);
-    const uint32_t x0 = cell0 - row * (uint32_t)I.nx;
-    const uint32_t z = fast_div(row, I.div_ny);
-    const uint32_t y = row - z * (uint32_t)I.ny;
-    if (lane == 0) mbar_arrive_expect_tx(bar, KIND == KIND_AA_LOCAL ? Wn::bytes_local : Wn::bytes_pull);
-    __syncwarp();
-    if (lane < Q) {
-        const int k = lane;
-        uint32_t src_row = row;
-        int arr = k, shift = 0;
-        if (KIND != KIND_AA_LOCAL) {
-            const int ky = ey_rt(k), kz = ez_rt(k);
-            const uint32_t ny = I.ny, nz = I.nz;
-            const uint32_t ys = ky == 1 ? (y == 0 ? ny - 1 : y - 1) : (ky == -1 ? (y == ny - 1 ? 0 : y + 1) : y);
-            const uint32_t zs = kz == 1 ? (z == 0 ? nz - 1 : z - 1) : (kz == -1 ? (z == nz - 1 ? 0 : z + 1) : z);
-            src_row = ys + ny * zs;
-            if (KIND == KIND_AA_PULL) arr = opp_rt(k);
-            shift = ex_rt(k) != 0;
-        }
-        const uint32_t start = (uint32_t)arr * I.n32 + src_row * (uint32_t)I.nx + x0 - (shift ? Wn::H : 0);
-        const uint32_t n = shift ? Wn::W : 32;
-        const uint32_t dst = stage_smem + (uint32_t)(k * Wn::W + (shift ? 0 : Wn::H)) * (uint32_t)sizeof(T);
-        bulk_g2s(dst, fs + start, n * (uint32_t)sizeof(T), bar);
-    }
-}
-
 // The fused step.  flip selects the A-B buffer pair (src = f[phase ^ flip]); reduce != 0
 // makes every chunk write its FP64 partial sums (drho, u_x, u_y, u_z) and flags diverged
 // cells in status[instance].  sched[0] is the chunk counter, sched[1] counts finished
@@ -226,21 +224,13 @@ __global__ void __launch_bounds__(256) step_kernel(const InstanceDev *__restrict
     using S = Store<STORE>;
     using T = typename S::T;
     using R = typename S::R;
-    using Wn = Window<STORE>;
+    using St = Stage<STORE>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
 
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    unsigned char *wbase = smem_raw + (size_t)warp * kStages * Wn::stage_bytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)nwarps * kStages * Wn::stage_bytes) +
-                     warp * kStages;
-    if (lane == 0)
-        for (int s = 0; s < kStages; ++s) mbar_init(smem_addr(&bars[s]), 1);
-    mbar_fence_init();
-    __syncwarp();
-    uint32_t parity = 0;  // bit s: parity of the phase awaited next on stage s
-    bool failed = false;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned char *ring = smem_raw + (size_t)warp * kStages * St::bytes;
 
-    while (!failed) {
+    while (true) {
         int c = 0;
         if (lane == 0) c = (int)atomicAdd(&sched[0], 1u);
         c = __shfl_sync(0xffffffffu, c, 0);
@@ -251,7 +241,7 @@ __global__ void __launch_bounds__(256) step_kernel(const InstanceDev *__restrict
         const int n_e = min(chunk_segs, (int)(I.n_active - e0));
         const uint4 meta_l = lane < n_e ? I.aseg[e0 + lane] : make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
         const uint32_t N = I.n32;
-        const uint32_t nx = I.nx, ny = I.ny, nz = I.nz;
+        const uint32_t nx = I.nx;
         const float sc = I.scale, isc = I.inv_scale;
         T *fs;  // state read this step
         T *fd;  // state written this step
@@ -262,47 +252,38 @@ __global__ void __launch_bounds__(256) step_kernel(const InstanceDev *__restrict
         } else {
             fs = fd = reinterpret_cast<T *>(I.f0);
         }
-        const bool staged = I.staged != 0;
         const R dshift = R(I.delta_rho);
         double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
 
-        if (staged)
-            for (int i = 0; i < kStages && i < n_e; ++i) {
-                const uint32_t seg_i = __shfl_sync(0xffffffffu, meta_l.w, i);
-                issue_segment<STORE, KIND>(I, fs, seg_i, smem_addr(wbase + i * Wn::stage_bytes),
-                                           smem_addr(&bars[i]), lane);
-            }
+        auto meta_at = [&](int i) {
+            uint4 m;
+            m.x = __shfl_sync(0xffffffffu, meta_l.x, i);
+            m.y = __shfl_sync(0xffffffffu, meta_l.y, i);
+            m.z = __shfl_sync(0xffffffffu, meta_l.z, i);
+            m.w = __shfl_sync(0xffffffffu, meta_l.w, i);
+            return m;
+        };
+        // prologue: kStages - 1 segments in flight
+#pragma unroll
+        for (int i = 0; i < kStages - 1; ++i) {
+            if (i < n_e) issue_cell<STORE, KIND>(I, fs, meta_at(i), lane, ring + i * St::bytes);
+            cp_commit();
+        }
 
         for (int i = 0; i < n_e; ++i) {
-            const int st = i % kStages;
-            uint4 meta;
-            meta.x = __shfl_sync(0xffffffffu, meta_l.x, i);
-            meta.y = __shfl_sync(0xffffffffu, meta_l.y, i);
-            meta.z = __shfl_sync(0xffffffffu, meta_l.z, i);
-            meta.w = __shfl_sync(0xffffffffu, meta_l.w, i);
-            const T *win = reinterpret_cast<const T *>(wbase + st * Wn::stage_bytes);
-            if (staged) {
-                const bool ok = mbar_wait(smem_addr(&bars[st]), (parity >> st) & 1u);
-                if (!__all_sync(0xffffffffu, ok)) {
-                    if (lane == 0) atomicOr(status + chunk.inst, STATUS_TIMEOUT);
-                    failed = true;
-                    break;
-                }
-                parity ^= 1u << st;
-            }
+            const int j = i + kStages - 1;
+            if (j < n_e) issue_cell<STORE, KIND>(I, fs, meta_at(j), lane, ring + (j % kStages) * St::bytes);
+            cp_commit();
+            cp_wait<kStages - 1>();  // this lane's copies of segment i have landed
+            const uint4 meta = meta_at(i);
+            const unsigned char *stage = ring + (i % kStages) * St::bytes;
 
             if (!((meta.x >> lane) & 1u)) {
                 const uint32_t cell = meta.w * 32u + lane;
-                const uint32_t yz = fast_div(cell, I.div_nx);
-                const uint32_t x = cell - yz * nx;
-                const uint32_t z = fast_div(yz, I.div_ny);
-                const uint32_t y = yz - z * ny;
-                const uint32_t nxy = nx * ny;
-                const uint32_t X[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
-                const uint32_t Y[3] = {(y == 0 ? ny - 1 : y - 1) * nx, y * nx, (y == ny - 1 ? 0 : y + 1) * nx};
-                const uint32_t Z[3] = {(z == 0 ? nz - 1 : z - 1) * nxy, z * nxy, (z == nz - 1 ? 0 : z + 1) * nxy};
-                // pull source of direction k: x - e_k
-                auto src_of = [&](int k) -> uint32_t { return X[1 - ex(k)] + Y[1 - ey(k)] + Z[1 - ez(k)]; };
+                const Coord co = coord_of(I, cell);
+                const uint32_t x = co.x;
+                uint32_t hmask = 0u;
+                if constexpr (St::halves) hmask = reinterpret_cast<const uint32_t *>(stage + Q * 32 * 4)[lane];
 
                 uint32_t wm = 0u, off = 0u;
                 if ((meta.y >> lane) & 1u) {
@@ -318,20 +299,7 @@ __global__ void __launch_bounds__(256) step_kernel(const InstanceDev *__restrict
                         g[k] = R(0);
                         continue;
                     }
-                    const int arr = KIND == KIND_AA_PULL ? opp(k) : k;
-                    R v;
-                    if (staged) {
-                        if (KIND == KIND_AA_LOCAL) {
-                            v = S::cvt(win[k * Wn::W + Wn::H + lane], isc);
-                        } else if ((ex(k) == 1 && x == 0) || (ex(k) == -1 && x == nx - 1)) {
-                            v = S::load(fs + ((uint32_t)arr * N + src_of(k)), isc);  // x-wrapped source
-                        } else {
-                            v = S::cvt(win[k * Wn::W + Wn::H + lane - ex(k)], isc);
-                        }
-                    } else {
-                        if constexpr (KIND == KIND_AA_LOCAL) v = S::load(fs + ((uint32_t)k * N + cell), isc);
-                        else v = S::load(fs + ((uint32_t)arr * N + src_of(k)), isc);
-                    }
+                    R v = staged_value<STORE>(stage, k, lane, hmask, isc);
                     if (ex(k) == 1 && x == 0) v += R(weight(k)) * dshift;
                     if (ex(k) == -1 && x == nx - 1) v -= R(weight(k)) * dshift;
                     g[k] = v;
@@ -350,12 +318,12 @@ __global__ void __launch_bounds__(256) step_kernel(const InstanceDev *__restrict
                         R v = C;
                         if (I.wall == 1) {
                             const uint32_t l = off + __popc(wm & ((1u << k) - 1u));
-                            const R c = linkc[l];
-                            if (c != R(0)) {
+                            const R cq = linkc[l];
+                            if (cq != R(0)) {
                                 R B;  // own post-collision g~_k(x)
                                 if constexpr (KIND == KIND_AB) B = S::load(fs + ((uint32_t)k * N + cell), isc);
                                 else B = S::load(linkB + l, isc);
-                                v = c * (g[kb] - B) + C;
+                                v = cq * (g[kb] - B) + C;
                             }
                         }
                         g[k] = v;
@@ -393,7 +361,7 @@ __global__ void __launch_bounds__(256) step_kernel(const InstanceDev *__restrict
                     } else {
                         // push to x + e_k = pull source of kbar, or bounce into the own slot
                         if ((wm >> opp(k)) & 1u) fd[(uint32_t)opp(k) * N + cell] = v;
-                        else fd[(uint32_t)k * N + src_of(opp(k))] = v;
+                        else fd[(uint32_t)k * N + co.pull(opp(k))] = v;
                     }
                 }
                 if constexpr (KIND != KIND_AB) {
@@ -407,18 +375,6 @@ __global__ void __launch_bounds__(256) step_kernel(const InstanceDev *__restrict
                     }
                 }
             }
-            // the stage is free once every lane has read it: refill it with segment i + kStages
-            __syncwarp();
-            if (staged && i + kStages < n_e) {
-                const uint32_t seg_n = __shfl_sync(0xffffffffu, meta_l.w, i + kStages);
-                issue_segment<STORE, KIND>(I, fs, seg_n, smem_addr(wbase + st * Wn::stage_bytes),
-                                           smem_addr(&bars[st]), lane);
-            }
-        }
-        if (failed) {
-            // let copies still in flight land before the block leaves (bounded again)
-            for (int s = 0; s < kStages; ++s) mbar_wait(smem_addr(&bars[s]), (parity >> s) & 1u);
-            break;
         }
         if (reduce) {  // deterministic: per-lane sums over the chunk, then a fixed shuffle tree
             a0 = warp_sum(a0);
@@ -434,6 +390,7 @@ __global__ void __launch_bounds__(256) step_kernel(const InstanceDev *__restrict
             }
         }
     }
+    cp_wait<0>();
 
     // the last block to finish resets the work counter for the next launch
     __syncthreads();

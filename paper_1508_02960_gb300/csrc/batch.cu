@@ -55,8 +55,9 @@ lbm_status validate_desc(const lbm_desc &d)
 {
     if (d.nx < 1 || d.ny < 1 || d.nz < 1) return fail(LBM_ERR_ARG, "nx, ny, nz must be >= 1");
     const long long n = (long long)d.nx * d.ny * d.nz;
-    // the kernels address populations with 32-bit element offsets: 19 n < 2^32
-    if (19 * n >= (1ll << 32)) return fail(LBM_ERR_ARG, "box too large: 19 * nx * ny * nz must be < 2^32");
+    // the kernels address populations with 32-bit element offsets: 19 * stride < 2^32
+    if (19 * direction_stride(n) >= (1ll << 32))
+        return fail(LBM_ERR_ARG, "box too large: 19 * nx * ny * nz must be below 2^32");
     if (!(d.tau > 0.5) || !std::isfinite(d.tau)) return fail(LBM_ERR_ARG, "tau must be a finite value > 1/2");
     if (!std::isfinite(d.delta_rho)) return fail(LBM_ERR_ARG, "delta_rho must be finite");
     if (d.rho0 < 0 || !std::isfinite(d.rho0)) return fail(LBM_ERR_ARG, "rho0 must be >= 0 (0 = 1)");
@@ -83,6 +84,14 @@ lbm_status validate_desc(const lbm_desc &d)
     return LBM_OK;
 }
 
+// Elements between consecutive direction arrays: the cell count rounded up to 64 elements
+// plus kDirPad, so that the 19 read and 19 write streams of a step do not all start at
+// the same power-of-two offset.
+long long direction_stride(long long ncells)
+{
+    return (ncells + 63) / 64 * 64 + kDirPad;
+}
+
 static int auto_dev_scale(const lbm_desc &d)
 {
     if (d.storage != LBM_F16DEV) return 0;
@@ -99,7 +108,8 @@ size_t Batch::footprint(const lbm_desc &d)
     const size_t es = storage_bytes(d.storage);
     const size_t bufs = d.layout == LBM_LAYOUT_AA ? 1 : 2;
     // populations + solid flags + segment table + partials + a boundary-table allowance
-    return bufs * Q * n * es + n + (n / 32 + 64) * (16 + 16) + n / 8 + (1u << 20);
+    return bufs * Q * (size_t)direction_stride((long long)n) * es + n + (n / 32 + 64) * (16 + 16) + n / 8 +
+           (1u << 20);
 }
 
 lbm_status Batch::make_instance(const lbm_desc &d0, cudaStream_t s, std::unique_ptr<Instance> *out)
@@ -142,7 +152,8 @@ lbm_status Batch::make_instance(const lbm_desc &d0, cudaStream_t s, std::unique_
     const long long n = in->geo.ncells;
     const size_t es = storage_bytes(d.storage);
     // 16 bytes of slack: 16-bit formats copy the aligned 32-bit word holding a population
-    const size_t pop = (size_t)Q * n * es + 16;
+    in->ks = direction_stride(n);
+    const size_t pop = (size_t)Q * in->ks * es + 16;
     auto cleanup = [&](cudaError_t ce, const char *what) {
         cudaFree(in->f0);
         cudaFree(in->f1);
@@ -271,6 +282,7 @@ static void fill_dev(const Instance &in, InstanceDev &D)
     D.partials = in.partials;
     D.ncells = in.geo.ncells;
     D.n32 = (uint32_t)in.geo.ncells;
+    D.ks = (uint32_t)in.ks;
     D.div_nx = make_fastdiv((uint32_t)d.nx);
     D.div_ny = make_fastdiv((uint32_t)d.ny);
     D.nx = d.nx;
@@ -677,7 +689,7 @@ void Batch::fill_info(int i, lbm_info *out) const
 struct CkptHeader {
     char magic[8];
     int32_t version, nx, ny, nz, storage, layout, collision, wall, aa_phase, dev_scale_log2;
-    int64_t steps, n_links, elem_bytes;
+    int64_t steps, n_links, elem_bytes, stride;
 };
 
 lbm_status Batch::save(int i, const char *path)
@@ -686,7 +698,7 @@ lbm_status Batch::save(int i, const char *path)
     Instance &in = *inst_[i];
     CK(cudaStreamSynchronize(stream_));
     const size_t es = storage_bytes(storage_);
-    const size_t pop = (size_t)Q * in.geo.ncells * es;
+    const size_t pop = (size_t)Q * in.ks * es;
     std::vector<char> buf(pop);
     const void *src = (layout_ == LBM_LAYOUT_AB) ? (cur_of(in) ? in.f1 : in.f0) : in.f0;
     CK(cudaMemcpy(buf.data(), src, pop, cudaMemcpyDeviceToHost));
@@ -711,6 +723,7 @@ lbm_status Batch::save(int i, const char *path)
     h.steps = in.steps;
     h.n_links = in.linkB ? in.geo.n_links : 0;
     h.elem_bytes = (int64_t)es;
+    h.stride = in.ks;
     FILE *f = std::fopen(path, "wb");
     if (!f) return fail(LBM_ERR_IO, std::string("cannot open ") + path);
     bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 && std::fwrite(buf.data(), 1, buf.size(), f) == buf.size() &&
@@ -738,11 +751,12 @@ lbm_status Batch::load(int i, const char *path)
     const size_t es = storage_bytes(storage_);
     if (h.nx != in.desc.nx || h.ny != in.desc.ny || h.nz != in.desc.nz || h.storage != storage_ ||
         h.layout != layout_ || h.collision != collision_ || h.wall != in.desc.wall || h.elem_bytes != (int64_t)es ||
-        h.dev_scale_log2 != in.dev_scale_log2 || h.n_links != (in.linkB ? in.geo.n_links : 0)) {
+        h.dev_scale_log2 != in.dev_scale_log2 || h.n_links != (in.linkB ? in.geo.n_links : 0) ||
+        h.stride != in.ks) {
         std::fclose(f);
         return fail(LBM_ERR_ARG, "checkpoint does not match this context's descriptor");
     }
-    const size_t pop = (size_t)Q * in.geo.ncells * es;
+    const size_t pop = (size_t)Q * in.ks * es;
     std::vector<char> buf(pop), lb(h.n_links * es);
     bool ok = std::fread(buf.data(), 1, pop, f) == pop && (lb.empty() || std::fread(lb.data(), 1, lb.size(), f) == lb.size());
     std::fclose(f);

@@ -31,6 +31,7 @@ struct Instance {
     bool have_sums = false;
     bool sums_pending = false;       // the last queued step reduced the moments
     size_t bytes_pop = 0;
+    long long ks = 0;                // elements between direction arrays
 };
 
 class Batch {

@@ -18,7 +18,7 @@ __device__ __forceinline__ long long canonical_index(const InstanceDev &I, int l
                                                      const long long (&X)[3], const long long (&Y)[3],
                                                      const long long (&Z)[3], int &buf)
 {
-    const long long N = I.ncells;
+    const long long N = I.ks;
     if (layout == 0) {
         buf = cur;
         return (long long)k * N + cell;
@@ -96,7 +96,7 @@ __global__ void init_kernel(const InstanceDev *__restrict__ table, int inst, int
         T *f = reinterpret_cast<T *>(layout == 0 ? (cur ? I.f1 : I.f0) : I.f0);
         if ((meta.x >> lane) & 1u) {
 #pragma unroll
-            for (int k = 0; k < Q; ++k) f[(long long)k * N + cell] = S::pack(0.0f, I.scale);
+            for (int k = 0; k < Q; ++k) f[(long long)k * I.ks + cell] = S::pack(0.0f, I.scale);
             continue;
         }
         double u[3] = {0.0, 0.0, 0.0};
@@ -115,7 +115,7 @@ __global__ void init_kernel(const InstanceDev *__restrict__ table, int inst, int
             const double eu = ex(k) * u[0] + ey(k) * u[1] + ez(k) * u[2];
             const double g = weight(k) * I.rho0 * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
             const T v = S::pack((typename S::R)g, I.scale);
-            f[(long long)(layout == 0 ? k : opp(k)) * N + cell] = v;
+            f[(long long)(layout == 0 ? k : opp(k)) * I.ks + cell] = v;
             if (layout == 1 && linkB && ((wm >> k) & 1u)) linkB[off + __popc(wm & ((1u << k) - 1u))] = v;
         }
     }
@@ -136,7 +136,7 @@ __global__ void import_kernel(const InstanceDev *__restrict__ table, int inst, i
          cell += (long long)gridDim.x * blockDim.x) {
         const uint4 meta = I.seg[cell >> 5];
         T *f = reinterpret_cast<T *>(layout == 0 ? (cur ? I.f1 : I.f0) : I.f0);
-        const long long slot = (long long)(layout == 0 ? k : opp(k)) * N + cell;
+        const long long slot = (long long)(layout == 0 ? k : opp(k)) * I.ks + cell;
         if ((meta.x >> lane) & 1u) {
             f[slot] = S::pack(0.0f, I.scale);
             continue;

@@ -172,7 +172,7 @@ __host__ __device__ __forceinline__ uint32_t fast_div(uint32_t n, const FastDiv 
 // the cell's own post-collision population of the link (AA layout only).
 // ------------------------------------------------------------------------------------
 struct InstanceDev {
-    void *f0, *f1;           // populations [19][ncells]; AA uses f0 only
+    void *f0, *f1;           // populations [19][ks] (direction k at k * ks); AA uses f0 only
     const uint4 *seg;        // [nseg]
     const uint4 *aseg;       // [n_active_padded]: seg entries of segments holding fluid, .w = segment
     const uint32_t *bmask;   // [n_boundary]
@@ -181,7 +181,8 @@ struct InstanceDev {
     void *linkB;             // [n_links], type T (AA layout)
     double *partials;        // [n_tiles of this instance][4]
     long long ncells;
-    uint32_t n32;            // ncells (19 * ncells < 2^32 is required)
+    uint32_t n32;            // ncells
+    uint32_t ks;             // elements between consecutive direction arrays (>= ncells; 19 ks < 2^32)
     uint32_t n_active;       // entries of aseg
     FastDiv div_nx, div_ny;  // division by nx and ny
     int nx, ny, nz;

@@ -81,5 +81,7 @@ void set_error(const std::string &msg);
 constexpr int kMaxWarpsPerBlock = 32;
 constexpr int kStepBlock = 256;        // threads of a step-kernel block (8 warps)
 constexpr int kMinChunkSegs = 4;       // smallest work chunk (segments)
+constexpr long long kDirPad = 0;       // extra elements between direction arrays
+long long direction_stride(long long ncells);
 
 }  // namespace lbm

@@ -3,7 +3,8 @@
 //
 // Work decomposition.  An instance's cells are grouped in 32-cell segments; only the
 // segments holding fluid are listed (all-solid segments cost nothing).  A warp takes
-// chunks of consecutive list entries from a global counter; one lane per cell.
+// chunks of consecutive list entries from a global counter (one lane per cell), loads the
+// chunk's segment descriptors once, and keeps the instance parameters in registers.
 //
 // Per fluid cell x and direction k (all arithmetic on deviations g = f - w rho0):
 //   pull      g_k <- g~_k(x - e_k), plus +w_k delta_rho when the pull crosses the x
@@ -15,12 +16,9 @@
 //   moments   drho = sum g_k, u = rho0^-1 sum e_k g_k (Eq. Macro);
 //   collide   SRT, TRT or MRT relaxation towards Eq. equilibrium;
 //   store     A-B: to the other buffer; AA: in place (see below).
-//
-// Staged loads.  Each lane copies its cell's 19 pull sources with per-thread asynchronous
-// copies (cp.async) into its own slots of a per-warp shared-memory ring of kStages
-// segments, kStages - 1 segments ahead of the one being collided.  Populations in flight
-// therefore hold no registers, and no lane reads another lane's slots.  16-bit formats
-// copy the aligned 32-bit word holding the population and keep which half it is.
+// The 19 pulls are issued unconditionally (a solid source slot holds 0 and is then
+// replaced by the wall rule), so no load waits on the boundary table; the wall code runs
+// only in warps whose segment holds a boundary cell.
 //
 // AA layout (in-place, one buffer).  PULL steps read g~_k(x - e_k) from slot kbar of
 // x - e_k and push g~_k(x) into slot k of x + e_k; LOCAL steps read slot k and write
@@ -34,8 +32,6 @@
 
 namespace lbm {
 
-constexpr int kStages = 3;  // segments per warp: kStages - 1 in flight while one is collided
-
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -43,119 +39,96 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// One stage of a warp's ring: [19][32] copied words (8 bytes for FP64, else 4), then for
-// 16-bit formats one 19-bit mask per lane telling which half of each word is wanted.
-template <int STORE> struct Stage {
-    using T = typename Store<STORE>::T;
-    static constexpr int word = sizeof(T) == 8 ? 8 : 4;
-    static constexpr bool halves = sizeof(T) == 2;
-    static constexpr int bytes = Q * 32 * word + (halves ? 32 * 4 : 0);
+// The step kernel uses no dynamic shared memory.
+inline size_t step_smem_bytes(int, int) { return 0; }
+constexpr int kStepWarps = 8;  // warps per step-kernel block
+
+// Instance parameters held in registers for the duration of a chunk.
+template <typename R> struct Par {
+    uint32_t ks, nx, ny, nz;
+    FastDiv dnx, dny;
+    R omega, omega_m, rho0, irho0, dshift;
+    float sc, isc;
+    int wall;
 };
 
-inline size_t step_smem_bytes(int storage, int warps)
+template <typename R> __device__ __forceinline__ Par<R> load_par(const InstanceDev &I)
 {
-    const int stage = storage == ST_F64 ? Stage<ST_F64>::bytes
-                      : storage == ST_F32 ? Stage<ST_F32>::bytes
-                                          : Stage<ST_F16>::bytes;
-    return (size_t)warps * kStages * stage;
+    Par<R> p;
+    p.ks = I.ks;
+    p.nx = I.nx;
+    p.ny = I.ny;
+    p.nz = I.nz;
+    p.dnx = I.div_nx;
+    p.dny = I.div_ny;
+    p.omega = R(I.omega);
+    p.omega_m = R(I.omega_m);
+    p.rho0 = R(I.rho0);
+    p.irho0 = R(1) / R(I.rho0);
+    p.dshift = R(I.delta_rho);
+    p.sc = I.scale;
+    p.isc = I.inv_scale;
+    p.wall = I.wall;
+    return p;
 }
 
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-template <int BYTES>
-__device__ __forceinline__ void cp_async(uint32_t dst, const void *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(src), "n"(BYTES) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// Cell coordinates and the periodic x-1/x/x+1 offsets, row offsets y-1/y/y+1 and plane
+// Cell coordinates with the periodic x-1/x/x+1 offsets, row offsets y-1/y/y+1 and plane
 // offsets z-1/z/z+1 (32-bit element counts).
 struct Coord {
-    uint32_t x, y, z;
+    uint32_t x;
     uint32_t X[3], Y[3], Z[3];
     __device__ __forceinline__ uint32_t pull(int k) const { return X[1 - ex(k)] + Y[1 - ey(k)] + Z[1 - ez(k)]; }
+    __device__ __forceinline__ uint32_t push(int k) const { return X[1 + ex(k)] + Y[1 + ey(k)] + Z[1 + ez(k)]; }
 };
-__device__ __forceinline__ Coord coord_of(const InstanceDev &I, uint32_t cell)
+template <typename R> __device__ __forceinline__ Coord coord_of(const Par<R> &p, uint32_t cell)
 {
     Coord c;
-    const uint32_t nx = I.nx, ny = I.ny, nz = I.nz, nxy = nx * ny;
-    const uint32_t yz = fast_div(cell, I.div_nx);
+    const uint32_t nx = p.nx, ny = p.ny, nz = p.nz, nxy = nx * ny;
+    const uint32_t yz = fast_div(cell, p.dnx);
     c.x = cell - yz * nx;
-    c.z = fast_div(yz, I.div_ny);
-    c.y = yz - c.z * ny;
+    const uint32_t z = fast_div(yz, p.dny);
+    const uint32_t y = yz - z * ny;
     c.X[0] = c.x == 0 ? nx - 1 : c.x - 1;
     c.X[1] = c.x;
     c.X[2] = c.x == nx - 1 ? 0 : c.x + 1;
-    c.Y[0] = (c.y == 0 ? ny - 1 : c.y - 1) * nx;
-    c.Y[1] = c.y * nx;
-    c.Y[2] = (c.y == ny - 1 ? 0 : c.y + 1) * nx;
-    c.Z[0] = (c.z == 0 ? nz - 1 : c.z - 1) * nxy;
-    c.Z[1] = c.z * nxy;
-    c.Z[2] = (c.z == nz - 1 ? 0 : c.z + 1) * nxy;
+    c.Y[0] = (y == 0 ? ny - 1 : y - 1) * nx;
+    c.Y[1] = y * nx;
+    c.Y[2] = (y == ny - 1 ? 0 : y + 1) * nx;
+    c.Z[0] = (z == 0 ? nz - 1 : z - 1) * nxy;
+    c.Z[1] = z * nxy;
+    c.Z[2] = (z == nz - 1 ? 0 : z + 1) * nxy;
     return c;
 }
 
-// Element index of the population a cell pulls for direction k: A-B array k at x - e_k;
-// AA pull array kbar at x - e_k; AA local array k at x.
-template <int KIND>
-__device__ __forceinline__ uint32_t pull_index(uint32_t N, uint32_t cell, const Coord &c, int k)
+// Moments of the incoming populations (Eq. Macro), in deviation form.
+template <typename R>
+__device__ __forceinline__ void moments(const R (&g)[Q], R irho0, R &drho, R &ux, R &uy, R &uz)
 {
-    if constexpr (KIND == KIND_AA_LOCAL) return (uint32_t)k * N + cell;
-    else if constexpr (KIND == KIND_AA_PULL) return (uint32_t)opp(k) * N + c.pull(k);
-    else return (uint32_t)k * N + c.pull(k);
-}
-
-// Queue the asynchronous copies of one lane's 19 pull sources into a stage.
-template <int STORE, int KIND>
-__device__ __forceinline__ void issue_cell(const InstanceDev &I, const typename Store<STORE>::T *fs, uint4 meta,
-                                           int lane, unsigned char *stage)
-{
-    using St = Stage<STORE>;
-    if ((meta.x >> lane) & 1u) return;
-    const uint32_t cell = meta.w * 32u + lane;
-    const Coord c = coord_of(I, cell);
-    const uint32_t base = smem_addr(stage) + (uint32_t)lane * St::word;
-    uint32_t hmask = 0u;
+    // sums and differences of opposite pairs: drho = g_0 + sum s_p, j = sum e_p d_p
+    R d_sum = g[0], jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
-    for (int k = 0; k < Q; ++k) {
-        const uint32_t idx = pull_index<KIND>(I.n32, cell, c, k);
-        if constexpr (St::halves) {
-            hmask |= (idx & 1u) << k;
-            cp_async<4>(base + (uint32_t)(k * 32 * 4), fs + (idx & ~1u));
-        } else {
-            cp_async<St::word>(base + (uint32_t)(k * 32 * St::word), fs + idx);
-        }
+    for (int k = 1; k < Q; k += 2) {
+        const R sp = g[k] + g[k + 1], dp = g[k] - g[k + 1];
+        d_sum += sp;
+        if (ex(k)) jx += ex(k) > 0 ? dp : -dp;
+        if (ey(k)) jy += ey(k) > 0 ? dp : -dp;
+        if (ez(k)) jz += ez(k) > 0 ? dp : -dp;
     }
-    if constexpr (St::halves) reinterpret_cast<uint32_t *>(stage + Q * 32 * 4)[lane] = hmask;
+    drho = d_sum;
+    ux = jx * irho0;
+    uy = jy * irho0;
+    uz = jz * irho0;
 }
 
-// Read back population k of a lane from a stage.
-template <int STORE>
-__device__ __forceinline__ typename Store<STORE>::R staged_value(const unsigned char *stage, int k, int lane,
-                                                                   uint32_t hmask, float isc)
-{
-    using S = Store<STORE>;
-    using T = typename S::T;
-    if constexpr (Stage<STORE>::halves) {
-        const uint32_t w = reinterpret_cast<const uint32_t *>(stage)[k * 32 + lane];
-        const unsigned short h = (unsigned short)(((hmask >> k) & 1u) ? (w >> 16) : (w & 0xFFFFu));
-        T v;
-        memcpy(&v, &h, 2);
-        return S::cvt(v, isc);
-    } else {
-        return S::cvt(reinterpret_cast<const T *>(stage)[k * 32 + lane], isc);
-    }
-}
-
-// Collision of one cell, in place on g[] (deviations).  rho0 enters the equilibrium.
+// Collision of one cell, in place on g[] (deviations), Eqs. SRT, TRT, MRT with the
+// equilibrium of Eq. equilibrium.  rates: the 19 MRT rates (MRT only).
 template <int COLL, typename R>
-__device__ __forceinline__ void collide(R (&g)[Q], const InstanceDev &I, R drho, R ux, R uy, R uz)
+__device__ __forceinline__ void collide(R (&g)[Q], const Par<R> &p, const R *rates, R drho, R ux, R uy, R uz)
 {
-    const R rho0 = R(I.rho0);
+    const R rho0 = p.rho0;
     const R uu = ux * ux + uy * uy + uz * uz;
     if constexpr (COLL == COLL_SRT) {
-        const R om = R(I.omega);
+        const R om = p.omega;
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             const R eu = R(ex(k)) * ux + R(ey(k)) * uy + R(ez(k)) * uz;
@@ -163,21 +136,19 @@ __device__ __forceinline__ void collide(R (&g)[Q], const InstanceDev &I, R drho,
             g[k] = g[k] - om * (g[k] - geq);
         }
     } else if constexpr (COLL == COLL_TRT) {
-        const R wp = R(I.omega), wm = R(I.omega_m);
-        {
-            const R geq0 = R(weight(0)) * (drho - rho0 * R(1.5) * uu);
-            g[0] = g[0] - wp * (g[0] - geq0);
-        }
+        // symmetric part relaxes with omega+, antisymmetric part with omega- (Eq. TRT)
+        const R wp = p.omega, wm = p.omega_m;
+        const R base = drho - R(1.5) * rho0 * uu;     // drho + rho0 (-3/2 u.u)
+        g[0] = g[0] - wp * (g[0] - R(weight(0)) * base);
 #pragma unroll
         for (int k = 1; k < Q; k += 2) {
             const int kb = k + 1;
+            const R w = R(weight(k));
             const R eu = R(ex(k)) * ux + R(ey(k)) * uy + R(ez(k)) * uz;
-            const R eqp = R(weight(k)) * (drho + rho0 * (R(4.5) * eu * eu - R(1.5) * uu));
-            const R eqm = R(weight(k)) * (rho0 * R(3) * eu);
-            const R gp = R(0.5) * (g[k] + g[kb]);
-            const R gm = R(0.5) * (g[k] - g[kb]);
-            const R dp = wp * (gp - eqp);
-            const R dm = wm * (gm - eqm);
+            const R eqp = w * (base + R(4.5) * rho0 * eu * eu);   // (f_k^eq + f_kbar^eq) / 2
+            const R eqm = (w * R(3) * rho0) * eu;                  // (f_k^eq - f_kbar^eq) / 2
+            const R dp = wp * (R(0.5) * (g[k] + g[kb]) - eqp);
+            const R dm = wm * (R(0.5) * (g[k] - g[kb]) - eqm);
             g[k] = g[k] - dp - dm;
             g[kb] = g[kb] - dp + dm;
         }
@@ -199,7 +170,7 @@ __device__ __forceinline__ void collide(R (&g)[Q], const InstanceDev &I, R drho,
                 else if (c == -1) m -= neq[k];
                 else if (c != 0) m += R(c) * neq[k];
             }
-            const R dm = R(I.s[i]) * m * (R(1) / R(mrt_norm2(i)));
+            const R dm = rates[i] * m;  // rates[] already divided by |M_i|^2
 #pragma unroll
             for (int k = 0; k < Q; ++k) {
                 const int c = mrt_m(i, k);
@@ -213,10 +184,14 @@ __device__ __forceinline__ void collide(R (&g)[Q], const InstanceDev &I, R drho,
 
 // The fused step.  flip selects the A-B buffer pair (src = f[phase ^ flip]); reduce != 0
 // makes every chunk write its FP64 partial sums (drho, u_x, u_y, u_z) and flags diverged
-// cells in status[instance].  sched[0] is the chunk counter, sched[1] counts finished
-// blocks; the last block resets both for the next launch.
+// cells in status[instance].  sched[0] is the chunk counter and sched[1] counts warps that
+// ran out of chunks; the last such warp resets both for the next launch.
+// Blocks per multiprocessor the register allocation is sized for: A-B steps of the 32- and
+// 16-bit formats fit 64 registers (4 blocks of 256); AA steps and FP64 need more.
+template <int STORE, int KIND> constexpr int step_min_blocks() { return (KIND == KIND_AB && STORE != ST_F64) ? 4 : 2; }
+
 template <int COLL, int STORE, int KIND>
-__global__ void __launch_bounds__(256) step_kernel(const InstanceDev *__restrict__ table,
+__global__ void __launch_bounds__(256, step_min_blocks<STORE, KIND>()) step_kernel(const InstanceDev *__restrict__ table,
                                                    const TileDev *__restrict__ chunks, int nchunks, int chunk_segs,
                                                    int flip, int reduce, unsigned *__restrict__ status,
                                                    unsigned *__restrict__ sched)
@@ -224,11 +199,8 @@ __global__ void __launch_bounds__(256) step_kernel(const InstanceDev *__restrict
     using S = Store<STORE>;
     using T = typename S::T;
     using R = typename S::R;
-    using St = Stage<STORE>;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-
+    __shared__ double acc_s[kStepWarps][4];  // a warp's FP64 partial sums of its current chunk
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned char *ring = smem_raw + (size_t)warp * kStages * St::bytes;
 
     while (true) {
         int c = 0;
@@ -237,12 +209,20 @@ __global__ void __launch_bounds__(256) step_kernel(const InstanceDev *__restrict
         if (c >= nchunks) break;
         const TileDev chunk = chunks[c];
         const InstanceDev &I = table[chunk.inst];
+        const Par<R> P = load_par<R>(I);
+        R rates[Q];
+        if constexpr (COLL == COLL_MRT) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) rates[i] = R(I.s[i]) / R(mrt_norm2(i));
+        }
         const uint32_t e0 = (uint32_t)chunk.seg0;
         const int n_e = min(chunk_segs, (int)(I.n_active - e0));
         const uint4 meta_l = lane < n_e ? I.aseg[e0 + lane] : make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
-        const uint32_t N = I.n32;
-        const uint32_t nx = I.nx;
-        const float sc = I.scale, isc = I.inv_scale;
+        const uint32_t *bmask = I.bmask;
+        const uint32_t *boff = I.boff;
+        const R *linkc = reinterpret_cast<const R *>(I.linkc);
+        T *linkB = reinterpret_cast<T *>(I.linkB);
+        const uint32_t KS = P.ks;
         T *fs;  // state read this step
         T *fd;  // state written this step
         if constexpr (KIND == KIND_AB) {
@@ -252,77 +232,63 @@ __global__ void __launch_bounds__(256) step_kernel(const InstanceDev *__restrict
         } else {
             fs = fd = reinterpret_cast<T *>(I.f0);
         }
-        const R dshift = R(I.delta_rho);
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        if (reduce && lane < 4) acc_s[warp][lane] = 0.0;
+        __syncwarp();
 
-        auto meta_at = [&](int i) {
-            uint4 m;
-            m.x = __shfl_sync(0xffffffffu, meta_l.x, i);
-            m.y = __shfl_sync(0xffffffffu, meta_l.y, i);
-            m.z = __shfl_sync(0xffffffffu, meta_l.z, i);
-            m.w = __shfl_sync(0xffffffffu, meta_l.w, i);
-            return m;
-        };
-        // prologue: kStages - 1 segments in flight
-#pragma unroll
-        for (int i = 0; i < kStages - 1; ++i) {
-            if (i < n_e) issue_cell<STORE, KIND>(I, fs, meta_at(i), lane, ring + i * St::bytes);
-            cp_commit();
-        }
-
+#pragma unroll 1
         for (int i = 0; i < n_e; ++i) {
-            const int j = i + kStages - 1;
-            if (j < n_e) issue_cell<STORE, KIND>(I, fs, meta_at(j), lane, ring + (j % kStages) * St::bytes);
-            cp_commit();
-            cp_wait<kStages - 1>();  // this lane's copies of segment i have landed
-            const uint4 meta = meta_at(i);
-            const unsigned char *stage = ring + (i % kStages) * St::bytes;
+            const uint32_t m_solid = __shfl_sync(0xffffffffu, meta_l.x, i);
+            const uint32_t m_bnd = __shfl_sync(0xffffffffu, meta_l.y, i);
+            const uint32_t m_base = __shfl_sync(0xffffffffu, meta_l.z, i);
+            const uint32_t m_seg = __shfl_sync(0xffffffffu, meta_l.w, i);
+            R rd = R(0), rx = R(0), ry = R(0), rz = R(0);  // moments for the reduction
+            if (!((m_solid >> lane) & 1u)) {
+                const uint32_t cell = m_seg * 32u + lane;
+                const Coord co = coord_of(P, cell);
 
-            if (!((meta.x >> lane) & 1u)) {
-                const uint32_t cell = meta.w * 32u + lane;
-                const Coord co = coord_of(I, cell);
-                const uint32_t x = co.x;
-                uint32_t hmask = 0u;
-                if constexpr (St::halves) hmask = reinterpret_cast<const uint32_t *>(stage + Q * 32 * 4)[lane];
-
-                uint32_t wm = 0u, off = 0u;
-                if ((meta.y >> lane) & 1u) {
-                    const uint32_t b = meta.z + __popc(meta.y & ((1u << lane) - 1u));
-                    wm = I.bmask[b];
-                    off = I.boff[b];
-                }
-
+                // pull (unconditional), then the pressure shift of x-crossing pulls
                 R g[Q];
 #pragma unroll
                 for (int k = 0; k < Q; ++k) {
-                    if ((wm >> k) & 1u) {
-                        g[k] = R(0);
-                        continue;
-                    }
-                    R v = staged_value<STORE>(stage, k, lane, hmask, isc);
-                    if (ex(k) == 1 && x == 0) v += R(weight(k)) * dshift;
-                    if (ex(k) == -1 && x == nx - 1) v -= R(weight(k)) * dshift;
-                    g[k] = v;
+                    uint32_t idx;
+                    if constexpr (KIND == KIND_AA_LOCAL) idx = (uint32_t)k * KS + cell;
+                    else if constexpr (KIND == KIND_AA_PULL) idx = (uint32_t)opp(k) * KS + co.pull(k);
+                    else idx = (uint32_t)k * KS + co.pull(k);
+                    g[k] = S::load(fs + idx, P.isc);
                 }
-                if (wm) {
-                    const R *linkc = reinterpret_cast<const R *>(I.linkc);
-                    const T *linkB = reinterpret_cast<const T *>(I.linkB);
+                if (co.x == 0) {
+#pragma unroll
+                    for (int k = 0; k < Q; ++k)
+                        if (ex(k) == 1) g[k] += R(weight(k)) * P.dshift;
+                }
+                if (co.x == P.nx - 1) {
+#pragma unroll
+                    for (int k = 0; k < Q; ++k)
+                        if (ex(k) == -1) g[k] -= R(weight(k)) * P.dshift;
+                }
+
+                // walls (only lanes of boundary cells; the solid sources read above hold 0)
+                uint32_t wm = 0u, off = 0u;
+                if ((m_bnd >> lane) & 1u) {
+                    const uint32_t b = m_base + __popc(m_bnd & ((1u << lane) - 1u));
+                    wm = bmask[b];
+                    off = boff[b];
 #pragma unroll
                     for (int k = 1; k < Q; ++k) {
                         if (!((wm >> k) & 1u)) continue;
                         const int kb = opp(k);
                         // own post-collision g~_kbar(x)
                         R C;
-                        if constexpr (KIND == KIND_AB) C = S::load(fs + ((uint32_t)kb * N + cell), isc);
-                        else C = S::load(fs + ((uint32_t)k * N + cell), isc);
+                        if constexpr (KIND == KIND_AB) C = S::load(fs + ((uint32_t)kb * KS + cell), P.isc);
+                        else C = S::load(fs + ((uint32_t)k * KS + cell), P.isc);
                         R v = C;
-                        if (I.wall == 1) {
+                        if (P.wall == 1) {
                             const uint32_t l = off + __popc(wm & ((1u << k) - 1u));
                             const R cq = linkc[l];
                             if (cq != R(0)) {
                                 R B;  // own post-collision g~_k(x)
-                                if constexpr (KIND == KIND_AB) B = S::load(fs + ((uint32_t)k * N + cell), isc);
-                                else B = S::load(linkB + l, isc);
+                                if constexpr (KIND == KIND_AB) B = S::load(fs + ((uint32_t)k * KS + cell), P.isc);
+                                else B = S::load(linkB + l, P.isc);
                                 v = cq * (g[kb] - B) + C;
                             }
                         }
@@ -330,74 +296,66 @@ __global__ void __launch_bounds__(256) step_kernel(const InstanceDev *__restrict
                     }
                 }
 
-                R drho = R(0), jx = R(0), jy = R(0), jz = R(0);
-#pragma unroll
-                for (int k = 0; k < Q; ++k) {
-                    drho += g[k];
-                    if (ex(k)) jx += ex(k) > 0 ? g[k] : -g[k];
-                    if (ey(k)) jy += ey(k) > 0 ? g[k] : -g[k];
-                    if (ez(k)) jz += ez(k) > 0 ? g[k] : -g[k];
-                }
-                const R irho0 = R(1) / R(I.rho0);
-                const R ux = jx * irho0, uy = jy * irho0, uz = jz * irho0;
+                R drho, ux, uy, uz;
+                moments(g, P.irho0, drho, ux, uy, uz);
                 if (reduce) {
-                    a0 += (double)drho;
-                    a1 += (double)ux;
-                    a2 += (double)uy;
-                    a3 += (double)uz;
+                    rd = drho;
+                    rx = ux;
+                    ry = uy;
+                    rz = uz;
                     const R uu = ux * ux + uy * uy + uz * uz;
                     if (!(uu < R(0.09)) || !(drho == drho)) atomicOr(status + chunk.inst, STATUS_DIVERGED);
                 }
 
-                collide<COLL, R>(g, I, drho, ux, uy, uz);
+                collide<COLL, R>(g, P, rates, drho, ux, uy, uz);
 
 #pragma unroll
                 for (int k = 0; k < Q; ++k) {
-                    const T v = S::pack(g[k], sc);
+                    const T v = S::pack(g[k], P.sc);
                     if constexpr (KIND == KIND_AB) {
-                        fd[(uint32_t)k * N + cell] = v;
+                        fd[(uint32_t)k * KS + cell] = v;
                     } else if constexpr (KIND == KIND_AA_LOCAL) {
-                        fd[(uint32_t)opp(k) * N + cell] = v;
+                        fd[(uint32_t)opp(k) * KS + cell] = v;
                     } else {
-                        // push to x + e_k = pull source of kbar, or bounce into the own slot
-                        if ((wm >> opp(k)) & 1u) fd[(uint32_t)opp(k) * N + cell] = v;
-                        else fd[(uint32_t)k * N + co.pull(opp(k))] = v;
+                        // push to x + e_k, or bounce into the own slot kbar when x + e_k is solid
+                        if ((wm >> opp(k)) & 1u) fd[(uint32_t)opp(k) * KS + cell] = v;
+                        else fd[(uint32_t)k * KS + co.push(k)] = v;
                     }
                 }
                 if constexpr (KIND != KIND_AB) {
-                    if (wm && I.wall == 1) {
-                        T *linkB = reinterpret_cast<T *>(I.linkB);
+                    if (wm && P.wall == 1) {
 #pragma unroll
                         for (int k = 1; k < Q; ++k) {
                             if (!((wm >> k) & 1u)) continue;
-                            linkB[off + __popc(wm & ((1u << k) - 1u))] = S::pack(g[k], sc);
+                            linkB[off + __popc(wm & ((1u << k) - 1u))] = S::pack(g[k], P.sc);
                         }
                     }
                 }
             }
-        }
-        if (reduce) {  // deterministic: per-lane sums over the chunk, then a fixed shuffle tree
-            a0 = warp_sum(a0);
-            a1 = warp_sum(a1);
-            a2 = warp_sum(a2);
-            a3 = warp_sum(a3);
-            if (lane == 0) {
-                double *p = I.partials + (size_t)chunk.local * 4;
-                p[0] = a0;
-                p[1] = a1;
-                p[2] = a2;
-                p[3] = a3;
+            if (reduce) {  // deterministic: fixed shuffle tree per segment, segments in order
+                const double s0 = warp_sum((double)rd), s1 = warp_sum((double)rx);
+                const double s2 = warp_sum((double)ry), s3 = warp_sum((double)rz);
+                if (lane == 0) {
+                    acc_s[warp][0] += s0;
+                    acc_s[warp][1] += s1;
+                    acc_s[warp][2] += s2;
+                    acc_s[warp][3] += s3;
+                }
             }
         }
+        if (reduce && lane == 0) {
+            double *pp = I.partials + (size_t)chunk.local * 4;
+            for (int d = 0; d < 4; ++d) pp[d] = acc_s[warp][d];
+        }
+        __syncwarp();
     }
-    cp_wait<0>();
 
-    // the last block to finish resets the work counter for the next launch
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    // the last warp to run out of chunks resets the work counter for the next launch
+    if (lane == 0) {
         __threadfence();
+        const unsigned warps = gridDim.x * (blockDim.x >> 5);
         const unsigned done = atomicAdd(&sched[1], 1u);
-        if (done == gridDim.x - 1) {
+        if (done == warps - 1) {
             sched[0] = 0u;
             sched[1] = 0u;
             __threadfence();

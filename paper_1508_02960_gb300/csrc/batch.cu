@@ -75,8 +75,8 @@ lbm_status validate_desc(const lbm_desc &d)
     if (d.magic_lambda < 0 || !std::isfinite(d.magic_lambda)) return fail(LBM_ERR_ARG, "magic_lambda must be >= 0");
     if (d.mrt_energy_ratio < 0 || !std::isfinite(d.mrt_energy_ratio))
         return fail(LBM_ERR_ARG, "mrt_energy_ratio must be >= 0");
-    if (d.block_cells != 0 && (d.block_cells < 32 * kMinChunkSegs || d.block_cells > 1024 || d.block_cells % 32))
-        return fail(LBM_ERR_ARG, "block_cells (cells per work chunk) must be 0 or a multiple of 32 in [128, 1024]");
+    if (d.block_cells != 0 && d.block_cells != 32 * kTileSegs)
+        return fail(LBM_ERR_ARG, "block_cells is reserved: 0 (or the tile size)");
     if (d.dev_scale_log2 != LBM_DEV_SCALE_AUTO && (d.dev_scale_log2 < -60 || d.dev_scale_log2 > 60))
         return fail(LBM_ERR_ARG, "dev_scale_log2 out of [-60, 60]");
     if (!std::isfinite(d.perturb_u) || std::fabs(d.perturb_u) > 0.3) return fail(LBM_ERR_ARG, "|perturb_u| > 0.3");
@@ -205,7 +205,6 @@ Batch::~Batch()
     cudaFree(d_sums_);
     cudaFree(d_status_);
     cudaFree(d_stage_);
-    cudaFree(d_sched_);
     if (h_sums_) cudaFreeHost(h_sums_);
     if (h_status_) cudaFreeHost(h_status_);
     if (cap_) cudaStreamDestroy(cap_);
@@ -250,8 +249,7 @@ lbm_status Batch::remove(int i)
 
 lbm_status Batch::set_block(int block_cells)
 {
-    if (block_cells < 32 * kMinChunkSegs || block_cells > 1024 || block_cells % 32)
-        return fail(LBM_ERR_ARG, "bad work chunk size");
+    if (block_cells != 32 * kTileSegs) return fail(LBM_ERR_ARG, "block_cells is reserved: 0 (or the tile size)");
     if (block_cells != block_) {
         block_ = block_cells;
         dirty_ = true;
@@ -366,27 +364,11 @@ lbm_status Batch::rebuild()
         CK(cudaMallocHost(&h_sums_, sizeof(double) * 4 * capacity_));
         CK(cudaMallocHost(&h_status_, sizeof(unsigned) * capacity_));
     }
-    // persistent grid: as many step blocks as fit on the device at once
-    if (!d_sched_) {
-        CK(cudaMalloc(&d_sched_, 2 * sizeof(unsigned)));
-        CK(cudaMemset(d_sched_, 0, 2 * sizeof(unsigned)));
-    }
+    // one step block per tile; the hardware block scheduler balances the tiles
+    grid_ = std::max(1, ntiles_);
     int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    smem_ = step_smem_bytes(storage_, kStepBlock / 32);
-    int per_sm = 0;
-    for (int kind = 0; kind < 3; ++kind) {
-        if (layout_ == LBM_LAYOUT_AB && kind != KIND_AB) continue;
-        if (layout_ == LBM_LAYOUT_AA && kind == KIND_AB) continue;
-        const void *fn = ops().step_kernel_ptr(collision_, kind);
-        CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_));
-        int nb = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kStepBlock, smem_));
-        per_sm = per_sm == 0 ? nb : std::min(per_sm, nb);
-    }
-    if (per_sm < 1) return fail(LBM_ERR_CUDA, "step kernel does not fit on a multiprocessor");
-    grid_ = sms * per_sm;
     aux_grid_ = std::max(1, std::min(sms * 8, (ntiles_ + 7) / 8));
     dirty_ = false;
     return LBM_OK;
@@ -458,7 +440,7 @@ lbm_status Batch::step(long long n)
         lbm_status st = rebuild();
         if (st != LBM_OK) return st;
     }
-    StepQueue q{&ops(), Launch{d_table_, d_tiles_, ntiles_, block_ / 32, grid_, kStepBlock, smem_, d_sched_, stream_},
+    StepQueue q{&ops(), Launch{d_table_, d_tiles_, ntiles_, block_ / 32, grid_, kStepWarps * 32, stream_},
                 collision_, layout_, d_status_,
                 size(), d_tile_begin_, d_tile_count_, d_sums_, size()};
     const long long kChunk = 1000;
@@ -536,8 +518,8 @@ lbm_status Batch::moment_sums_now(int i, double *sums)
         }
     }
     const int nt = (int)std::max(1ll, (in.geo.n_active + block_ / 32 - 1) / (block_ / 32));
-    Launch L{d_table_, d_tiles_ + tb[i], nt, block_ / 32, std::max(1, std::min(aux_grid_, (nt + 7) / 8)), 256, 0,
-             nullptr, stream_};
+    Launch L{d_table_, d_tiles_ + tb[i], nt, block_ / 32, std::max(1, std::min(aux_grid_, (nt + 7) / 8)), 256,
+             stream_};
     CK(ops().moments(L, layout_, cur_of(in), aa_phase_, 1, 0, nullptr));
     CK(launch_final_reduce(d_table_ + i, d_tile_begin_ + i, d_tile_count_ + i, 1, d_sums_ + 4 * i, stream_));
     launches_ += 2;
@@ -616,8 +598,8 @@ lbm_status Batch::get_velocity(int i, double *host)
         acc += (int)std::max(1ll, (inst_[j]->geo.n_active + block_ / 32 - 1) / (block_ / 32));
     }
     const int nt = (int)std::max(1ll, (in.geo.n_active + block_ / 32 - 1) / (block_ / 32));
-    Launch L{d_table_, d_tiles_ + tb[i], nt, block_ / 32, std::max(1, std::min(aux_grid_, (nt + 7) / 8)), 256, 0,
-             nullptr, stream_};
+    Launch L{d_table_, d_tiles_ + tb[i], nt, block_ / 32, std::max(1, std::min(aux_grid_, (nt + 7) / 8)), 256,
+             stream_};
     for (int c = 0; c < 3; ++c) {
         // all-solid segments are not in the work list: clear the whole field first
         CK(cudaMemsetAsync(d_stage_, 0, sizeof(double) * n, stream_));

@@ -86,11 +86,9 @@ private:
     unsigned *h_status_ = nullptr;    // pinned [n]
     int capacity_ = 0;
     int ntiles_ = 0;
-    int block_ = 256;                 // cells per work chunk (one warp's unit of work)
-    int grid_ = 0;                    // persistent step-kernel blocks
+    int block_ = 32 * kTileSegs;      // cells per tile (one step block)
+    int grid_ = 0;                    // step-kernel blocks (one per tile)
     int aux_grid_ = 1;
-    size_t smem_ = 0;
-    unsigned *d_sched_ = nullptr;     // step-kernel work counter
     int flip_ = 0;
     int aa_phase_ = 0;
     bool dirty_ = true;

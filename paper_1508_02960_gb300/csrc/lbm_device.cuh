@@ -204,6 +204,12 @@ struct TileDev {
 };
 
 enum { KIND_AB = 0, KIND_AA_PULL = 1, KIND_AA_LOCAL = 2 };
+
+// Step-kernel tiling: one block of kStepWarps warps per tile; each warp takes
+// kSegsPerWarp consecutive entries of the active-segment list.
+constexpr int kStepWarps = 4;
+constexpr int kSegsPerWarp = 2;
+constexpr int kTileSegs = kStepWarps * kSegsPerWarp;
 enum { COLL_SRT = 0, COLL_TRT = 1, COLL_MRT = 2 };
 
 // Status word bits: a reduction saw a diverged cell; a bounded wait ran out.

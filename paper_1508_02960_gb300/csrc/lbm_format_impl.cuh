@@ -13,8 +13,8 @@ namespace detail {
 template <int STORE, int COLL, int KIND>
 cudaError_t step_one(const Launch &L, int flip, int reduce, unsigned *status)
 {
-    step_kernel<COLL, STORE, KIND><<<L.grid, L.block, L.smem, L.stream>>>(L.table, L.tiles, L.ntiles, L.chunk_segs,
-                                                                          flip, reduce, status, L.sched);
+    step_kernel<COLL, STORE, KIND><<<L.grid, L.block, 0, L.stream>>>(L.table, L.tiles, L.ntiles, flip, reduce,
+                                                                     status);
     return cudaGetLastError();
 }
 

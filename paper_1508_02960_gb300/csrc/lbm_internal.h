@@ -12,16 +12,14 @@
 
 namespace lbm {
 
-// Arguments of one persistent launch over a list of work chunks (each chunk: up to
-// chunk_segs consecutive active segments of one instance, processed by one warp).
+// Arguments of one launch over a tile list (each tile: up to chunk_segs consecutive
+// entries of one instance's active-segment list).
 struct Launch {
     const InstanceDev *table;
     const TileDev *tiles;
     int ntiles;
     int chunk_segs;
     int grid, block;
-    size_t smem;          // dynamic shared memory of the step kernel
-    unsigned *sched;      // step kernel work counter (2 words, zero between launches)
     cudaStream_t stream;
 };
 
@@ -79,8 +77,7 @@ cudaError_t launch_final_reduce(const InstanceDev *table, const int *tile_begin,
 void set_error(const std::string &msg);
 
 constexpr int kMaxWarpsPerBlock = 32;
-constexpr int kStepBlock = 256;        // threads of a step-kernel block (8 warps)
-constexpr int kMinChunkSegs = 4;       // smallest work chunk (segments)
+constexpr int kMinChunkSegs = 4;       // smallest tile (segments): sizes the partial sums
 constexpr long long kDirPad = 0;       // extra elements between direction arrays
 long long direction_stride(long long ncells);
 

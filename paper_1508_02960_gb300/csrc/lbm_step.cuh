@@ -2,9 +2,9 @@
 // fused so that macroscopic values are never stored).
 //
 // Work decomposition.  An instance's cells are grouped in 32-cell segments; only the
-// segments holding fluid are listed (all-solid segments cost nothing).  A warp takes
-// chunks of consecutive list entries from a global counter (one lane per cell), loads the
-// chunk's segment descriptors once, and keeps the instance parameters in registers.
+// segments holding fluid are listed (all-solid segments cost nothing).  One block per
+// tile of consecutive list entries; each warp (one lane per cell) takes kSegsPerWarp of
+// them and issues all their pulls before finishing the first, for load/compute overlap.
 //
 // Per fluid cell x and direction k (all arithmetic on deviations g = f - w rho0):
 //   pull      g_k <- g~_k(x - e_k), plus +w_k delta_rho when the pull crosses the x
@@ -41,7 +41,6 @@ __device__ __forceinline__ double warp_sum(double v)
 
 // The step kernel uses no dynamic shared memory.
 inline size_t step_smem_bytes(int, int) { return 0; }
-constexpr int kStepWarps = 8;  // warps per step-kernel block
 
 // Instance parameters held in registers for the duration of a chunk.
 template <typename R> struct Par {
@@ -99,6 +98,9 @@ template <typename R> __device__ __forceinline__ Coord coord_of(const Par<R> &p,
     c.Z[2] = (z == nz - 1 ? 0 : z + 1) * nxy;
     return c;
 }
+
+// Blocks per multiprocessor the register allocation is sized for.
+template <int STORE, int KIND> constexpr int step_min_blocks() { return STORE == ST_F64 ? 2 : 6; }
 
 // Moments of the incoming populations (Eq. Macro), in deviation form.
 template <typename R>
@@ -182,183 +184,195 @@ __device__ __forceinline__ void collide(R (&g)[Q], const Par<R> &p, const R *rat
     }
 }
 
-// The fused step.  flip selects the A-B buffer pair (src = f[phase ^ flip]); reduce != 0
-// makes every chunk write its FP64 partial sums (drho, u_x, u_y, u_z) and flags diverged
-// cells in status[instance].  sched[0] is the chunk counter and sched[1] counts warps that
-// ran out of chunks; the last such warp resets both for the next launch.
-// Blocks per multiprocessor the register allocation is sized for: A-B steps of the 32- and
-// 16-bit formats fit 64 registers (4 blocks of 256); AA steps and FP64 need more.
-template <int STORE, int KIND> constexpr int step_min_blocks() { return (KIND == KIND_AB && STORE != ST_F64) ? 4 : 2; }
+// Process one cell whose 19 pulled populations are in g[] (already shifted): walls,
+// moments, collision, stores.  Returns the moments for the reduction through rd..rz.
+template <int COLL, int STORE, int KIND, typename R>
+__device__ __forceinline__ void finish_cell(R (&g)[Q], const Par<R> &P, const R *rates, uint32_t cell,
+                                            uint32_t wm, uint32_t off, const typename Store<STORE>::T *fs,
+                                            typename Store<STORE>::T *fd, const R *linkc,
+                                            typename Store<STORE>::T *linkB, int reduce, unsigned *status,
+                                            R &rd, R &rx, R &ry, R &rz)
+{
+    using S = Store<STORE>;
+    using T = typename S::T;
+    const uint32_t KS = P.ks;
+    if (wm) {  // walls: the solid sources read for these directions held 0
+#pragma unroll
+        for (int k = 1; k < Q; ++k) {
+            if (!((wm >> k) & 1u)) continue;
+            const int kb = opp(k);
+            // own post-collision g~_kbar(x)
+            R C;
+            if constexpr (KIND == KIND_AB) C = S::load(fs + ((uint32_t)kb * KS + cell), P.isc);
+            else C = S::load(fs + ((uint32_t)k * KS + cell), P.isc);
+            R v = C;
+            if (P.wall == 1) {
+                const uint32_t l = off + __popc(wm & ((1u << k) - 1u));
+                const R cq = linkc[l];
+                if (cq != R(0)) {
+                    R B;  // own post-collision g~_k(x)
+                    if constexpr (KIND == KIND_AB) B = S::load(fs + ((uint32_t)k * KS + cell), P.isc);
+                    else B = S::load(linkB + l, P.isc);
+                    v = cq * (g[kb] - B) + C;
+                }
+            }
+            g[k] = v;
+        }
+    }
 
+    R drho, ux, uy, uz;
+    moments(g, P.irho0, drho, ux, uy, uz);
+    if (reduce) {
+        rd = drho;
+        rx = ux;
+        ry = uy;
+        rz = uz;
+        const R uu = ux * ux + uy * uy + uz * uz;
+        if (!(uu < R(0.09)) || !(drho == drho)) atomicOr(status, STATUS_DIVERGED);
+    }
+
+    collide<COLL, R>(g, P, rates, drho, ux, uy, uz);
+
+    if constexpr (KIND == KIND_AA_PULL) {
+        const Coord co = coord_of(P, cell);
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const T v = S::pack(g[k], P.sc);
+            // push to x + e_k, or bounce into the own slot kbar when x + e_k is solid
+            if ((wm >> opp(k)) & 1u) fd[(uint32_t)opp(k) * KS + cell] = v;
+            else fd[(uint32_t)k * KS + co.push(k)] = v;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const T v = S::pack(g[k], P.sc);
+            if constexpr (KIND == KIND_AB) fd[(uint32_t)k * KS + cell] = v;
+            else fd[(uint32_t)opp(k) * KS + cell] = v;
+        }
+    }
+    if constexpr (KIND != KIND_AB) {
+        if (wm && P.wall == 1) {
+#pragma unroll
+            for (int k = 1; k < Q; ++k) {
+                if (!((wm >> k) & 1u)) continue;
+                linkB[off + __popc(wm & ((1u << k) - 1u))] = S::pack(g[k], P.sc);
+            }
+        }
+    }
+}
+
+// The fused step.  One block per tile: kStepWarps warps, each taking kSegsPerWarp
+// consecutive entries of the instance's active-segment list.  A warp first issues the
+// pulls of all its segments, then finishes them one after the other, so the loads of one
+// overlap the collision of the other.  flip selects the A-B buffer pair (src = f[phase ^
+// flip]); reduce != 0 makes every tile write its FP64 partial sums (drho, u_x, u_y, u_z)
+// and flags diverged cells in status[instance].
 template <int COLL, int STORE, int KIND>
-__global__ void __launch_bounds__(256, step_min_blocks<STORE, KIND>()) step_kernel(const InstanceDev *__restrict__ table,
-                                                   const TileDev *__restrict__ chunks, int nchunks, int chunk_segs,
-                                                   int flip, int reduce, unsigned *__restrict__ status,
-                                                   unsigned *__restrict__ sched)
+__global__ void __launch_bounds__(kStepWarps * 32, step_min_blocks<STORE, KIND>())
+    step_kernel(const InstanceDev *__restrict__ table, const TileDev *__restrict__ tiles, int ntiles, int flip,
+                int reduce, unsigned *__restrict__ status)
 {
     using S = Store<STORE>;
     using T = typename S::T;
     using R = typename S::R;
-    __shared__ double acc_s[kStepWarps][4];  // a warp's FP64 partial sums of its current chunk
+    constexpr int NS = kSegsPerWarp;
+    __shared__ double red[kStepWarps][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-    while (true) {
-        int c = 0;
-        if (lane == 0) c = (int)atomicAdd(&sched[0], 1u);
-        c = __shfl_sync(0xffffffffu, c, 0);
-        if (c >= nchunks) break;
-        const TileDev chunk = chunks[c];
-        const InstanceDev &I = table[chunk.inst];
-        const Par<R> P = load_par<R>(I);
-        R rates[Q];
-        if constexpr (COLL == COLL_MRT) {
+    const int t = blockIdx.x;
+    if (t >= ntiles) return;
+    const TileDev tile = tiles[t];
+    const InstanceDev &I = table[tile.inst];
+    const Par<R> P = load_par<R>(I);
+    R rates[Q];
+    if constexpr (COLL == COLL_MRT) {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) rates[i] = R(I.s[i]) / R(mrt_norm2(i));
-        }
-        const uint32_t e0 = (uint32_t)chunk.seg0;
-        const int n_e = min(chunk_segs, (int)(I.n_active - e0));
-        const uint4 meta_l = lane < n_e ? I.aseg[e0 + lane] : make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
-        const uint32_t *bmask = I.bmask;
-        const uint32_t *boff = I.boff;
-        const R *linkc = reinterpret_cast<const R *>(I.linkc);
-        T *linkB = reinterpret_cast<T *>(I.linkB);
-        const uint32_t KS = P.ks;
-        T *fs;  // state read this step
-        T *fd;  // state written this step
-        if constexpr (KIND == KIND_AB) {
-            const int cur = I.phase ^ flip;
-            fs = reinterpret_cast<T *>(cur ? I.f1 : I.f0);
-            fd = reinterpret_cast<T *>(cur ? I.f0 : I.f1);
-        } else {
-            fs = fd = reinterpret_cast<T *>(I.f0);
-        }
-        if (reduce && lane < 4) acc_s[warp][lane] = 0.0;
-        __syncwarp();
-
-#pragma unroll 1
-        for (int i = 0; i < n_e; ++i) {
-            const uint32_t m_solid = __shfl_sync(0xffffffffu, meta_l.x, i);
-            const uint32_t m_bnd = __shfl_sync(0xffffffffu, meta_l.y, i);
-            const uint32_t m_base = __shfl_sync(0xffffffffu, meta_l.z, i);
-            const uint32_t m_seg = __shfl_sync(0xffffffffu, meta_l.w, i);
-            R rd = R(0), rx = R(0), ry = R(0), rz = R(0);  // moments for the reduction
-            if (!((m_solid >> lane) & 1u)) {
-                const uint32_t cell = m_seg * 32u + lane;
-                const Coord co = coord_of(P, cell);
-
-                // pull (unconditional), then the pressure shift of x-crossing pulls
-                R g[Q];
-#pragma unroll
-                for (int k = 0; k < Q; ++k) {
-                    uint32_t idx;
-                    if constexpr (KIND == KIND_AA_LOCAL) idx = (uint32_t)k * KS + cell;
-                    else if constexpr (KIND == KIND_AA_PULL) idx = (uint32_t)opp(k) * KS + co.pull(k);
-                    else idx = (uint32_t)k * KS + co.pull(k);
-                    g[k] = S::load(fs + idx, P.isc);
-                }
-                if (co.x == 0) {
-#pragma unroll
-                    for (int k = 0; k < Q; ++k)
-                        if (ex(k) == 1) g[k] += R(weight(k)) * P.dshift;
-                }
-                if (co.x == P.nx - 1) {
-#pragma unroll
-                    for (int k = 0; k < Q; ++k)
-                        if (ex(k) == -1) g[k] -= R(weight(k)) * P.dshift;
-                }
-
-                // walls (only lanes of boundary cells; the solid sources read above hold 0)
-                uint32_t wm = 0u, off = 0u;
-                if ((m_bnd >> lane) & 1u) {
-                    const uint32_t b = m_base + __popc(m_bnd & ((1u << lane) - 1u));
-                    wm = bmask[b];
-                    off = boff[b];
-#pragma unroll
-                    for (int k = 1; k < Q; ++k) {
-                        if (!((wm >> k) & 1u)) continue;
-                        const int kb = opp(k);
-                        // own post-collision g~_kbar(x)
-                        R C;
-                        if constexpr (KIND == KIND_AB) C = S::load(fs + ((uint32_t)kb * KS + cell), P.isc);
-                        else C = S::load(fs + ((uint32_t)k * KS + cell), P.isc);
-                        R v = C;
-                        if (P.wall == 1) {
-                            const uint32_t l = off + __popc(wm & ((1u << k) - 1u));
-                            const R cq = linkc[l];
-                            if (cq != R(0)) {
-                                R B;  // own post-collision g~_k(x)
-                                if constexpr (KIND == KIND_AB) B = S::load(fs + ((uint32_t)k * KS + cell), P.isc);
-                                else B = S::load(linkB + l, P.isc);
-                                v = cq * (g[kb] - B) + C;
-                            }
-                        }
-                        g[k] = v;
-                    }
-                }
-
-                R drho, ux, uy, uz;
-                moments(g, P.irho0, drho, ux, uy, uz);
-                if (reduce) {
-                    rd = drho;
-                    rx = ux;
-                    ry = uy;
-                    rz = uz;
-                    const R uu = ux * ux + uy * uy + uz * uz;
-                    if (!(uu < R(0.09)) || !(drho == drho)) atomicOr(status + chunk.inst, STATUS_DIVERGED);
-                }
-
-                collide<COLL, R>(g, P, rates, drho, ux, uy, uz);
-
-#pragma unroll
-                for (int k = 0; k < Q; ++k) {
-                    const T v = S::pack(g[k], P.sc);
-                    if constexpr (KIND == KIND_AB) {
-                        fd[(uint32_t)k * KS + cell] = v;
-                    } else if constexpr (KIND == KIND_AA_LOCAL) {
-                        fd[(uint32_t)opp(k) * KS + cell] = v;
-                    } else {
-                        // push to x + e_k, or bounce into the own slot kbar when x + e_k is solid
-                        if ((wm >> opp(k)) & 1u) fd[(uint32_t)opp(k) * KS + cell] = v;
-                        else fd[(uint32_t)k * KS + co.push(k)] = v;
-                    }
-                }
-                if constexpr (KIND != KIND_AB) {
-                    if (wm && P.wall == 1) {
-#pragma unroll
-                        for (int k = 1; k < Q; ++k) {
-                            if (!((wm >> k) & 1u)) continue;
-                            linkB[off + __popc(wm & ((1u << k) - 1u))] = S::pack(g[k], P.sc);
-                        }
-                    }
-                }
-            }
-            if (reduce) {  // deterministic: fixed shuffle tree per segment, segments in order
-                const double s0 = warp_sum((double)rd), s1 = warp_sum((double)rx);
-                const double s2 = warp_sum((double)ry), s3 = warp_sum((double)rz);
-                if (lane == 0) {
-                    acc_s[warp][0] += s0;
-                    acc_s[warp][1] += s1;
-                    acc_s[warp][2] += s2;
-                    acc_s[warp][3] += s3;
-                }
-            }
-        }
-        if (reduce && lane == 0) {
-            double *pp = I.partials + (size_t)chunk.local * 4;
-            for (int d = 0; d < 4; ++d) pp[d] = acc_s[warp][d];
-        }
-        __syncwarp();
+        for (int i = 0; i < Q; ++i) rates[i] = R(I.s[i]) / R(mrt_norm2(i));
+    }
+    const uint32_t KS = P.ks;
+    T *fs;  // state read this step
+    T *fd;  // state written this step
+    if constexpr (KIND == KIND_AB) {
+        const int cur = I.phase ^ flip;
+        fs = reinterpret_cast<T *>(cur ? I.f1 : I.f0);
+        fd = reinterpret_cast<T *>(cur ? I.f0 : I.f1);
+    } else {
+        fs = fd = reinterpret_cast<T *>(I.f0);
     }
 
-    // the last warp to run out of chunks resets the work counter for the next launch
-    if (lane == 0) {
-        __threadfence();
-        const unsigned warps = gridDim.x * (blockDim.x >> 5);
-        const unsigned done = atomicAdd(&sched[1], 1u);
-        if (done == warps - 1) {
-            sched[0] = 0u;
-            sched[1] = 0u;
-            __threadfence();
+    // descriptors of this warp's segments (entries past the list are all solid)
+    const uint32_t e0 = (uint32_t)tile.seg0 + (uint32_t)(warp * NS);
+    uint4 meta[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+        meta[s] = e0 + s < I.n_active ? I.aseg[e0 + s] : make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+
+    // issue every pull of the warp's cells (unconditional: solid sources hold 0)
+    R g[NS][Q];
+    uint32_t cell[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        cell[s] = meta[s].w * 32u + lane;
+        if ((meta[s].x >> lane) & 1u) continue;
+        const Coord co = coord_of(P, cell[s]);
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            uint32_t idx;
+            if constexpr (KIND == KIND_AA_LOCAL) idx = (uint32_t)k * KS + cell[s];
+            else if constexpr (KIND == KIND_AA_PULL) idx = (uint32_t)opp(k) * KS + co.pull(k);
+            else idx = (uint32_t)k * KS + co.pull(k);
+            g[s][k] = S::load(fs + idx, P.isc);
+        }
+        // pressure shift of pulls that cross the x boundary
+        if (co.x == 0) {
+#pragma unroll
+            for (int k = 0; k < Q; ++k)
+                if (ex(k) == 1) g[s][k] += R(weight(k)) * P.dshift;
+        }
+        if (co.x == P.nx - 1) {
+#pragma unroll
+            for (int k = 0; k < Q; ++k)
+                if (ex(k) == -1) g[s][k] -= R(weight(k)) * P.dshift;
+        }
+    }
+
+    R rd = R(0), rx = R(0), ry = R(0), rz = R(0);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        if ((meta[s].x >> lane) & 1u) continue;
+        uint32_t wm = 0u, off = 0u;
+        if ((meta[s].y >> lane) & 1u) {
+            const uint32_t b = meta[s].z + __popc(meta[s].y & ((1u << lane) - 1u));
+            wm = I.bmask[b];
+            off = I.boff[b];
+        }
+        finish_cell<COLL, STORE, KIND, R>(g[s], P, rates, cell[s], wm, off, fs, fd,
+                                          reinterpret_cast<const R *>(I.linkc), reinterpret_cast<T *>(I.linkB),
+                                          reduce, status + tile.inst, rd, rx, ry, rz);
+        if (reduce) {  // lane sums over the warp's segments, in order
+            a0 += (double)rd;
+            a1 += (double)rx;
+            a2 += (double)ry;
+            a3 += (double)rz;
+        }
+    }
+
+    if (reduce) {  // deterministic: fixed shuffle tree, then the block's warps in order
+        a0 = warp_sum(a0);
+        a1 = warp_sum(a1);
+        a2 = warp_sum(a2);
+        a3 = warp_sum(a3);
+        if (lane == 0) {
+            red[warp][0] = a0;
+            red[warp][1] = a1;
+            red[warp][2] = a2;
+            red[warp][3] = a3;
+        }
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            double sum = 0.0;
+            for (int w = 0; w < kStepWarps; ++w) sum += red[w][threadIdx.x];
+            I.partials[(size_t)tile.local * 4 + threadIdx.x] = sum;
         }
     }
 }

@@ -66,7 +66,7 @@ int main(void) {
 
 @pytest.mark.parametrize("bad", [
     dict(tau=0.5), dict(tau=float("nan")), dict(nx=0), dict(collision=7), dict(wall=2), dict(storage=9),
-    dict(layout=3), dict(block_cells=100), dict(block_cells=64), dict(block_cells=2048), dict(perturb_u=0.5),
+    dict(layout=3), dict(block_cells=100), dict(block_cells=64), dict(block_cells=2048), dict(block_cells=512), dict(perturb_u=0.5),
     dict(spheres=[[1, 1, 1, -2.0]]), dict(dev_scale_log2=99), dict(magic_lambda=-1.0),
 ])
 def test_invalid_descriptor_rejected_before_gpu(L, bad):

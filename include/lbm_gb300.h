@@ -192,6 +192,25 @@ LBM_API lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *out);
 /* Wait for all queued work of the context. */
 LBM_API lbm_status lbm_synchronize(lbm_ctx *ctx);
 
+/* Moment sums without any allocation, for callers that cannot let a library allocate
+ * device memory (every byte owned by a memory pool, no allocation allowed after start-up,
+ * or work about to be captured into a CUDA graph).  The paper has no counterpart; it is
+ * lbm_moment_sums for a caller-owned field and needs no context.
+ *   f_dev     device, FP64 populations f_k (not deviations), [19][n_cells] in the
+ *             direction order above; entries of solid cells are ignored
+ *   solid_dev device, n_cells flags (1 = solid), or NULL when every cell is fluid
+ *   sums_dev  device, 4 doubles out: sums over fluid cells of (rho - rho0, u_x, u_y, u_z),
+ *             u = rho0^-1 sum e_k f_k, reduced in a fixed order
+ *   cuda_stream  stream the two kernels are queued on (NULL = legacy default stream)
+ * Calls no cudaMalloc or cudaFree: block sums go to a fixed 256 KiB scratch array inside
+ * the library, held by every GPU that loads it.  n_cells is limited to 268,435,456
+ * (8192 blocks of 32768 cells); larger fields return LBM_ERR_ARG.  The first call on
+ * each device looks up the scratch address (cudaGetSymbolAddress) and should come before
+ * any stream capture.  Calls share the scratch: calls that overlap on the GPU race.
+ * Returns without waiting for the kernels. */
+LBM_API lbm_status lbm_moment_sums_f64_noalloc(const double *f_dev, const uint8_t *solid_dev, int64_t n_cells,
+                                               double rho0, double *sums_dev, void *cuda_stream);
+
 /* Checkpoint: header, parameters, step count, AA parity and the stored populations in
  * their native format.  lbm_load needs a context created from the same descriptor. */
 LBM_API lbm_status lbm_save(lbm_ctx *ctx, const char *path);

@@ -121,6 +121,7 @@ PROTOTYPES = {
     "lbm_get_wall_distances": (_st, [_vp, _dp]),
     "lbm_get_info": (_st, [_vp, ctypes.POINTER(Info)]),
     "lbm_synchronize": (_st, [_vp]),
+    "lbm_moment_sums_f64_noalloc": (_st, [_vp, _vp, ctypes.c_int64, ctypes.c_double, _vp, _vp]),
     "lbm_save": (_st, [_vp, ctypes.c_char_p]),
     "lbm_load": (_st, [_vp, ctypes.c_char_p]),
     "lbm_delta_rho_for_re_p": (ctypes.c_double, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -433,6 +434,15 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def moment_sums_f64_noalloc(f_dev_ptr: int, solid_dev_ptr: int | None, n_cells: int, rho0: float,
+                            sums_dev_ptr: int, stream=None) -> None:
+    """Moment sums of a device FP64 population field without any allocation inside the
+    library (lbm_moment_sums_f64_noalloc); pointers are device addresses (e.g.
+    tensor.data_ptr()).  Queued on the stream; does not wait."""
+    check(lib().lbm_moment_sums_f64_noalloc(f_dev_ptr, solid_dev_ptr, int(n_cells), float(rho0), sums_dev_ptr,
+                                            _stream_handle(stream)), "lbm_moment_sums_f64_noalloc")
 
 
 def delta_rho_for_re_p(re_p, tau, d_p, lx, K_D, C_F=0.0, rho0=1.0) -> float:

@@ -114,6 +114,55 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def kernel_source_sha() -> str:
+    """Short hash of the step-kernel sources, recorded beside the ncu counters."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1508_02960_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in ("lbm_step.cuh", "lbm_device.cuh"):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per step-kernel launch from the committed ncu summary of this workload,
+    or None when there is none or the kernel sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"step_kernel_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    with open(path) as fh:
+        for ln in fh:
+            if ":" in ln and ln.split(":")[0].strip() in ("kernel_source_sha", "dram_bytes_per_launch"):
+                k, v = ln.split(":", 1)
+                fields[k.strip()] = v.strip()
+    if fields.get("kernel_source_sha") != kernel_source_sha():
+        return None
+    try:
+        return int(fields["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def run_profile(args):
+    """Build the workload's context and run a few steps (the command ncu wraps)."""
+    import torch
+
+    from paper_1508_02960_gb300 import capi
+    from paper_1508_02960_gb300 import inputs as I
+    L, r, storage, layout, coll, wall, tau, dr = WORKLOADS[args.workload]
+    g = I.centred_sphere(L, r)
+    ctx = capi.Context(spheres=g.spheres, shape=g.shape, tau=tau, delta_rho=dr, magic_lambda=3 / 16,
+                       collision=getattr(capi, coll), wall=getattr(capi, wall), storage=getattr(capi, storage),
+                       layout=getattr(capi, "LAYOUT_" + layout), stream=torch.cuda.current_stream())
+    ctx.init_equilibrium()
+    ctx.step(args.profile_steps)
+    print(json.dumps({"workload": args.workload, "steps": args.profile_steps,
+                      "U_sup": ctx.observables()["U_sup"]}))
+    ctx.close()
+
+
 def dist_setup(n_gpus: int):
     import torch
     rank, world, local = 0, 1, 0
@@ -298,11 +347,7 @@ def run_gpu(args, rank, world, local):
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     e2e_value = sum_over_ranks(updates, world) / e2e_s / 1e6
 
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", f"{args.workload}.traffic.json")
-    if os.path.exists(prof):
-        with open(prof) as fh:
-            traffic = json.load(fh).get("dram_bytes_per_launch")
+    traffic = profiled_traffic(args.workload)
 
     if rank == 0:
         cpu = None
@@ -346,7 +391,12 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--block", type=int, default=0, help="cells per thread block (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="only build the workload and run this many steps (for ncu), no timing")
     args = ap.parse_args()
+    if args.profile_steps > 0:
+        run_profile(args)
+        return
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", 0))
         run_reference(args, rank, int(os.environ.get("WORLD_SIZE", 1)))

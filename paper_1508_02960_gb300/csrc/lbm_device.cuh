@@ -208,7 +208,7 @@ enum { KIND_AB = 0, KIND_AA_PULL = 1, KIND_AA_LOCAL = 2 };
 // Step-kernel tiling: one block of kStepWarps warps per tile; each warp takes
 // kSegsPerWarp consecutive entries of the active-segment list.
 constexpr int kStepWarps = 4;
-constexpr int kSegsPerWarp = 2;
+constexpr int kSegsPerWarp = 1;
 constexpr int kTileSegs = kStepWarps * kSegsPerWarp;
 enum { COLL_SRT = 0, COLL_TRT = 1, COLL_MRT = 2 };
 

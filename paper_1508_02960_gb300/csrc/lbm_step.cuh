@@ -100,7 +100,7 @@ template <typename R> __device__ __forceinline__ Coord coord_of(const Par<R> &p,
 }
 
 // Blocks per multiprocessor the register allocation is sized for.
-template <int STORE, int KIND> constexpr int step_min_blocks() { return STORE == ST_F64 ? 2 : 6; }
+template <int STORE, int KIND> constexpr int step_min_blocks() { return STORE == ST_F64 ? 2 : 8; }
 
 // Moments of the incoming populations (Eq. Macro), in deviation form.
 template <typename R>

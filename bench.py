@@ -163,6 +163,132 @@ def run_profile(args):
     ctx.close()
 
 
+def _scaled_pack(L: int):
+    """The 40-sphere random pack of the 256^3 precision workload, scaled to an L^3 box."""
+    from paper_1508_02960_gb300 import inputs as I
+    g = I.random_pack(256, 40, 18.0, 30.0, 20150811)
+    return I.Geometry(L, L, L, g.spheres * (L / 256.0))
+
+
+def study_precision(args):
+    """Error of the reduced storage formats in K (Re_p ~ 1) and Forchheimer beta (Re_p ~ 100)
+    against FP64 storage on the same geometry, TRT + CLI, steady state (|dU|/U < tol)."""
+    import numpy as np
+    import torch
+
+    from paper_1508_02960_gb300 import capi
+    from paper_1508_02960_gb300 import inputs as I
+    L = args.study_size
+    geoms = {"sphere": I.centred_sphere(L, 120.0 * L / 256), "pack40": _scaled_pack(L)}
+    tau, tol, check, cap = 0.6, 1e-7, 200, args.study_max_steps
+    out = []
+    for gname, g in geoms.items():
+        def run(storage, dr):
+            ctx = capi.Context(spheres=g.spheres, shape=g.shape, tau=tau, delta_rho=dr, collision=capi.TRT,
+                               wall=capi.CLI, storage=getattr(capi, storage), stream=torch.cuda.current_stream())
+            ctx.init_equilibrium()
+            t0 = time.perf_counter()
+            st, steps = ctx.run_to_convergence(tol, check, cap)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            o = ctx.observables()
+            nf = ctx.info()["n_fluid"]
+            ctx.close()
+            return o, steps, st, nf * steps / dt / 1e6
+        # Darcy permeability in FP64 at a Stokes-regime pressure drop
+        o, _, _, _ = run("F64", 1e-6)
+        K_D = o["K"]
+        d_p = g.d_p
+        rows = {}
+        for re_p in (1.0, 100.0):
+            dr = capi.delta_rho_for_re_p(re_p, tau, d_p, L, K_D, 0.0078 if re_p > 1 else 0.0)
+            ref = None
+            for fmt in ("F64", "F32", "F16DEV", "BF16DEV"):
+                o, steps, st, mlups = run(fmt, dr)
+                rec = {"geometry": gname, "L": L, "re_p_target": re_p, "format": fmt, "steps": steps,
+                       "status": capi.STATUS.get(st, st), "Re_p": o["Re_p"], "K": o["K"], "MLUPS_incl_host": mlups}
+                if fmt == "F64":
+                    ref = o
+                rec["K_rel_err"] = abs(o["K"] / ref["K"] - 1.0)
+                rows[(re_p, fmt)] = (o, rec)
+                out.append(rec)
+        # Forchheimer beta at Re_p ~ 100 with each format's own K_D (Re_p ~ 1 run)
+        for fmt in ("F64", "F32", "F16DEV", "BF16DEV"):
+            o1, _ = rows[(1.0, fmt)]
+            o100, rec = rows[(100.0, fmt)]
+            mu = (tau - 0.5) / 3.0
+            U = o100["U_sup"]
+            gradP = capi.delta_rho_for_re_p(100.0, tau, d_p, L, K_D, 0.0078) / 3.0 / L
+            beta = (gradP - mu * U / o1["K"]) / (U * U)
+            rec["beta"] = beta
+        b64 = rows[(100.0, "F64")][1]["beta"]
+        for fmt in ("F32", "F16DEV", "BF16DEV"):
+            rec = rows[(100.0, fmt)][1]
+            rec["beta_rel_err"] = abs(rec["beta"] / b64 - 1.0)
+    for rec in out:
+        print(json.dumps({"study": "precision", **rec}), flush=True)
+
+
+def study_sweep(args):
+    """The batched Reynolds-number / porosity sweep served through the memory-admitted
+    request loop: 64 seeded simple-cubic cells, FP16-deviation storage."""
+    import numpy as np
+    import torch
+
+    from paper_1508_02960_gb300 import capi
+    from paper_1508_02960_gb300 import inputs as I
+    pts = I.sweep_points(args.sweep_points)
+    # Darcy permeability estimate per point: a short FP32 run at a Stokes pressure drop
+    descs, keep = [], []
+    for p in pts:
+        g = p.geometry
+        d, k = capi.make_desc(spheres=g.spheres, shape=g.shape, tau=p.tau, delta_rho=1e-6, collision=capi.TRT,
+                              wall=capi.CLI, storage=capi.F32, magic_lambda=p.magic_lambda)
+        descs.append(d)
+        keep.append(k)
+    b = capi.Batch(descs)
+    b.init_equilibrium()
+    b.step(2000)
+    K_est = [b.observables(i)["K"] for i in range(len(pts))]
+    b.close()
+    sub = []
+    for p, K in zip(pts, K_est):
+        g = p.geometry
+        dr = capi.delta_rho_for_re_p(p.re_p, p.tau, g.d_p, p.L, K, 0.0078)
+        d, k = capi.make_desc(spheres=g.spheres, shape=g.shape, tau=p.tau, delta_rho=dr, collision=capi.TRT,
+                              wall=capi.CLI, storage=capi.F16DEV, magic_lambda=p.magic_lambda)
+        sub.append((d, k, p))
+    total_bytes = sum(2 * 19 * 2 * p.L ** 3 for p in pts)
+    srv = capi.Server(hbm_budget_bytes=int(args.sweep_budget_gb * 2 ** 30), check_interval=200, max_resident=256)
+    t0 = time.perf_counter()
+    ids = [srv.submit(d, 1e-6, args.study_max_steps) for d, _, _ in sub]
+    srv.drain(3600.0)
+    wall = time.perf_counter() - t0
+    res = [srv.poll(i) for i in ids]
+    stats = srv.stats()
+    srv.close()
+    lat = np.array([r[2] for r in res])
+    conv = sum(1 for r in res if r[0] == capi.OK)
+    # the same point alone: identical result expected
+    checks = []
+    for j in (0, len(sub) // 2, len(sub) - 1):
+        d, _, p = sub[j]
+        ctx = capi.Context(desc=d)
+        ctx.init_equilibrium()
+        st, steps = ctx.run_to_convergence(1e-6, 200, args.study_max_steps)
+        o = ctx.observables()
+        ctx.close()
+        checks.append({"point": j, "L": p.L, "steps_alone": steps, "steps_mix": res[j][1]["steps"],
+                       "U_alone": o["U_sup"], "U_mix": res[j][1]["U_sup"],
+                       "identical": o["U_sup"] == res[j][1]["U_sup"] and steps == res[j][1]["steps"]})
+    print(json.dumps({"study": "sweep", "points": len(pts), "cells_total": int(sum(p.L ** 3 for p in pts)),
+                      "population_bytes_total": total_bytes, "budget_gb": args.sweep_budget_gb,
+                      "wall_s": wall, "aggregate_mlups": stats["mlups"], "busy_s": stats["busy_seconds"],
+                      "fluid_updates": stats["fluid_updates"], "converged": conv, "capped": len(pts) - conv,
+                      "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+                      "kernel_launches": stats["kernel_launches"], "alone_vs_mix": checks}), flush=True)
+
+
 def dist_setup(n_gpus: int):
     import torch
     rank, world, local = 0, 1, 0
@@ -183,24 +309,18 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x: float, world: int) -> float:
+def aggregate_over_ranks(units: float, seconds: float, world: int, device: str = "cuda"):
+    """Whole-job figures of independent replicas: (sum of units over ranks, max of the timed
+    seconds over ranks).  world <= 1: the local values."""
     if world <= 1:
-        return x
+        return units, seconds
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def sum_over_ranks(x: float, world: int) -> float:
-    if world <= 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([units], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    m = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return float(t.item()), float(m.item())
 
 
 def cpu_baseline(workload: str, target_s: float = 12.0) -> dict:
@@ -319,9 +439,10 @@ def run_gpu(args, rank, world, local):
     launches = ctx.info()["kernel_launches"] - launches0
     total_ms = t_start.elapsed_time(t_end)
     graph_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = max_over_ranks(total_ms, world)
     updates = float(nf) * CHECK_INTERVAL * args.steps
-    value = sum_over_ranks(updates, world) / (total_ms * 1e-3) / 1e6
+    all_updates, total_s = aggregate_over_ranks(updates, total_ms * 1e-3, world)
+    total_ms = total_s * 1e3
+    value = all_updates / total_s / 1e6
 
     # per-launch duration of the step kernel inside the timed region
     kernel_ms = statistics.mean(graph_ms) / CHECK_INTERVAL
@@ -344,8 +465,8 @@ def run_gpu(args, rank, world, local):
         ctx.step(CHECK_INTERVAL)
         ctx.observables()                     # D2H of the step's result
     torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
-    e2e_value = sum_over_ranks(updates, world) / e2e_s / 1e6
+    all_updates, e2e_s = aggregate_over_ranks(updates, time.perf_counter() - t0, world)
+    e2e_value = all_updates / e2e_s / 1e6
 
     traffic = profiled_traffic(args.workload)
 
@@ -393,9 +514,21 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only build the workload and run this many steps (for ncu), no timing")
+    ap.add_argument("--study", choices=["precision", "sweep"], default=None,
+                    help="run a study instead of the benchmark (JSON lines)")
+    ap.add_argument("--study-size", type=int, default=64)
+    ap.add_argument("--study-max-steps", type=int, default=60000)
+    ap.add_argument("--sweep-points", type=int, default=64)
+    ap.add_argument("--sweep-budget-gb", type=float, default=6.0)
     args = ap.parse_args()
     if args.profile_steps > 0:
         run_profile(args)
+        return
+    if args.study == "precision":
+        study_precision(args)
+        return
+    if args.study == "sweep":
+        study_sweep(args)
         return
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", 0))

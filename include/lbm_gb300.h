@@ -53,7 +53,7 @@ typedef enum {
     LBM_ERR_ARG = -1,           /* invalid argument or descriptor */
     LBM_ERR_NO_MEMORY = -2,     /* device or host allocation failed, or over budget */
     LBM_ERR_CUDA = -3,          /* a CUDA runtime call failed */
-    LBM_ERR_DIVERGED = -4,      /* non-finite moments or |u| > 0.3 seen by a reduction */
+    LBM_ERR_DIVERGED = -4,      /* non-finite moments or |u| > 1 seen by a reduction */
     LBM_ERR_NOT_CONVERGED = -5, /* max_steps reached before the convergence test passed */
     LBM_ERR_TIMEOUT = -6,       /* a bounded wait ran out */
     LBM_ERR_STATE = -7,         /* call not valid in the object's current state */

@@ -160,7 +160,7 @@ lbm_status lbm_run_to_convergence(lbm_ctx *ctx, double tol, int64_t check_interv
         st = ctx->b.fetch_sums();
         if (st != LBM_OK) return st;
         if (in.status & STATUS_DIVERGED) {
-            result = fail(LBM_ERR_DIVERGED, "diverged (non-finite moments or |u| > 0.3)");
+            result = fail(LBM_ERR_DIVERGED, "diverged (non-finite moments or |u| > 1)");
             break;
         }
         const double U = in.sums[1] / (double)in.geo.ncells;

@@ -89,6 +89,13 @@ __host__ __device__ constexpr int mrt_norm2(int i)
 // ------------------------------------------------------------------------------------
 // Storage formats.  Every format stores the deviation g_k = f_k - w_k rho0; R is the
 // arithmetic type of the collision.
+//
+// The 16-bit formats store with stochastic rounding: a per-step change of a population
+// that is below half a unit of the stored format would otherwise round to no change at
+// all, and a run started from rest then stops short of its steady state.  The random bits
+// come from a multiplicative hash of the cell, the direction and the value itself, so a
+// run is reproducible, a true fixed point stays fixed, and the rounding is unbiased over
+// the changing values of a flow that is still evolving.
 // ------------------------------------------------------------------------------------
 enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
 
@@ -99,6 +106,7 @@ template <> struct Store<ST_F64> {
     __device__ static R load(const T *p, float) { return __ldg(p); }
     __device__ static R cvt(T v, float) { return v; }
     __device__ static T pack(R v, float) { return v; }
+    __device__ static T pack_sr(R v, float, uint32_t) { return v; }
 };
 template <> struct Store<ST_F32> {
     using T = float;
@@ -106,6 +114,7 @@ template <> struct Store<ST_F32> {
     __device__ static R load(const T *p, float) { return __ldg(p); }
     __device__ static R cvt(T v, float) { return v; }
     __device__ static T pack(R v, float) { return v; }
+    __device__ static T pack_sr(R v, float, uint32_t) { return v; }
 };
 // FP16 deviation with a power-of-two scale 2^s: stored = g * 2^s (exact scaling).
 template <> struct Store<ST_F16> {
@@ -114,6 +123,12 @@ template <> struct Store<ST_F16> {
     __device__ static R load(const T *p, float inv_scale) { return __half2float(__ldg(p)) * inv_scale; }
     __device__ static R cvt(T v, float inv_scale) { return __half2float(v) * inv_scale; }
     __device__ static T pack(R v, float scale) { return __float2half_rn(v * scale); }
+    // stochastic rounding: 13 random bits added below the FP16 mantissa, then truncation
+    __device__ static T pack_sr(R v, float scale, uint32_t rnd)
+    {
+        const float x = v * scale;
+        return __float2half_rz(__uint_as_float(__float_as_uint(x) + (rnd >> 19)));
+    }
 };
 template <> struct Store<ST_BF16> {
     using T = __nv_bfloat16;
@@ -121,7 +136,30 @@ template <> struct Store<ST_BF16> {
     __device__ static R load(const T *p, float) { return __bfloat162float(__ldg(p)); }
     __device__ static R cvt(T v, float) { return __bfloat162float(v); }
     __device__ static T pack(R v, float) { return __float2bfloat16_rn(v); }
+    // stochastic rounding: 16 random bits added below the BF16 mantissa, then truncation
+    __device__ static T pack_sr(R v, float, uint32_t rnd)
+    {
+        const uint32_t b = __float_as_uint(v) + (rnd >> 16);
+        return __ushort_as_bfloat16((unsigned short)(b >> 16));
+    }
 };
+
+// Random bits for the stochastic rounding of population k of a cell: cell_hash mixes the
+// cell index once (SplitMix-style finaliser), then one multiply per direction folds in the
+// value's own bits.
+__device__ __forceinline__ uint32_t cell_hash(uint32_t cell)
+{
+    uint32_t h = cell * 0x9E3779B9u;
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    return h ^ (h >> 16);
+}
+__device__ __forceinline__ uint32_t round_bits(uint32_t h, int k, float v)
+{
+    return (h ^ __float_as_uint(v)) * (0x9E3779B1u + 0x6A09E666u * (uint32_t)k);
+}
 
 inline size_t storage_bytes(int s) { return s == ST_F64 ? 8 : (s == ST_F32 ? 4 : 2); }
 

@@ -228,26 +228,31 @@ __device__ __forceinline__ void finish_cell(R (&g)[Q], const Par<R> &P, const R 
         ry = uy;
         rz = uz;
         const R uu = ux * ux + uy * uy + uz * uz;
-        if (!(uu < R(0.09)) || !(drho == drho)) atomicOr(status, STATUS_DIVERGED);
+        if (!(uu < R(1)) || !(drho == drho)) atomicOr(status, STATUS_DIVERGED);
     }
 
     collide<COLL, R>(g, P, rates, drho, ux, uy, uz);
 
+    // 16-bit formats round stochastically (see Store); wider formats round to nearest
+    constexpr bool sr = sizeof(T) == 2;
+    const uint32_t h = sr ? cell_hash(cell) : 0u;
+    T packed[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k)
+        packed[k] = sr ? S::pack_sr(g[k], P.sc, round_bits(h, k, float(g[k]))) : S::pack(g[k], P.sc);
     if constexpr (KIND == KIND_AA_PULL) {
         const Coord co = coord_of(P, cell);
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
-            const T v = S::pack(g[k], P.sc);
             // push to x + e_k, or bounce into the own slot kbar when x + e_k is solid
-            if ((wm >> opp(k)) & 1u) fd[(uint32_t)opp(k) * KS + cell] = v;
-            else fd[(uint32_t)k * KS + co.push(k)] = v;
+            if ((wm >> opp(k)) & 1u) fd[(uint32_t)opp(k) * KS + cell] = packed[k];
+            else fd[(uint32_t)k * KS + co.push(k)] = packed[k];
         }
     } else {
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
-            const T v = S::pack(g[k], P.sc);
-            if constexpr (KIND == KIND_AB) fd[(uint32_t)k * KS + cell] = v;
-            else fd[(uint32_t)opp(k) * KS + cell] = v;
+            if constexpr (KIND == KIND_AB) fd[(uint32_t)k * KS + cell] = packed[k];
+            else fd[(uint32_t)opp(k) * KS + cell] = packed[k];
         }
     }
     if constexpr (KIND != KIND_AB) {
@@ -255,7 +260,7 @@ __device__ __forceinline__ void finish_cell(R (&g)[Q], const Par<R> &P, const R 
 #pragma unroll
             for (int k = 1; k < Q; ++k) {
                 if (!((wm >> k) & 1u)) continue;
-                linkB[off + __popc(wm & ((1u << k) - 1u))] = S::pack(g[k], P.sc);
+                linkB[off + __popc(wm & ((1u << k) - 1u))] = packed[k];
             }
         }
     }

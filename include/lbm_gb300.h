@@ -166,6 +166,14 @@ LBM_API lbm_status lbm_step(lbm_ctx *ctx, int64_t n_steps);
 LBM_API lbm_status lbm_run_to_convergence(lbm_ctx *ctx, double tol, int64_t check_interval,
                                   int64_t max_steps, int64_t *steps_done);
 
+/* Time average (Sec. 4: volume-averaged velocity averaged over a period of the developed
+ * flow): advance n_samples * sample_interval steps, reduce the moments after every
+ * sample_interval steps and average them in FP64; *out receives the observables of the
+ * averaged U_sup (K_darcy as in lbm_observables), u_max unused, steps = steps done so far.
+ * Returns LBM_ERR_DIVERGED (with the average so far) when a sample diverged. */
+LBM_API lbm_status lbm_average(lbm_ctx *ctx, int64_t n_samples, int64_t sample_interval, double K_darcy,
+                               lbm_obs *out);
+
 /* Observables of the last step (synchronises the stream).  K_darcy > 0 enables beta,
  * C_F, F_K and Re_K; K_darcy = 0 leaves them NaN.  Returns LBM_ERR_DIVERGED (with *out
  * filled) when the last reduction saw a diverged cell. */

@@ -114,6 +114,7 @@ PROTOTYPES = {
                                      ctypes.POINTER(ctypes.c_int64)]),
     "lbm_observables": (_st, [_vp, ctypes.c_double, ctypes.POINTER(Obs)]),
     "lbm_moment_sums": (_st, [_vp, _dp]),
+    "lbm_average": (_st, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(Obs)]),
     "lbm_get_populations_f64": (_st, [_vp, _dp]),
     "lbm_set_populations_f64": (_st, [_vp, _dp]),
     "lbm_get_velocity_f64": (_st, [_vp, _dp]),
@@ -287,6 +288,16 @@ class Context:
         st = lib().lbm_observables(self._h, float(K_darcy), ctypes.byref(o))
         if st not in (OK, ERR_DIVERGED):
             check(st, "lbm_observables")
+        d = o.as_dict()
+        d["status"] = st
+        return d
+
+    def average(self, n_samples: int, sample_interval: int, K_darcy: float = 0.0) -> dict:
+        """Time-averaged observables over n_samples * sample_interval further steps."""
+        o = Obs()
+        st = lib().lbm_average(self._h, int(n_samples), int(sample_interval), float(K_darcy), ctypes.byref(o))
+        if st not in (OK, ERR_DIVERGED):
+            check(st, "lbm_average")
         d = o.as_dict()
         d["status"] = st
         return d

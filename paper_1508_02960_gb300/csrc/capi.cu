@@ -175,6 +175,36 @@ lbm_status lbm_run_to_convergence(lbm_ctx *ctx, double tol, int64_t check_interv
     return result;
 }
 
+lbm_status lbm_average(lbm_ctx *ctx, int64_t n_samples, int64_t sample_interval, double K_darcy, lbm_obs *out)
+{
+    if (!ctx || !out) return fail(LBM_ERR_ARG, "NULL argument");
+    if (n_samples < 1 || sample_interval < 1) return fail(LBM_ERR_ARG, "n_samples and sample_interval must be >= 1");
+    Instance &in = ctx->b.at(0);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int64_t done = 0;
+    lbm_status result = LBM_OK;
+    for (int64_t i = 0; i < n_samples; ++i) {
+        lbm_status st = ctx->b.step(sample_interval);
+        if (st != LBM_OK) return st;
+        st = ctx->b.fetch_sums();
+        if (st != LBM_OK) return st;
+        for (int d = 0; d < 4; ++d) acc[d] += in.sums[d];
+        ++done;
+        if (in.status & STATUS_DIVERGED) {
+            result = fail(LBM_ERR_DIVERGED, "a sample saw a diverged cell");
+            break;
+        }
+    }
+    double keep[4];
+    for (int d = 0; d < 4; ++d) {
+        keep[d] = in.sums[d];
+        in.sums[d] = acc[d] / (double)done;
+    }
+    compute_obs(in, K_darcy, out);
+    for (int d = 0; d < 4; ++d) in.sums[d] = keep[d];
+    return result;
+}
+
 lbm_status lbm_moment_sums(lbm_ctx *ctx, double *sums)
 {
     if (!ctx || !sums) return fail(LBM_ERR_ARG, "NULL argument");

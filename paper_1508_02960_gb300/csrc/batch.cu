@@ -273,6 +273,12 @@ static void fill_dev(const Instance &in, InstanceDev &D)
     D.seg = in.geo.seg;
     D.aseg = in.geo.aseg;
     D.n_active = (uint32_t)in.geo.n_active;
+    for (int k = 0; k < Q; ++k) {
+        const long long dk = ex(k) + (long long)ey(k) * d.nx + (long long)ez(k) * d.nx * d.ny;  // e_k as an offset
+        const long long arr = d.layout == LBM_LAYOUT_AA ? opp(k) : k;
+        D.pull_off[k] = (uint32_t)(arr * in.ks - dk);
+        D.push_off[k] = (uint32_t)((long long)k * in.ks + dk);
+    }
     D.bmask = in.geo.bmask;
     D.boff = in.geo.boff;
     D.linkc = in.geo.linkc;
@@ -338,6 +344,7 @@ lbm_status Batch::rebuild()
     d_table_ = nullptr;
     d_tiles_ = nullptr;
     d_tile_begin_ = d_tile_count_ = nullptr;
+    h_table_ = table;
     CK(cudaMalloc(&d_table_, sizeof(InstanceDev) * table.size()));
     CK(cudaMemcpy(d_table_, table.data(), sizeof(InstanceDev) * table.size(), cudaMemcpyHostToDevice));
     if (ntiles_ > 0) {
@@ -397,6 +404,7 @@ lbm_status Batch::init_equilibrium(int i)
 struct StepQueue {
     const FormatOps *ops;
     Launch L;
+    const InstanceDev *one;  // single instance: its parameters by value; else NULL
     int collision, layout;
     unsigned *status;
     int n_status;
@@ -418,7 +426,7 @@ static cudaError_t queue_steps(const StepQueue &q, cudaStream_t s, long long n, 
             if (e != cudaSuccess) return e;
         }
         const int kind = q.layout == LBM_LAYOUT_AB ? KIND_AB : (aa == 0 ? KIND_AA_PULL : KIND_AA_LOCAL);
-        cudaError_t e = q.ops->step(q.collision, kind, L, flip, red ? 1 : 0, q.status);
+        cudaError_t e = q.ops->step(q.collision, kind, L, flip, red ? 1 : 0, q.status, q.one);
         if (e != cudaSuccess) return e;
         ++launches;
         if (q.layout == LBM_LAYOUT_AB) flip ^= 1;
@@ -441,7 +449,7 @@ lbm_status Batch::step(long long n)
         if (st != LBM_OK) return st;
     }
     StepQueue q{&ops(), Launch{d_table_, d_tiles_, ntiles_, block_ / 32, grid_, kStepWarps * 32, stream_},
-                collision_, layout_, d_status_,
+                size() == 1 ? &h_table_[0] : nullptr, collision_, layout_, d_status_,
                 size(), d_tile_begin_, d_tile_count_, d_sums_, size()};
     const long long kChunk = 1000;
     long long left = n;

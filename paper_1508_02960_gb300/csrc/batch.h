@@ -78,6 +78,7 @@ private:
     cudaStream_t stream_ = nullptr;   // user stream (launches)
     cudaStream_t cap_ = nullptr;      // private stream for graph capture
     InstanceDev *d_table_ = nullptr;
+    std::vector<InstanceDev> h_table_;  // host copy (the single-instance launch passes it by value)
     TileDev *d_tiles_ = nullptr;
     int *d_tile_begin_ = nullptr, *d_tile_count_ = nullptr;
     double *d_sums_ = nullptr;        // [n][4]

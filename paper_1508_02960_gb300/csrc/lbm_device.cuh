@@ -222,6 +222,10 @@ struct InstanceDev {
     uint32_t n32;            // ncells
     uint32_t ks;             // elements between consecutive direction arrays (>= ncells; 19 ks < 2^32)
     uint32_t n_active;       // entries of aseg
+    // interior cells (no periodic wrap): element offset of the pulled population of
+    // direction k relative to the cell, and (AA) of the pushed one (mod 2^32)
+    uint32_t pull_off[Q];
+    uint32_t push_off[Q];
     FastDiv div_nx, div_ny;  // division by nx and ny
     int nx, ny, nz;
     int wall;                // 0 = SBB, 1 = CLI

@@ -11,26 +11,34 @@ namespace lbm {
 namespace detail {
 
 template <int STORE, int COLL, int KIND>
-cudaError_t step_one(const Launch &L, int flip, int reduce, unsigned *status)
+cudaError_t step_one(const Launch &L, int flip, int reduce, unsigned *status, const InstanceDev *one)
 {
-    step_kernel<COLL, STORE, KIND><<<L.grid, L.block, 0, L.stream>>>(L.table, L.tiles, L.ntiles, flip, reduce,
-                                                                     status);
+    if (one) {  // a single instance: parameters travel in the constant bank
+        step_kernel<COLL, STORE, KIND, false><<<L.grid, L.block, 0, L.stream>>>(L.table, *one, L.tiles, L.ntiles, flip,
+                                                                               reduce, status);
+    } else if constexpr (KIND == KIND_AB) {
+        static const InstanceDev unused{};
+        step_kernel<COLL, STORE, KIND, true><<<L.grid, L.block, 0, L.stream>>>(L.table, unused, L.tiles, L.ntiles, flip,
+                                                                              reduce, status);
+    } else {
+        return cudaErrorInvalidValue;  // the AA layout runs single instances only
+    }
     return cudaGetLastError();
 }
 
 template <int STORE>
-cudaError_t step(int coll, int kind, const Launch &L, int flip, int reduce, unsigned *status)
+cudaError_t step(int coll, int kind, const Launch &L, int flip, int reduce, unsigned *status, const InstanceDev *one)
 {
     switch (coll * 3 + kind) {
-    case COLL_SRT * 3 + KIND_AB: return step_one<STORE, COLL_SRT, KIND_AB>(L, flip, reduce, status);
-    case COLL_SRT * 3 + KIND_AA_PULL: return step_one<STORE, COLL_SRT, KIND_AA_PULL>(L, flip, reduce, status);
-    case COLL_SRT * 3 + KIND_AA_LOCAL: return step_one<STORE, COLL_SRT, KIND_AA_LOCAL>(L, flip, reduce, status);
-    case COLL_TRT * 3 + KIND_AB: return step_one<STORE, COLL_TRT, KIND_AB>(L, flip, reduce, status);
-    case COLL_TRT * 3 + KIND_AA_PULL: return step_one<STORE, COLL_TRT, KIND_AA_PULL>(L, flip, reduce, status);
-    case COLL_TRT * 3 + KIND_AA_LOCAL: return step_one<STORE, COLL_TRT, KIND_AA_LOCAL>(L, flip, reduce, status);
-    case COLL_MRT * 3 + KIND_AB: return step_one<STORE, COLL_MRT, KIND_AB>(L, flip, reduce, status);
-    case COLL_MRT * 3 + KIND_AA_PULL: return step_one<STORE, COLL_MRT, KIND_AA_PULL>(L, flip, reduce, status);
-    case COLL_MRT * 3 + KIND_AA_LOCAL: return step_one<STORE, COLL_MRT, KIND_AA_LOCAL>(L, flip, reduce, status);
+    case COLL_SRT * 3 + KIND_AB: return step_one<STORE, COLL_SRT, KIND_AB>(L, flip, reduce, status, one);
+    case COLL_SRT * 3 + KIND_AA_PULL: return step_one<STORE, COLL_SRT, KIND_AA_PULL>(L, flip, reduce, status, one);
+    case COLL_SRT * 3 + KIND_AA_LOCAL: return step_one<STORE, COLL_SRT, KIND_AA_LOCAL>(L, flip, reduce, status, one);
+    case COLL_TRT * 3 + KIND_AB: return step_one<STORE, COLL_TRT, KIND_AB>(L, flip, reduce, status, one);
+    case COLL_TRT * 3 + KIND_AA_PULL: return step_one<STORE, COLL_TRT, KIND_AA_PULL>(L, flip, reduce, status, one);
+    case COLL_TRT * 3 + KIND_AA_LOCAL: return step_one<STORE, COLL_TRT, KIND_AA_LOCAL>(L, flip, reduce, status, one);
+    case COLL_MRT * 3 + KIND_AB: return step_one<STORE, COLL_MRT, KIND_AB>(L, flip, reduce, status, one);
+    case COLL_MRT * 3 + KIND_AA_PULL: return step_one<STORE, COLL_MRT, KIND_AA_PULL>(L, flip, reduce, status, one);
+    case COLL_MRT * 3 + KIND_AA_LOCAL: return step_one<STORE, COLL_MRT, KIND_AA_LOCAL>(L, flip, reduce, status, one);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -39,15 +47,15 @@ template <int STORE>
 const void *step_ptr(int coll, int kind)
 {
     switch (coll * 3 + kind) {
-    case COLL_SRT * 3 + KIND_AB: return (const void *)step_kernel<COLL_SRT, STORE, KIND_AB>;
-    case COLL_SRT * 3 + KIND_AA_PULL: return (const void *)step_kernel<COLL_SRT, STORE, KIND_AA_PULL>;
-    case COLL_SRT * 3 + KIND_AA_LOCAL: return (const void *)step_kernel<COLL_SRT, STORE, KIND_AA_LOCAL>;
-    case COLL_TRT * 3 + KIND_AB: return (const void *)step_kernel<COLL_TRT, STORE, KIND_AB>;
-    case COLL_TRT * 3 + KIND_AA_PULL: return (const void *)step_kernel<COLL_TRT, STORE, KIND_AA_PULL>;
-    case COLL_TRT * 3 + KIND_AA_LOCAL: return (const void *)step_kernel<COLL_TRT, STORE, KIND_AA_LOCAL>;
-    case COLL_MRT * 3 + KIND_AB: return (const void *)step_kernel<COLL_MRT, STORE, KIND_AB>;
-    case COLL_MRT * 3 + KIND_AA_PULL: return (const void *)step_kernel<COLL_MRT, STORE, KIND_AA_PULL>;
-    case COLL_MRT * 3 + KIND_AA_LOCAL: return (const void *)step_kernel<COLL_MRT, STORE, KIND_AA_LOCAL>;
+    case COLL_SRT * 3 + KIND_AB: return (const void *)step_kernel<COLL_SRT, STORE, KIND_AB, false>;
+    case COLL_SRT * 3 + KIND_AA_PULL: return (const void *)step_kernel<COLL_SRT, STORE, KIND_AA_PULL, false>;
+    case COLL_SRT * 3 + KIND_AA_LOCAL: return (const void *)step_kernel<COLL_SRT, STORE, KIND_AA_LOCAL, false>;
+    case COLL_TRT * 3 + KIND_AB: return (const void *)step_kernel<COLL_TRT, STORE, KIND_AB, false>;
+    case COLL_TRT * 3 + KIND_AA_PULL: return (const void *)step_kernel<COLL_TRT, STORE, KIND_AA_PULL, false>;
+    case COLL_TRT * 3 + KIND_AA_LOCAL: return (const void *)step_kernel<COLL_TRT, STORE, KIND_AA_LOCAL, false>;
+    case COLL_MRT * 3 + KIND_AB: return (const void *)step_kernel<COLL_MRT, STORE, KIND_AB, false>;
+    case COLL_MRT * 3 + KIND_AA_PULL: return (const void *)step_kernel<COLL_MRT, STORE, KIND_AA_PULL, false>;
+    case COLL_MRT * 3 + KIND_AA_LOCAL: return (const void *)step_kernel<COLL_MRT, STORE, KIND_AA_LOCAL, false>;
     default: return nullptr;
     }
 }

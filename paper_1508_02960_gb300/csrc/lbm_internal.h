@@ -25,7 +25,9 @@ struct Launch {
 
 // Per-storage-format kernel entry points (one translation unit per format).
 struct FormatOps {
-    cudaError_t (*step)(int coll, int kind, const Launch &L, int flip, int reduce, unsigned *status);
+    // one: host copy of the only instance's parameters (passed by value), or NULL for a batch
+    cudaError_t (*step)(int coll, int kind, const Launch &L, int flip, int reduce, unsigned *status,
+                        const InstanceDev *one);
     cudaError_t (*init)(const InstanceDev *table, int inst, long long ncells, int layout, int cur,
                         double amp, unsigned long long seed, cudaStream_t s);
     cudaError_t (*import_dir)(const InstanceDev *table, int inst, long long ncells, int layout, int cur,

@@ -187,11 +187,11 @@ __device__ __forceinline__ void collide(R (&g)[Q], const Par<R> &p, const R *rat
 // Process one cell whose 19 pulled populations are in g[] (already shifted): walls,
 // moments, collision, stores.  Returns the moments for the reduction through rd..rz.
 template <int COLL, int STORE, int KIND, typename R>
-__device__ __forceinline__ void finish_cell(R (&g)[Q], const Par<R> &P, const R *rates, uint32_t cell,
-                                            uint32_t wm, uint32_t off, const typename Store<STORE>::T *fs,
-                                            typename Store<STORE>::T *fd, const R *linkc,
-                                            typename Store<STORE>::T *linkB, int reduce, unsigned *status,
-                                            R &rd, R &rx, R &ry, R &rz)
+__device__ __forceinline__ void finish_cell(R (&g)[Q], const Par<R> &P, const R *rates, uint32_t cell, uint32_t x,
+                                            const uint32_t *push_off, uint32_t wm, uint32_t off,
+                                            const typename Store<STORE>::T *fs, typename Store<STORE>::T *fd,
+                                            const R *linkc, typename Store<STORE>::T *linkB, int reduce,
+                                            unsigned *status, R &rd, R &rx, R &ry, R &rz)
 {
     using S = Store<STORE>;
     using T = typename S::T;
@@ -241,12 +241,24 @@ __device__ __forceinline__ void finish_cell(R (&g)[Q], const Par<R> &P, const R 
     for (int k = 0; k < Q; ++k)
         packed[k] = sr ? S::pack_sr(g[k], P.sc, round_bits(h, k, float(g[k]))) : S::pack(g[k], P.sc);
     if constexpr (KIND == KIND_AA_PULL) {
-        const Coord co = coord_of(P, cell);
+        if (push_off) {  // interior cell: x + e_k is cell + e_k, except across the x faces
+            const uint32_t cxm = x == 0 ? P.nx : 0u, cxp = x == P.nx - 1 ? P.nx : 0u;
 #pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            // push to x + e_k, or bounce into the own slot kbar when x + e_k is solid
-            if ((wm >> opp(k)) & 1u) fd[(uint32_t)opp(k) * KS + cell] = packed[k];
-            else fd[(uint32_t)k * KS + co.push(k)] = packed[k];
+            for (int k = 0; k < Q; ++k) {
+                uint32_t idx = cell + push_off[k];
+                if (ex(k) == 1) idx -= cxp;
+                if (ex(k) == -1) idx += cxm;
+                // push to x + e_k, or bounce into the own slot kbar when x + e_k is solid
+                if ((wm >> opp(k)) & 1u) idx = (uint32_t)opp(k) * KS + cell;
+                fd[idx] = packed[k];
+            }
+        } else {
+            const Coord co = coord_of(P, cell);
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                if ((wm >> opp(k)) & 1u) fd[(uint32_t)opp(k) * KS + cell] = packed[k];
+                else fd[(uint32_t)k * KS + co.push(k)] = packed[k];
+            }
         }
     } else {
 #pragma unroll
@@ -266,16 +278,27 @@ __device__ __forceinline__ void finish_cell(R (&g)[Q], const Par<R> &P, const R 
     }
 }
 
+// Instance parameters: from the device table (batches), or from a kernel argument in the
+// constant bank (a single instance).
+template <bool BATCH>
+__device__ __forceinline__ const InstanceDev &instance_of(const InstanceDev *table, const InstanceDev &one, int i)
+{
+    if constexpr (BATCH) return table[i];
+    else return one;
+}
+
 // The fused step.  One block per tile: kStepWarps warps, each taking kSegsPerWarp
 // consecutive entries of the instance's active-segment list.  A warp first issues the
-// pulls of all its segments, then finishes them one after the other, so the loads of one
-// overlap the collision of the other.  flip selects the A-B buffer pair (src = f[phase ^
-// flip]); reduce != 0 makes every tile write its FP64 partial sums (drho, u_x, u_y, u_z)
-// and flags diverged cells in status[instance].
-template <int COLL, int STORE, int KIND>
+// pulls of all its segments, then finishes them one after the other.  Warps whose cells
+// are all away from the y and z faces use precomputed offsets (cell + pull_off[k], with a
+// fix-up on the first and last cell of a row); the others index through their periodic
+// neighbours.  flip selects the A-B buffer pair (src = f[phase ^ flip]); reduce != 0 makes
+// every tile write its FP64 partial sums (drho, u_x, u_y, u_z) and flags diverged cells in
+// status[instance].
+template <int COLL, int STORE, int KIND, bool BATCH>
 __global__ void __launch_bounds__(kStepWarps * 32, step_min_blocks<STORE, KIND>())
-    step_kernel(const InstanceDev *__restrict__ table, const TileDev *__restrict__ tiles, int ntiles, int flip,
-                int reduce, unsigned *__restrict__ status)
+    step_kernel(const InstanceDev *__restrict__ table, const __grid_constant__ InstanceDev one,
+                const TileDev *__restrict__ tiles, int ntiles, int flip, int reduce, unsigned *__restrict__ status)
 {
     using S = Store<STORE>;
     using T = typename S::T;
@@ -286,7 +309,7 @@ __global__ void __launch_bounds__(kStepWarps * 32, step_min_blocks<STORE, KIND>(
     const int t = blockIdx.x;
     if (t >= ntiles) return;
     const TileDev tile = tiles[t];
-    const InstanceDev &I = table[tile.inst];
+    const InstanceDev &I = instance_of<BATCH>(table, one, tile.inst);
     const Par<R> P = load_par<R>(I);
     R rates[Q];
     if constexpr (COLL == COLL_MRT) {
@@ -313,27 +336,47 @@ __global__ void __launch_bounds__(kStepWarps * 32, step_min_blocks<STORE, KIND>(
 
     // issue every pull of the warp's cells (unconditional: solid sources hold 0)
     R g[NS][Q];
-    uint32_t cell[NS];
+    uint32_t cell[NS], xs[NS];
+    bool inner[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         cell[s] = meta[s].w * 32u + lane;
+        const uint32_t yz = fast_div(cell[s], P.dnx);
+        const uint32_t x = cell[s] - yz * P.nx;
+        const uint32_t z = fast_div(yz, P.dny);
+        const uint32_t y = yz - z * P.ny;
+        xs[s] = x;
+        // every lane away from the y and z faces (solid lanes do not matter)
+        const bool in_yz = ((meta[s].x >> lane) & 1u) || (y - 1u < P.ny - 2u && z - 1u < P.nz - 2u);
+        inner[s] = __all_sync(0xffffffffu, in_yz);
         if ((meta[s].x >> lane) & 1u) continue;
-        const Coord co = coord_of(P, cell[s]);
+        if (KIND != KIND_AA_LOCAL && inner[s]) {
+            const uint32_t cxm = x == 0 ? P.nx : 0u, cxp = x == P.nx - 1 ? P.nx : 0u;
 #pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            uint32_t idx;
-            if constexpr (KIND == KIND_AA_LOCAL) idx = (uint32_t)k * KS + cell[s];
-            else if constexpr (KIND == KIND_AA_PULL) idx = (uint32_t)opp(k) * KS + co.pull(k);
-            else idx = (uint32_t)k * KS + co.pull(k);
-            g[s][k] = S::load(fs + idx, P.isc);
+            for (int k = 0; k < Q; ++k) {
+                uint32_t idx = cell[s] + I.pull_off[k];
+                if (ex(k) == 1) idx += cxm;   // x - 1 wraps to the end of the row
+                if (ex(k) == -1) idx -= cxp;  // x + 1 wraps to the start of the row
+                g[s][k] = S::load(fs + idx, P.isc);
+            }
+        } else {
+            const Coord co = coord_of(P, cell[s]);
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                uint32_t idx;
+                if constexpr (KIND == KIND_AA_LOCAL) idx = (uint32_t)k * KS + cell[s];
+                else if constexpr (KIND == KIND_AA_PULL) idx = (uint32_t)opp(k) * KS + co.pull(k);
+                else idx = (uint32_t)k * KS + co.pull(k);
+                g[s][k] = S::load(fs + idx, P.isc);
+            }
         }
         // pressure shift of pulls that cross the x boundary
-        if (co.x == 0) {
+        if (x == 0) {
 #pragma unroll
             for (int k = 0; k < Q; ++k)
                 if (ex(k) == 1) g[s][k] += R(weight(k)) * P.dshift;
         }
-        if (co.x == P.nx - 1) {
+        if (x == P.nx - 1) {
 #pragma unroll
             for (int k = 0; k < Q; ++k)
                 if (ex(k) == -1) g[s][k] -= R(weight(k)) * P.dshift;
@@ -351,9 +394,10 @@ __global__ void __launch_bounds__(kStepWarps * 32, step_min_blocks<STORE, KIND>(
             wm = I.bmask[b];
             off = I.boff[b];
         }
-        finish_cell<COLL, STORE, KIND, R>(g[s], P, rates, cell[s], wm, off, fs, fd,
-                                          reinterpret_cast<const R *>(I.linkc), reinterpret_cast<T *>(I.linkB),
-                                          reduce, status + tile.inst, rd, rx, ry, rz);
+        finish_cell<COLL, STORE, KIND, R>(g[s], P, rates, cell[s], xs[s], inner[s] ? I.push_off : nullptr, wm, off,
+                                          fs, fd, reinterpret_cast<const R *>(I.linkc),
+                                          reinterpret_cast<T *>(I.linkB), reduce, status + tile.inst, rd, rx, ry,
+                                          rz);
         if (reduce) {  // lane sums over the warp's segments, in order
             a0 += (double)rd;
             a1 += (double)rx;

@@ -70,11 +70,12 @@ def _load():
             lib.orc_voxelize.restype = ctypes.c_int
             lib.orc_wall_distances.argtypes = [ctypes.c_int] * 3 + [u8p, dp, ctypes.c_int, dp]
             lib.orc_wall_distances.restype = ctypes.c_int
-            lib.orc_run.argtypes = [ctypes.POINTER(Params), u8p, dp, dp, ctypes.c_int, dp, dp]
+            lib.orc_run.argtypes = [ctypes.POINTER(Params), u8p, dp, dp, ctypes.c_int, dp, dp, dp]
             lib.orc_run.restype = ctypes.c_int
             lib.orc_init_rest.argtypes = [ctypes.c_int] * 3 + [u8p, ctypes.c_double, dp]
             lib.orc_observables.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int, ctypes.c_double,
                                                                     ctypes.c_double, dp]
+            lib.orc_drag_coefficients.argtypes = [ctypes.c_double] * 6 + [dp]
             lib.orc_set_threads.argtypes = [ctypes.c_int]
             lib.orc_max_threads.restype = ctypes.c_int
             _lib = lib
@@ -181,11 +182,12 @@ def init_rest(solid, rho0: float = 1.0) -> np.ndarray:
     return f
 
 
-def run(solid, f, nsteps: int, *, q=None, want_u: bool = False, **kw):
+def run(solid, f, nsteps: int, *, q=None, want_u: bool = False, force=None, **kw):
     """Advance f (post-collision, [19,nz,ny,nx]) by nsteps.  Returns (f, sums, u|None).
 
     sums = [sum rho, sum u_x, sum u_y, sum u_z] over fluid cells of the last step's
-    streamed moments."""
+    streamed moments.  force: optional float64 array of 3 that receives the momentum
+    exchanged with the solid during the last step (the drag F_D of Sec. 3)."""
     solid = np.ascontiguousarray(solid, dtype=np.uint8)
     f = np.array(f, dtype=np.float64, order="C", copy=True)
     p, keep = make_params(solid.shape, **kw)
@@ -194,11 +196,24 @@ def run(solid, f, nsteps: int, *, q=None, want_u: bool = False, **kw):
         qq = np.ascontiguousarray(q, dtype=np.float64)
     sums = np.zeros(4)
     u = np.zeros((3,) + solid.shape) if want_u else None
+    if force is not None and (not isinstance(force, np.ndarray) or force.dtype != np.float64
+                              or force.shape != (3,) or not force.flags.c_contiguous):
+        raise ValueError("force must be a contiguous float64 array of 3")
     rc = _load().orc_run(ctypes.byref(p), _u8(solid), _dp(qq) if qq is not None else None,
-                         _dp(f), int(nsteps), _dp(sums), _dp(u) if u is not None else None)
+                         _dp(f), int(nsteps), _dp(sums), _dp(u) if u is not None else None,
+                         _dp(force) if force is not None else None)
     if rc != 0:
         raise ValueError(f"orc_run failed ({rc})")
     return f, sums, u
+
+
+def drag_coefficients(F_D, U, tau, r_sum, area_sum, rho0=1.0):
+    """[C_D, C_D_A]: F_D / (6 pi mu U r) (Eq. AnalyticForce, r = sum of radii) and
+    F_D / (rho0 A U^2) (Sec. 4, A = sum of frontal areas pi r^2)."""
+    out = np.zeros(2)
+    _load().orc_drag_coefficients(float(F_D), float(U), float(tau), float(rho0), float(r_sum),
+                                  float(area_sum), _dp(out))
+    return out
 
 
 def observables(U, tau, delta_rho, lx, d_p, K_D=0.0, rho0=1.0):

@@ -11,7 +11,7 @@
  *
  * Every routine follows the paper's notation (k, k-bar, x_f1, x_f2, q, f-tilde) and
  * takes the steps in the order the paper states them.  Where the paper is silent or
- * ambiguous, the reading taken is stated in the comment (readings O1..O12).
+ * ambiguous, the reading taken is stated in the comment (readings O1..O14).
  *
  * Compiled as C99 with -O2 -ffp-contract=off (no fused multiply-add), optionally
  * with OpenMP over z.  All arithmetic is IEEE double.
@@ -391,15 +391,21 @@ static double read_pop(const double *f, int64_t n, int k, int xv, int yv, int zv
  *
  * sums (optional, 4 doubles): sum over fluid nodes of rho, u_x, u_y, u_z of the
  * streamed moments (Eq. Macro) -- reading O9.  uvec (optional, 3*N): per-node u.
+ *
+ * force (optional, 3 doubles): the drag F_D of Sec. 3 (Eq. AnalyticForce) on all solid nodes
+ * during this step, by momentum exchange (reading O13): every wall link (x, kbar) with
+ * x - e_k solid carries f~_kbar(x, t) into the wall and brings f_k(x, t+1) back, so the
+ * solid receives e_kbar (f~_kbar(x, t) + f_k(x, t+1)).
  * ---------------------------------------------------------------------------- */
 static void step_once(const orc_params *p, const uint8_t *solid, const double *q,
-                      const double *f, double *ft, double *sums, double *uvec)
+                      const double *f, double *ft, double *sums, double *uvec, double *force)
 {
     const int nx = p->nx, ny = p->ny, nz = p->nz;
     const int64_t n = (int64_t)nx * ny * nz;
     double srho = 0.0, sux = 0.0, suy = 0.0, suz = 0.0;
+    double sfx = 0.0, sfy = 0.0, sfz = 0.0;
 
-#pragma omp parallel for schedule(static) reduction(+ : srho, sux, suy, suz)
+#pragma omp parallel for schedule(static) reduction(+ : srho, sux, suy, suz, sfx, sfy, sfz)
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
@@ -430,6 +436,11 @@ static void step_once(const orc_params *p, const uint8_t *solid, const double *q
                     } else {
                         fin[k] = own_kb;
                     }
+                    /* momentum given to the solid through link (x, kbar) */
+                    double ex_in = own_kb + fin[k];
+                    sfx += E[kb][0] * ex_in;
+                    sfy += E[kb][1] * ex_in;
+                    sfz += E[kb][2] * ex_in;
                 }
                 double rho, u[3];
                 moments(fin, p->rho0, &rho, u);
@@ -451,12 +462,17 @@ static void step_once(const orc_params *p, const uint8_t *solid, const double *q
         sums[2] = suy;
         sums[3] = suz;
     }
+    if (force) {
+        force[0] = sfx;
+        force[1] = sfy;
+        force[2] = sfz;
+    }
 }
 
 /* Run nsteps time steps.  f (19*N, [k][z][y][x]) holds f-tilde on entry and on exit.
- * sums / uvec describe the last step's streamed moments (see step_once). */
+ * sums / uvec / force describe the last step (see step_once); each may be NULL. */
 int orc_run(const orc_params *p, const uint8_t *solid, const double *q, double *f,
-            int nsteps, double *sums, double *uvec)
+            int nsteps, double *sums, double *uvec, double *force)
 {
     lattice_init();
     mrt_init();
@@ -469,7 +485,7 @@ int orc_run(const orc_params *p, const uint8_t *solid, const double *q, double *
     double *a = f, *b = g;
     for (int t = 0; t < nsteps; ++t) {
         int last = (t == nsteps - 1);
-        step_once(p, solid, q, a, b, last ? sums : NULL, last ? uvec : NULL);
+        step_once(p, solid, q, a, b, last ? sums : NULL, last ? uvec : NULL, last ? force : NULL);
         double *tmp = a;
         a = b;
         b = tmp;
@@ -516,6 +532,24 @@ void orc_observables(double U, double tau, double delta_rho, double rho0, int lx
     } else {
         out[3] = out[4] = out[5] = out[6] = NAN;
     }
+}
+
+/* ------------------------------------------------------------------------------
+ * Drag coefficients from the streamwise drag F_D (Sec. 3 Eq. AnalyticForce and the
+ * resolution study of Sec. 4), lattice units, U = U_sup, mu = rho0 (tau - 1/2)/3:
+ *   C_D   = F_D / (6 pi mu U r)       -- Stokes normalisation; for several spheres r is
+ *                                        the sum of their radii (reading O14)
+ *   C_D,A = F_D / (rho0 A U^2)        -- A = sum of the spheres' frontal areas pi r^2
+ *                                        (reading O14)
+ * out: [C_D, C_D,A]
+ * ---------------------------------------------------------------------------- */
+void orc_drag_coefficients(double F_D, double U, double tau, double rho0, double r_sum,
+                           double area_sum, double *out)
+{
+    const double pi = 3.14159265358979323846;
+    double mu = rho0 * (tau - 0.5) / 3.0;
+    out[0] = F_D / (6.0 * pi * mu * U * r_sum);
+    out[1] = F_D / (rho0 * area_sum * U * U);
 }
 
 /* Thread control for the timed CPU baseline (OpenMP over z when compiled with it). */

@@ -119,6 +119,13 @@ typedef struct {
     double C_F;       /* beta sqrt(K_D) */
     double F_K;       /* (delta_p / L) sqrt(K_D) / (rho U^2) */
     double u_max;     /* largest |u| seen by the last reduction (0 when not tracked) */
+    double F_x, F_y, F_z; /* drag force F_D on all solids: momentum handed to the solid
+                             through the cut links in the last reducing step, by momentum
+                             exchange (Sec. 3); NaN when the moments came from a stored state
+                             rather than a step */
+    double C_D;       /* F_x / (6 pi mu U_sup r), Eq. AnalyticForce; r = sum of the sphere
+                         radii (NaN for a flag-field geometry) */
+    double C_D_A;     /* F_x / (rho0 A U_sup^2), A = sum of pi r^2 (Sec. 4 resolution study) */
     int64_t steps;    /* time steps completed */
     int64_t n_fluid;  /* fluid cells */
 } lbm_obs;
@@ -167,9 +174,10 @@ LBM_API lbm_status lbm_run_to_convergence(lbm_ctx *ctx, double tol, int64_t chec
                                   int64_t max_steps, int64_t *steps_done);
 
 /* Time average (Sec. 4: volume-averaged velocity averaged over a period of the developed
- * flow): advance n_samples * sample_interval steps, reduce the moments after every
- * sample_interval steps and average them in FP64; *out receives the observables of the
- * averaged U_sup (K_darcy as in lbm_observables), u_max unused, steps = steps done so far.
+ * flow, and the time-averaged drag of the resolution study): advance n_samples *
+ * sample_interval steps, reduce the moments and the drag after every sample_interval steps
+ * and average them in FP64; *out receives the observables of the averaged U_sup and F_D
+ * (K_darcy as in lbm_observables), u_max unused, steps = steps done so far.
  * Returns LBM_ERR_DIVERGED (with the average so far) when a sample diverged. */
 LBM_API lbm_status lbm_average(lbm_ctx *ctx, int64_t n_samples, int64_t sample_interval, double K_darcy,
                                lbm_obs *out);

@@ -65,7 +65,8 @@ class Desc(ctypes.Structure):
 class Obs(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in
                 ("U_sup", "U_int", "mass", "porosity", "K", "K_app", "Re_p", "Re_K", "beta",
-                 "C_F", "F_K", "u_max")] + [("steps", ctypes.c_int64), ("n_fluid", ctypes.c_int64)]
+                 "C_F", "F_K", "u_max", "F_x", "F_y", "F_z", "C_D", "C_D_A")] + \
+               [("steps", ctypes.c_int64), ("n_fluid", ctypes.c_int64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

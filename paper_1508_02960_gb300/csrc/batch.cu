@@ -132,6 +132,10 @@ lbm_status Batch::make_instance(const lbm_desc &d0, cudaStream_t s, std::unique_
         for (int i = 0; i < d0.n_spheres; ++i) m3 += std::pow(d0.spheres[i].r, 3.0);
         in->d_p = 2.0 * std::cbrt(m3 / d0.n_spheres);
     }
+    for (int i = 0; i < d0.n_spheres; ++i) {  // drag normalisation (Eq. AnalyticForce, Sec. 4)
+        in->r_sum += d0.spheres[i].r;
+        in->area_sum += M_PI * d0.spheres[i].r * d0.spheres[i].r;
+    }
     std::vector<double> sph;
     for (int i = 0; i < d0.n_spheres; ++i) {
         sph.push_back(d0.spheres[i].cx);
@@ -173,10 +177,9 @@ lbm_status Batch::make_instance(const lbm_desc &d0, cudaStream_t s, std::unique_
         if ((e = cudaMemsetAsync(in->linkB, 0, es * in->geo.n_links, s)) != cudaSuccess)
             return cleanup(e, "cudaMemset");
     }
-    // partial sums: one slot of 4 doubles per tile at the smallest tile (2 segments)
-    // partial sums: one slot of 4 doubles per work chunk at the smallest chunk size
+    // partial sums: one row of kRedSlots doubles per work chunk at the smallest chunk size
     in->partial_capacity = std::max(1ll, (in->geo.n_active + kMinChunkSegs - 1) / kMinChunkSegs);
-    if ((e = cudaMalloc(&in->partials, sizeof(double) * 4 * in->partial_capacity)) != cudaSuccess)
+    if ((e = cudaMalloc(&in->partials, sizeof(double) * kRedSlots * in->partial_capacity)) != cudaSuccess)
         return cleanup(e, "cudaMalloc(partials)");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cleanup(e, "cudaStreamSynchronize");
     in->bytes_pop = pop * (d.layout == LBM_LAYOUT_AB ? 2 : 1);
@@ -202,6 +205,9 @@ Batch::~Batch()
     cudaFree(d_tiles_);
     cudaFree(d_tile_begin_);
     cudaFree(d_tile_count_);
+    cudaFree(d_stiles_);
+    cudaFree(d_stile_begin_);
+    cudaFree(d_stile_count_);
     cudaFree(d_sums_);
     cudaFree(d_status_);
     cudaFree(d_stage_);
@@ -273,6 +279,9 @@ static void fill_dev(const Instance &in, InstanceDev &D)
     D.seg = in.geo.seg;
     D.aseg = in.geo.aseg;
     D.n_active = (uint32_t)in.geo.n_active;
+    D.fcell = in.geo.fcell;
+    D.fwarp = in.geo.fwarp;
+    D.n_fwarps = (uint32_t)in.geo.n_fwarps;
     for (int k = 0; k < Q; ++k) {
         const long long dk = ex(k) + (long long)ey(k) * d.nx + (long long)ez(k) * d.nx * d.ny;  // e_k as an offset
         const long long arr = d.layout == LBM_LAYOUT_AA ? opp(k) : k;
@@ -323,27 +332,42 @@ lbm_status Batch::rebuild()
     graphs_.clear();
     const int n = size();
     const int CS = block_ / 32;  // segments per work chunk
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     std::vector<InstanceDev> table(std::max(n, 1));
-    std::vector<TileDev> tiles;
-    std::vector<int> tb(std::max(n, 1)), tc(std::max(n, 1));
+    std::vector<TileDev> tiles, stiles;
+    std::vector<int> tb(std::max(n, 1)), tc(std::max(n, 1)), sb(std::max(n, 1)), sc(std::max(n, 1));
     for (int i = 0; i < n; ++i) {
         Instance &in = *inst_[i];
         fill_dev(in, table[i]);
+        // state kernels: chunks of the active-segment list
         const long long nt = std::max(1ll, (in.geo.n_active + CS - 1) / CS);
-        if (nt > in.partial_capacity) return fail(LBM_ERR_STATE, "partials too small");
+        // step kernels: kTileSegs fluid warps per tile (the list is padded to whole tiles)
+        const long long ns = std::max(1ll, (in.geo.n_fwarps + kTileSegs - 1) / kTileSegs);
+        if (nt > in.partial_capacity || ns > in.partial_capacity) return fail(LBM_ERR_STATE, "partials too small");
+        if (ns * kTileSegs > in.geo.n_fwarps_padded) return fail(LBM_ERR_STATE, "fluid work list too short");
         tb[i] = (int)tiles.size();
         tc[i] = (int)nt;
         for (long long t = 0; t < nt; ++t) tiles.push_back(TileDev{i, (int)t, t * CS});
+        sb[i] = (int)stiles.size();
+        sc[i] = (int)ns;
+        for (long long t = 0; t < ns; ++t) stiles.push_back(TileDev{i, (int)t, t * kTileSegs});
     }
-    if (tiles.size() > (size_t)INT32_MAX) return fail(LBM_ERR_ARG, "too many tiles");
+    if (tiles.size() > (size_t)INT32_MAX || stiles.size() > (size_t)INT32_MAX)
+        return fail(LBM_ERR_ARG, "too many tiles");
     ntiles_ = (int)tiles.size();
+    nstiles_ = (int)stiles.size();
     cudaFree(d_table_);
     cudaFree(d_tiles_);
     cudaFree(d_tile_begin_);
     cudaFree(d_tile_count_);
+    cudaFree(d_stiles_);
+    cudaFree(d_stile_begin_);
+    cudaFree(d_stile_count_);
     d_table_ = nullptr;
-    d_tiles_ = nullptr;
-    d_tile_begin_ = d_tile_count_ = nullptr;
+    d_tiles_ = d_stiles_ = nullptr;
+    d_tile_begin_ = d_tile_count_ = d_stile_begin_ = d_stile_count_ = nullptr;
     h_table_ = table;
     CK(cudaMalloc(&d_table_, sizeof(InstanceDev) * table.size()));
     CK(cudaMemcpy(d_table_, table.data(), sizeof(InstanceDev) * table.size(), cudaMemcpyHostToDevice));
@@ -355,6 +379,14 @@ lbm_status Batch::rebuild()
     CK(cudaMalloc(&d_tile_count_, sizeof(int) * tc.size()));
     CK(cudaMemcpy(d_tile_begin_, tb.data(), sizeof(int) * tb.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_tile_count_, tc.data(), sizeof(int) * tc.size(), cudaMemcpyHostToDevice));
+    if (nstiles_ > 0) {
+        CK(cudaMalloc(&d_stiles_, sizeof(TileDev) * stiles.size()));
+        CK(cudaMemcpy(d_stiles_, stiles.data(), sizeof(TileDev) * stiles.size(), cudaMemcpyHostToDevice));
+    }
+    CK(cudaMalloc(&d_stile_begin_, sizeof(int) * sb.size()));
+    CK(cudaMalloc(&d_stile_count_, sizeof(int) * sc.size()));
+    CK(cudaMemcpy(d_stile_begin_, sb.data(), sizeof(int) * sb.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_stile_count_, sc.data(), sizeof(int) * sc.size(), cudaMemcpyHostToDevice));
     if (n > capacity_) {
         cudaFree(d_sums_);
         cudaFree(d_status_);
@@ -365,17 +397,14 @@ lbm_status Batch::rebuild()
         h_sums_ = nullptr;
         h_status_ = nullptr;
         capacity_ = std::max(n, 2 * capacity_);
-        CK(cudaMalloc(&d_sums_, sizeof(double) * 4 * capacity_));
+        CK(cudaMalloc(&d_sums_, sizeof(double) * kRedSlots * capacity_));
         CK(cudaMalloc(&d_status_, sizeof(unsigned) * capacity_));
         CK(cudaMemset(d_status_, 0, sizeof(unsigned) * capacity_));
-        CK(cudaMallocHost(&h_sums_, sizeof(double) * 4 * capacity_));
+        CK(cudaMallocHost(&h_sums_, sizeof(double) * kRedSlots * capacity_));
         CK(cudaMallocHost(&h_status_, sizeof(unsigned) * capacity_));
     }
     // one step block per tile; the hardware block scheduler balances the tiles
-    grid_ = std::max(1, ntiles_);
-    int dev = 0, sms = 0;
-    CK(cudaGetDevice(&dev));
-    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    grid_ = std::max(1, nstiles_);
     aux_grid_ = std::max(1, std::min(sms * 8, (ntiles_ + 7) / 8));
     dirty_ = false;
     return LBM_OK;
@@ -394,6 +423,7 @@ lbm_status Batch::init_equilibrium(int i)
                       (unsigned long long)in.desc.seed, stream_));
         ++launches_;
         in.have_sums = false;
+        in.have_force = false;
         in.sums_pending = false;
         in.steps = 0;
     }
@@ -448,9 +478,9 @@ lbm_status Batch::step(long long n)
         lbm_status st = rebuild();
         if (st != LBM_OK) return st;
     }
-    StepQueue q{&ops(), Launch{d_table_, d_tiles_, ntiles_, block_ / 32, grid_, kStepWarps * 32, stream_},
+    StepQueue q{&ops(), Launch{d_table_, d_stiles_, nstiles_, kTileSegs, grid_, kStepWarps * 32, stream_},
                 size() == 1 ? &h_table_[0] : nullptr, collision_, layout_, d_status_,
-                size(), d_tile_begin_, d_tile_count_, d_sums_, size()};
+                size(), d_stile_begin_, d_stile_count_, d_sums_, size()};
     const long long kChunk = 1000;
     long long left = n;
     while (left > 0) {
@@ -487,6 +517,7 @@ lbm_status Batch::step(long long n)
     for (auto &p : inst_) {
         p->steps += n;
         p->have_sums = false;
+        p->have_force = false;
         p->sums_pending = true;
     }
     return LBM_OK;
@@ -496,14 +527,14 @@ lbm_status Batch::fetch_sums()
 {
     const int n = size();
     if (n == 0) return LBM_OK;
-    CK(cudaMemcpyAsync(h_sums_, d_sums_, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, stream_));
+    CK(cudaMemcpyAsync(h_sums_, d_sums_, sizeof(double) * kRedSlots * n, cudaMemcpyDeviceToHost, stream_));
     CK(cudaMemcpyAsync(h_status_, d_status_, sizeof(unsigned) * n, cudaMemcpyDeviceToHost, stream_));
     CK(cudaStreamSynchronize(stream_));
     for (int i = 0; i < n; ++i) {
         Instance &in = *inst_[i];
-        for (int d = 0; d < 4; ++d) in.sums[d] = h_sums_[4 * i + d];
+        for (int d = 0; d < kRedSlots; ++d) in.sums[d] = h_sums_[kRedSlots * i + d];
         in.status = h_status_[i];
-        if (in.sums_pending) in.have_sums = true;
+        if (in.sums_pending) in.have_sums = in.have_force = true;
         in.sums_pending = false;
     }
     return LBM_OK;
@@ -529,11 +560,13 @@ lbm_status Batch::moment_sums_now(int i, double *sums)
     Launch L{d_table_, d_tiles_ + tb[i], nt, block_ / 32, std::max(1, std::min(aux_grid_, (nt + 7) / 8)), 256,
              stream_};
     CK(ops().moments(L, layout_, cur_of(in), aa_phase_, 1, 0, nullptr));
-    CK(launch_final_reduce(d_table_ + i, d_tile_begin_ + i, d_tile_count_ + i, 1, d_sums_ + 4 * i, stream_));
+    double *ds = d_sums_ + (size_t)kRedSlots * i;
+    double *hs = h_sums_ + (size_t)kRedSlots * i;
+    CK(launch_final_reduce(d_table_ + i, d_tile_begin_ + i, d_tile_count_ + i, 1, ds, stream_));
     launches_ += 2;
-    CK(cudaMemcpyAsync(h_sums_ + 4 * i, d_sums_ + 4 * i, sizeof(double) * 4, cudaMemcpyDeviceToHost, stream_));
+    CK(cudaMemcpyAsync(hs, ds, sizeof(double) * 4, cudaMemcpyDeviceToHost, stream_));
     CK(cudaStreamSynchronize(stream_));
-    for (int d = 0; d < 4; ++d) sums[d] = h_sums_[4 * i + d];
+    for (int d = 0; d < 4; ++d) sums[d] = hs[d];
     return LBM_OK;
 }
 
@@ -584,6 +617,7 @@ lbm_status Batch::set_f64(int i, const double *host)
         ++launches_;
     }
     in.have_sums = false;
+    in.have_force = false;
     in.sums_pending = false;
     CK(cudaStreamSynchronize(stream_));
     return LBM_OK;
@@ -758,6 +792,7 @@ lbm_status Batch::load(int i, const char *path)
     if (!lb.empty()) CK(cudaMemcpy(in.linkB, lb.data(), lb.size(), cudaMemcpyHostToDevice));
     in.steps = h.steps;
     in.have_sums = false;
+    in.have_force = false;
     in.sums_pending = false;
     return LBM_OK;
 }

@@ -24,11 +24,13 @@ struct Instance {
     int phase = 0;                   // A-B buffer holding the state when the batch flip is 0
     int dev_scale_log2 = 0;
     double d_p = 0.0;
+    double r_sum = 0.0, area_sum = 0.0;  // sum of sphere radii and of pi r^2 (0: flag geometry)
     long long steps = 0;
-    // results of the last reduction
-    double sums[4] = {0, 0, 0, 0};
+    // results of the last reduction (slots RED_DRHO, RED_U.., RED_F..)
+    double sums[kRedSlots] = {};
     unsigned status = 0;
     bool have_sums = false;
+    bool have_force = false;         // sums[RED_F..] come from a step (not a state reduction)
     bool sums_pending = false;       // the last queued step reduced the moments
     size_t bytes_pop = 0;
     long long ks = 0;                // elements between direction arrays
@@ -50,7 +52,7 @@ public:
 
     lbm_status init_equilibrium(int i);                // i < 0: all
     lbm_status step(long long n);                      // queue n steps (+ final reduction)
-    lbm_status moment_sums_now(int i, double *sums);   // reduce the stored state (synchronises)
+    lbm_status moment_sums_now(int i, double *sums);   // sums[4] of the stored state (synchronises)
     lbm_status fetch_sums();                           // copy last reduction to host (synchronises)
     lbm_status get_f64(int i, double *host);
     lbm_status set_f64(int i, const double *host);
@@ -79,16 +81,19 @@ private:
     cudaStream_t cap_ = nullptr;      // private stream for graph capture
     InstanceDev *d_table_ = nullptr;
     std::vector<InstanceDev> h_table_;  // host copy (the single-instance launch passes it by value)
-    TileDev *d_tiles_ = nullptr;
+    TileDev *d_tiles_ = nullptr;      // tiles of the active-segment lists (state kernels)
     int *d_tile_begin_ = nullptr, *d_tile_count_ = nullptr;
-    double *d_sums_ = nullptr;        // [n][4]
+    TileDev *d_stiles_ = nullptr;     // tiles of the fluid-warp lists (step kernels)
+    int *d_stile_begin_ = nullptr, *d_stile_count_ = nullptr;
+    int nstiles_ = 0;
+    double *d_sums_ = nullptr;        // [n][kRedSlots]
     unsigned *d_status_ = nullptr;    // [n]
-    double *h_sums_ = nullptr;        // pinned [n][4]
+    double *h_sums_ = nullptr;        // pinned [n][kRedSlots]
     unsigned *h_status_ = nullptr;    // pinned [n]
     int capacity_ = 0;
     int ntiles_ = 0;
     int block_ = 32 * kTileSegs;      // cells per tile (one step block)
-    int grid_ = 0;                    // step-kernel blocks (one per tile)
+    int grid_ = 0;                    // step-kernel blocks (one per step tile)
     int aux_grid_ = 1;
     int flip_ = 0;
     int aa_phase_ = 0;

@@ -26,7 +26,9 @@ namespace lbm {
 // delta_p = delta_rho / 3 (p = rho c_s^2), gradP = delta_p / L_x, K = mu U / gradP
 // (Eq. Darcy), Re_p = U d_p / nu, and with K_D: beta = (gradP - mu U / K_D)/(rho U^2)
 // (Eq. Forchheimer), C_F = beta sqrt(K_D), F_K = gradP sqrt(K_D)/(rho U^2),
-// Re_K = rho U sqrt(K_D)/mu (Eq. frictionFactor).
+// Re_K = rho U sqrt(K_D)/mu (Eq. frictionFactor).  Drag: F_D = the momentum handed to the
+// solid in the last reducing step, C_D = F_x / (6 pi mu U r) with r the sum of the sphere
+// radii (Eq. AnalyticForce) and C_D_A = F_x / (rho0 A U^2) with A the sum of pi r^2 (Sec. 4).
 void compute_obs(const Instance &in, double K_D, lbm_obs *o)
 {
     const lbm_desc &d = in.desc;
@@ -53,6 +55,15 @@ void compute_obs(const Instance &in, double K_D, lbm_obs *o)
         o->beta = o->C_F = o->F_K = o->Re_K = nan;
     }
     o->u_max = 0.0;
+    if (in.have_force) {
+        o->F_x = in.sums[RED_F + 0];
+        o->F_y = in.sums[RED_F + 1];
+        o->F_z = in.sums[RED_F + 2];
+    } else {
+        o->F_x = o->F_y = o->F_z = nan;
+    }
+    o->C_D = in.r_sum > 0 ? o->F_x / (6.0 * M_PI * mu * U * in.r_sum) : nan;
+    o->C_D_A = in.area_sum > 0 ? o->F_x / (d.rho0 * in.area_sum * U * U) : nan;
     o->steps = in.steps;
     o->n_fluid = in.geo.n_fluid;
 }
@@ -135,6 +146,7 @@ lbm_status lbm_observables(lbm_ctx *ctx, double K_darcy, lbm_obs *out)
             st = ctx->b.moment_sums_now(0, in.sums);
             in.status = 0;
             in.have_sums = (st == LBM_OK);
+            in.have_force = false;
         }
         if (st != LBM_OK) return st;
     }
@@ -180,7 +192,7 @@ lbm_status lbm_average(lbm_ctx *ctx, int64_t n_samples, int64_t sample_interval,
     if (!ctx || !out) return fail(LBM_ERR_ARG, "NULL argument");
     if (n_samples < 1 || sample_interval < 1) return fail(LBM_ERR_ARG, "n_samples and sample_interval must be >= 1");
     Instance &in = ctx->b.at(0);
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    double acc[kRedSlots] = {};
     int64_t done = 0;
     lbm_status result = LBM_OK;
     for (int64_t i = 0; i < n_samples; ++i) {
@@ -188,20 +200,20 @@ lbm_status lbm_average(lbm_ctx *ctx, int64_t n_samples, int64_t sample_interval,
         if (st != LBM_OK) return st;
         st = ctx->b.fetch_sums();
         if (st != LBM_OK) return st;
-        for (int d = 0; d < 4; ++d) acc[d] += in.sums[d];
+        for (int d = 0; d < kRedSlots; ++d) acc[d] += in.sums[d];
         ++done;
         if (in.status & STATUS_DIVERGED) {
             result = fail(LBM_ERR_DIVERGED, "a sample saw a diverged cell");
             break;
         }
     }
-    double keep[4];
-    for (int d = 0; d < 4; ++d) {
+    double keep[kRedSlots];
+    for (int d = 0; d < kRedSlots; ++d) {
         keep[d] = in.sums[d];
         in.sums[d] = acc[d] / (double)done;
     }
     compute_obs(in, K_darcy, out);
-    for (int d = 0; d < 4; ++d) in.sums[d] = keep[d];
+    for (int d = 0; d < kRedSlots; ++d) in.sums[d] = keep[d];
     return result;
 }
 
@@ -323,6 +335,7 @@ lbm_status lbm_batch_observables(lbm_batch *b, int32_t i, double K_darcy, lbm_ob
             st = b->b.moment_sums_now(i, in.sums);
             in.status = 0;
             in.have_sums = (st == LBM_OK);
+            in.have_force = false;
         }
         if (st != LBM_OK) return st;
     }

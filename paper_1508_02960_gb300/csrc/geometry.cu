@@ -7,7 +7,8 @@
 //      of the nearest periodic image of a sphere centre (or copied from a flag field);
 //   2. wm[cell]: bit k set when the fluid cell's pull source x - e_k is solid;
 //   3. per 32-cell segment: solid/out-of-range bits, boundary bits, boundary count;
-//   4. exclusive scan of the counts -> first boundary index of every segment;
+//   4. exclusive scan of the counts -> first boundary index of every segment; the list
+//      of segments holding fluid; the fluid cells in cell order, 32 per warp;
 //   5. boundary table (mask, cell) and link counts; scan -> first link of every cell;
 //   6. per link: q from the ray x_f1 + t e_kbar against the spheres (nearest crossing),
 //      or from a caller-supplied q field, and the CLI coefficient (1-2q)/(1+2q), set
@@ -126,6 +127,50 @@ __global__ void active_scatter_kernel(long long nseg, long long n_active_padded,
     for (long long i = n_active + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_active_padded;
          i += (long long)gridDim.x * blockDim.x)
         aseg[i] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+}
+
+// Fluid cells in cell order: count per segment, then each fluid cell's rank -> fcell.
+__global__ void fluid_count_kernel(long long nseg, const uint4 *__restrict__ seg, unsigned long long *__restrict__ cnt)
+{
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < nseg;
+         s += (long long)gridDim.x * blockDim.x)
+        cnt[s] = 32u - __popc(seg[s].x);
+}
+
+__global__ void fluid_scatter_kernel(long long n, const uint4 *__restrict__ seg,
+                                     const unsigned long long *__restrict__ fbase, uint32_t *__restrict__ fcell)
+{
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        const uint32_t lane = (uint32_t)(c & 31);
+        const uint32_t sb = seg[c >> 5].x;
+        if (!((sb >> lane) & 1u)) fcell[fbase[c >> 5] + __popc(~sb & ((1u << lane) - 1u))] = (uint32_t)c;
+    }
+}
+
+// One warp per fluid warp w (fluid cells 32w .. 32w+31 in cell order): the boundary bits of
+// its lanes and the boundary-table index of its first boundary cell.  The boundary table
+// lists boundary cells in cell order, so the warp's boundary cells are consecutive there,
+// starting at the number of boundary cells before its first cell.
+__global__ void fwarp_kernel(long long nw, const uint32_t *__restrict__ fcell, const uint4 *__restrict__ seg,
+                             uint2 *__restrict__ fwarp)
+{
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nw; w += warps) {
+        const uint32_t c = fcell[w * 32 + lane];
+        const bool live = c != 0xFFFFFFFFu;
+        const bool bnd = live && ((seg[c >> 5].y >> (c & 31u)) & 1u);
+        const unsigned bb = __ballot_sync(0xffffffffu, bnd);
+        if (lane == 0) {
+            uint32_t base = 0u;
+            if (live) {
+                const uint4 m = seg[c >> 5];
+                base = m.z + __popc(m.y & ((1u << (c & 31u)) - 1u));
+            }
+            fwarp[w] = make_uint2(bb, base);
+        }
+    }
 }
 
 __global__ void seg_base_kernel(long long nseg, uint4 *__restrict__ seg, const unsigned long long *__restrict__ base)
@@ -316,6 +361,8 @@ void free_geometry(GeometryDev *g)
     cudaFree(g->solid);
     cudaFree(g->seg);
     cudaFree(g->aseg);
+    cudaFree(g->fcell);
+    cudaFree(g->fwarp);
     cudaFree(g->bmask);
     cudaFree(g->boff);
     cudaFree(g->bcell);
@@ -398,6 +445,28 @@ cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_
                                                                          d_cnt, d_base, g->aseg, g->n_active);
     GEO_CHECK(cudaGetLastError());
 
+    // the step kernels' work list: fluid cells in cell order, 32 per warp (padding lanes
+    // hold 0xFFFFFFFF), and per warp its boundary bits and first boundary-table index
+    fluid_count_kernel<<<grid_for(g->nseg_padded, 256), 256, 0, s>>>(g->nseg_padded, g->seg, d_cnt);
+    GEO_CHECK(cudaGetLastError());
+    GEO_CHECK(exclusive_scan(d_cnt, d_base, g->nseg_padded, s));
+    GEO_CHECK(cudaMemcpy(&h_last[0], d_base + g->nseg_padded - 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    GEO_CHECK(cudaMemcpy(&h_last[1], d_cnt + g->nseg_padded - 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    {
+        const long long nf = (long long)(h_last[0] + h_last[1]);
+        g->n_fwarps = (nf + 31) / 32;
+        g->n_fwarps_padded = std::max<long long>(kMaxWarpsPerBlock,
+            (g->n_fwarps + kMaxWarpsPerBlock - 1) / kMaxWarpsPerBlock * kMaxWarpsPerBlock);
+    }
+    GEO_CHECK(cudaMalloc(&g->fcell, sizeof(uint32_t) * 32 * g->n_fwarps_padded));
+    GEO_CHECK(cudaMalloc(&g->fwarp, sizeof(uint2) * g->n_fwarps_padded));
+    GEO_CHECK(cudaMemsetAsync(g->fcell, 0xFF, sizeof(uint32_t) * 32 * g->n_fwarps_padded, s));
+    fluid_scatter_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, g->seg, d_base, g->fcell);
+    GEO_CHECK(cudaGetLastError());
+    fwarp_kernel<<<grid_for(g->n_fwarps_padded * 32, 256), 256, 0, s>>>(g->n_fwarps_padded, g->fcell, g->seg,
+                                                                          g->fwarp);
+    GEO_CHECK(cudaGetLastError());
+
     if (g->n_boundary > 0) {
         const long long nb = g->n_boundary;
         GEO_CHECK(cudaMalloc(&g->bmask, sizeof(uint32_t) * nb));
@@ -442,6 +511,7 @@ cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_
     g->n_fluid = (long long)h_ctr[0];
     g->n_links_cli = (long long)h_ctr[1];
     g->bytes = n + sizeof(uint4) * (g->nseg_padded + g->n_active_padded) +
+               (sizeof(uint32_t) * 32 + sizeof(uint2)) * g->n_fwarps_padded +
                (sizeof(uint32_t) * 2 + sizeof(long long)) * g->n_boundary +
                (sizeof(double) + (c_double ? 8 : 4)) * g->n_links;
 
@@ -482,22 +552,24 @@ cudaError_t export_wall_distances(const GeometryDev &g, int kdir, double *qk, cu
 __global__ void final_reduce_kernel(const InstanceDev *__restrict__ table, const int *__restrict__ tile_begin,
                                     const int *__restrict__ tile_count, double *__restrict__ out)
 {
-    __shared__ double sm[256][4];
+    constexpr int D = RED_F + 3;  // slots in use
+    __shared__ double sm[256][D];
     const int inst = blockIdx.x;
     const double *p = table[inst].partials;
     const int nt = tile_count[inst];
     (void)tile_begin;
-    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    double a[D];
+    for (int d = 0; d < D; ++d) a[d] = 0.0;
     for (int t = threadIdx.x; t < nt; t += blockDim.x)
-        for (int d = 0; d < 4; ++d) a[d] += p[(long long)t * 4 + d];
-    for (int d = 0; d < 4; ++d) sm[threadIdx.x][d] = a[d];
+        for (int d = 0; d < D; ++d) a[d] += p[(long long)t * kRedSlots + d];
+    for (int d = 0; d < D; ++d) sm[threadIdx.x][d] = a[d];
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w)
-            for (int d = 0; d < 4; ++d) sm[threadIdx.x][d] += sm[threadIdx.x + w][d];
+            for (int d = 0; d < D; ++d) sm[threadIdx.x][d] += sm[threadIdx.x + w][d];
         __syncthreads();
     }
-    if (threadIdx.x < 4) out[(long long)inst * 4 + threadIdx.x] = sm[0][threadIdx.x];
+    if (threadIdx.x < kRedSlots) out[(long long)inst * kRedSlots + threadIdx.x] = threadIdx.x < D ? sm[0][threadIdx.x] : 0.0;
 }
 
 cudaError_t launch_final_reduce(const InstanceDev *table, const int *tile_begin, const int *tile_count, int n_inst,

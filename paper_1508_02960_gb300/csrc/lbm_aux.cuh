@@ -182,7 +182,8 @@ __global__ void export_kernel(const InstanceDev *__restrict__ table, int inst, i
 // Moments of the stored post-collision state of every fluid cell, one warp per work
 // chunk.  mode 0: write the velocity component `comp` to out[cell] of fluid cells (the
 // caller clears out first).  mode 1: chunk partial sums (drho, u_x, u_y, u_z) into
-// I.partials, in the same fixed order as the step kernel's.
+// I.partials, in the same fixed order as the step kernel's; the force slots, which only a
+// step defines, are written as 0.
 template <int STORE>
 __global__ void __launch_bounds__(256) moments_kernel(const InstanceDev *__restrict__ table,
                                                       const TileDev *__restrict__ chunks, int nchunks, int chunk_segs,
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(256) moments_kernel(const InstanceDev *__restr
 #pragma unroll
             for (int d = 0; d < 4; ++d) a[d] = warp_sum(a[d]);
             if (lane == 0)
-                for (int d = 0; d < 4; ++d) I.partials[(long long)chunk.local * 4 + d] = a[d];
+                for (int d = 0; d < kRedSlots; ++d) I.partials[(long long)chunk.local * kRedSlots + d] = d < 4 ? a[d] : 0.0;
         }
     }
 }

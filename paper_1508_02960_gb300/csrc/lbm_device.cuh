@@ -204,6 +204,10 @@ __host__ __device__ __forceinline__ uint32_t fast_div(uint32_t n, const FastDiv 
 //   seg[s].x  bit l set: cell 32s+l is solid or beyond the box (no work)
 //   seg[s].y  bit l set: cell 32s+l is fluid with at least one solid pull source
 //   seg[s].z  index of the first such boundary cell of the segment in the boundary table
+// The step kernels take the fluid cells themselves, in cell order, 32 per warp: fcell[32w +
+// l] is the cell of lane l of fluid warp w (0xFFFFFFFF past the last fluid cell), fwarp[w].x
+// bit l set when that cell is a boundary cell, fwarp[w].y the boundary-table index of the
+// warp's first boundary cell.
 // Boundary cell b: bmask[b] bit k set when x - e_k is solid (the pull of direction k hits
 // the wall), boff[b] the index of its first link; its links are ordered by k.  Link l:
 // linkc[l] = CLI coefficient (1-2q)/(1+2q) (0 where CLI falls back to SBB), linkB[l] =
@@ -213,15 +217,18 @@ struct InstanceDev {
     void *f0, *f1;           // populations [19][ks] (direction k at k * ks); AA uses f0 only
     const uint4 *seg;        // [nseg]
     const uint4 *aseg;       // [n_active_padded]: seg entries of segments holding fluid, .w = segment
+    const uint32_t *fcell;   // [32 n_fwarps_padded]
+    const uint2 *fwarp;      // [n_fwarps_padded]
     const uint32_t *bmask;   // [n_boundary]
     const uint32_t *boff;    // [n_boundary]
     const void *linkc;       // [n_links], type R
     void *linkB;             // [n_links], type T (AA layout)
-    double *partials;        // [n_tiles of this instance][4]
+    double *partials;        // [n_tiles of this instance][kRedSlots]
     long long ncells;
     uint32_t n32;            // ncells
     uint32_t ks;             // elements between consecutive direction arrays (>= ncells; 19 ks < 2^32)
     uint32_t n_active;       // entries of aseg
+    uint32_t n_fwarps;       // fluid warps (entries of fwarp before the padding)
     // interior cells (no periodic wrap): element offset of the pulled population of
     // direction k relative to the cell, and (AA) of the pushed one (mod 2^32)
     uint32_t pull_off[Q];
@@ -237,8 +244,9 @@ struct InstanceDev {
     double delta_rho, rho0;
 };
 
-// A tile: blockDim/32 consecutive entries of an instance's active-segment list (the
-// segments that hold at least one fluid cell), processed by one thread block.
+// A tile: consecutive entries of one instance's work list, processed by one thread block:
+// for the step kernels kTileSegs fluid warps (seg0 = the first), for the other kernels
+// blockDim/32 entries of the active-segment list (the segments holding fluid).
 struct TileDev {
     int inst;
     int local;       // tile index within its instance (partials slot)
@@ -247,14 +255,18 @@ struct TileDev {
 
 enum { KIND_AB = 0, KIND_AA_PULL = 1, KIND_AA_LOCAL = 2 };
 
-// Step-kernel tiling: one block of kStepWarps warps per tile; each warp takes
-// kSegsPerWarp consecutive entries of the active-segment list.
+// Step-kernel tiling: a tile is kStepWarps consecutive work items (32 fluid cells each),
+// one per warp of a kStepWarps-warp block.
 constexpr int kStepWarps = 4;
-constexpr int kSegsPerWarp = 1;
-constexpr int kTileSegs = kStepWarps * kSegsPerWarp;
+constexpr int kTileSegs = kStepWarps;
 enum { COLL_SRT = 0, COLL_TRT = 1, COLL_MRT = 2 };
 
 // Status word bits: a reduction saw a diverged cell; a bounded wait ran out.
 enum { STATUS_DIVERGED = 1u, STATUS_TIMEOUT = 2u };
+
+// FP64 reduction slots per tile and per instance: sum of (rho - rho0), of u_x, u_y, u_z
+// over fluid cells, then the x, y, z momentum exchanged with the solid in the step
+// (drag force, Sec. 3), and one unused slot (64-byte rows).
+enum { RED_DRHO = 0, RED_U = 1, RED_F = 4, kRedSlots = 8 };
 
 }  // namespace lbm

@@ -3,6 +3,8 @@
 // formats compile in parallel.
 #pragma once
 
+#include <utility>
+
 #include "lbm_aux.cuh"
 #include "lbm_internal.h"
 #include "lbm_step.cuh"
@@ -10,20 +12,46 @@
 namespace lbm {
 namespace detail {
 
-template <int STORE, int COLL, int KIND>
-cudaError_t step_one(const Launch &L, int flip, int reduce, unsigned *status, const InstanceDev *one)
+// Launch of a step kernel with programmatic stream serialisation: the kernel may start
+// (up to its wait on the previous step) while the previous kernel of the stream is still
+// running.  Captured into a graph, this becomes a programmatic dependency edge.
+template <typename... P, typename... A>
+cudaError_t launch_step(void (*kernel)(P...), const Launch &L, A &&...args)
 {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)L.grid);
+    cfg.blockDim = dim3((unsigned)L.block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = L.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
+template <int STORE, int COLL, int KIND, bool RED>
+cudaError_t step_red(const Launch &L, int flip, unsigned *status, const InstanceDev *one)
+{
+    cudaError_t e;
     if (one) {  // a single instance: parameters travel in the constant bank
-        step_kernel<COLL, STORE, KIND, false><<<L.grid, L.block, 0, L.stream>>>(L.table, *one, L.tiles, L.ntiles, flip,
-                                                                               reduce, status);
+        e = launch_step(step_kernel<COLL, STORE, KIND, false, RED>, L, L.table, *one, L.tiles, L.ntiles, flip, status);
     } else if constexpr (KIND == KIND_AB) {
         static const InstanceDev unused{};
-        step_kernel<COLL, STORE, KIND, true><<<L.grid, L.block, 0, L.stream>>>(L.table, unused, L.tiles, L.ntiles, flip,
-                                                                              reduce, status);
+        e = launch_step(step_kernel<COLL, STORE, KIND, true, RED>, L, L.table, unused, L.tiles, L.ntiles, flip, status);
     } else {
         return cudaErrorInvalidValue;  // the AA layout runs single instances only
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+template <int STORE, int COLL, int KIND>
+cudaError_t step_one(const Launch &L, int flip, int reduce, unsigned *status, const InstanceDev *one)
+{
+    return reduce ? step_red<STORE, COLL, KIND, true>(L, flip, status, one)
+                  : step_red<STORE, COLL, KIND, false>(L, flip, status, one);
 }
 
 template <int STORE>
@@ -43,19 +71,20 @@ cudaError_t step(int coll, int kind, const Launch &L, int flip, int reduce, unsi
     }
 }
 
+// The single-instance, non-reducing kernel of (coll, kind): the one a time step runs.
 template <int STORE>
 const void *step_ptr(int coll, int kind)
 {
     switch (coll * 3 + kind) {
-    case COLL_SRT * 3 + KIND_AB: return (const void *)step_kernel<COLL_SRT, STORE, KIND_AB, false>;
-    case COLL_SRT * 3 + KIND_AA_PULL: return (const void *)step_kernel<COLL_SRT, STORE, KIND_AA_PULL, false>;
-    case COLL_SRT * 3 + KIND_AA_LOCAL: return (const void *)step_kernel<COLL_SRT, STORE, KIND_AA_LOCAL, false>;
-    case COLL_TRT * 3 + KIND_AB: return (const void *)step_kernel<COLL_TRT, STORE, KIND_AB, false>;
-    case COLL_TRT * 3 + KIND_AA_PULL: return (const void *)step_kernel<COLL_TRT, STORE, KIND_AA_PULL, false>;
-    case COLL_TRT * 3 + KIND_AA_LOCAL: return (const void *)step_kernel<COLL_TRT, STORE, KIND_AA_LOCAL, false>;
-    case COLL_MRT * 3 + KIND_AB: return (const void *)step_kernel<COLL_MRT, STORE, KIND_AB, false>;
-    case COLL_MRT * 3 + KIND_AA_PULL: return (const void *)step_kernel<COLL_MRT, STORE, KIND_AA_PULL, false>;
-    case COLL_MRT * 3 + KIND_AA_LOCAL: return (const void *)step_kernel<COLL_MRT, STORE, KIND_AA_LOCAL, false>;
+    case COLL_SRT * 3 + KIND_AB: return (const void *)step_kernel<COLL_SRT, STORE, KIND_AB, false, false>;
+    case COLL_SRT * 3 + KIND_AA_PULL: return (const void *)step_kernel<COLL_SRT, STORE, KIND_AA_PULL, false, false>;
+    case COLL_SRT * 3 + KIND_AA_LOCAL: return (const void *)step_kernel<COLL_SRT, STORE, KIND_AA_LOCAL, false, false>;
+    case COLL_TRT * 3 + KIND_AB: return (const void *)step_kernel<COLL_TRT, STORE, KIND_AB, false, false>;
+    case COLL_TRT * 3 + KIND_AA_PULL: return (const void *)step_kernel<COLL_TRT, STORE, KIND_AA_PULL, false, false>;
+    case COLL_TRT * 3 + KIND_AA_LOCAL: return (const void *)step_kernel<COLL_TRT, STORE, KIND_AA_LOCAL, false, false>;
+    case COLL_MRT * 3 + KIND_AB: return (const void *)step_kernel<COLL_MRT, STORE, KIND_AB, false, false>;
+    case COLL_MRT * 3 + KIND_AA_PULL: return (const void *)step_kernel<COLL_MRT, STORE, KIND_AA_PULL, false, false>;
+    case COLL_MRT * 3 + KIND_AA_LOCAL: return (const void *)step_kernel<COLL_MRT, STORE, KIND_AA_LOCAL, false, false>;
     default: return nullptr;
     }
 }

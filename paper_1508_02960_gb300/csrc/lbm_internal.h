@@ -51,6 +51,9 @@ struct GeometryDev {
     uint4 *seg = nullptr;          // [nseg_padded]
     uint4 *aseg = nullptr;         // [n_active_padded] segments holding fluid: {x, y, z, segment}
     long long n_active = 0, n_active_padded = 0;
+    uint32_t *fcell = nullptr;     // [32 n_fwarps_padded] fluid cells in cell order (pad 0xFFFFFFFF)
+    uint2 *fwarp = nullptr;        // [n_fwarps_padded] per 32 fluid cells: boundary bits, first boundary
+    long long n_fwarps = 0, n_fwarps_padded = 0;
     uint32_t *bmask = nullptr;     // [n_boundary]
     uint32_t *boff = nullptr;      // [n_boundary]
     long long *bcell = nullptr;    // [n_boundary] cell index of each boundary cell
@@ -70,8 +73,8 @@ void free_geometry(GeometryDev *g);
 // Scatter link q values into qk[ncells] for link direction kdir (NaN elsewhere).
 cudaError_t export_wall_distances(const GeometryDev &g, int kdir, double *qk, cudaStream_t s);
 
-// Deterministic final sum of an instance's tile partials: out[4] = sum over tiles
-// t0 .. t0+nt-1 of partials[t][0..3], in a fixed order.  One block per instance.
+// Deterministic final sum of an instance's tile partials: out[kRedSlots] = sum over
+// tiles t0 .. t0+nt-1 of partials[t][...], in a fixed order.  One block per instance.
 cudaError_t launch_final_reduce(const InstanceDev *table, const int *tile_begin, const int *tile_count,
                                 int n_inst, double *out, cudaStream_t s);
 

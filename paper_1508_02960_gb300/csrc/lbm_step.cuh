@@ -1,10 +1,11 @@
 // lbm_step.cuh -- the fused D3Q19 time step (Sec. 2: stream first, then collide, the two
 // fused so that macroscopic values are never stored).
 //
-// Work decomposition.  An instance's cells are grouped in 32-cell segments; only the
-// segments holding fluid are listed (all-solid segments cost nothing).  One block per
-// tile of consecutive list entries; each warp (one lane per cell) takes kSegsPerWarp of
-// them and issues all their pulls before finishing the first, for load/compute overlap.
+// Work decomposition.  An instance's fluid cells, in cell order, are dealt out 32 per
+// warp (solid cells cost nothing and every lane has a cell, up to the last warp); runs of
+// consecutive fluid cells keep the loads of a warp coalesced.  One block per tile of
+// kStepWarps such warps; each warp (one lane per cell) takes kSegsPerWarp of them and
+// issues all their pulls before finishing the first, for load/compute overlap.
 //
 // Per fluid cell x and direction k (all arithmetic on deviations g = f - w rho0):
 //   pull      g_k <- g~_k(x - e_k), plus +w_k delta_rho when the pull crosses the x
@@ -185,13 +186,17 @@ __device__ __forceinline__ void collide(R (&g)[Q], const Par<R> &p, const R *rat
 }
 
 // Process one cell whose 19 pulled populations are in g[] (already shifted): walls,
-// moments, collision, stores.  Returns the moments for the reduction through rd..rz.
-template <int COLL, int STORE, int KIND, typename R>
+// moments, collision, stores.  When reduce is set, returns the moments through rd..rz and
+// the momentum the cell's wall links hand to the solid in this step through fm[3]: a link
+// (x, kbar) with x - e_k solid carries g~_kbar(x) into the wall and brings the new g_k
+// back, so the solid gains e_kbar (g~_kbar(x) + g_k).  (Deviations suffice: the 2 w rho0
+// of full populations sums to zero over a periodic domain.)
+template <int COLL, int STORE, int KIND, bool RED, typename R>
 __device__ __forceinline__ void finish_cell(R (&g)[Q], const Par<R> &P, const R *rates, uint32_t cell, uint32_t x,
                                             const uint32_t *push_off, uint32_t wm, uint32_t off,
                                             const typename Store<STORE>::T *fs, typename Store<STORE>::T *fd,
-                                            const R *linkc, typename Store<STORE>::T *linkB, int reduce,
-                                            unsigned *status, R &rd, R &rx, R &ry, R &rz)
+                                            const R *linkc, typename Store<STORE>::T *linkB, unsigned *status,
+                                            R &rd, R &rx, R &ry, R &rz, R (&fm)[3])
 {
     using S = Store<STORE>;
     using T = typename S::T;
@@ -217,12 +222,18 @@ __device__ __forceinline__ void finish_cell(R (&g)[Q], const Par<R> &P, const R 
                 }
             }
             g[k] = v;
+            if constexpr (RED) {  // e_kbar = -e_k
+                const R m = C + v;
+                if (ex(k)) fm[0] += ex(k) > 0 ? -m : m;
+                if (ey(k)) fm[1] += ey(k) > 0 ? -m : m;
+                if (ez(k)) fm[2] += ez(k) > 0 ? -m : m;
+            }
         }
     }
 
     R drho, ux, uy, uz;
     moments(g, P.irho0, drho, ux, uy, uz);
-    if (reduce) {
+    if constexpr (RED) {
         rd = drho;
         rx = ux;
         ry = uy;
@@ -278,8 +289,148 @@ __device__ __forceinline__ void finish_cell(R (&g)[Q], const Par<R> &P, const R 
     }
 }
 
-// Instance parameters: from the device table (batches), or from a kernel argument in the
-// constant bank (a single instance).
+// One warp's work item: 32 fluid cells of the work list (w = its index), their raw pulled
+// values (see pull_item) and what the finish needs.
+struct WarpItem {
+    uint32_t cell, x;  // this lane's cell (0xFFFFFFFF: padding lane) and its x
+    uint2 wd;          // boundary bits of the 32 lanes, first boundary-table index
+    bool inner;        // every lane away from the y and z faces
+};
+
+// Locate one work item: this lane's cell and coordinates, the warp's boundary bits, and
+// whether every lane is away from the y and z faces.  Reads only the work list, which no
+// step writes.
+template <typename R>
+__device__ __forceinline__ void locate_item(const InstanceDev &I, const Par<R> &P, uint32_t w, int lane, WarpItem &it)
+{
+    it.wd = I.fwarp[w];
+    it.cell = I.fcell[w * 32u + (uint32_t)lane];
+    const bool live = it.cell != 0xFFFFFFFFu;
+    const uint32_t yz = fast_div(it.cell, P.dnx);
+    it.x = it.cell - yz * P.nx;
+    const uint32_t z = fast_div(yz, P.dny);
+    const uint32_t y = yz - z * P.ny;
+    const bool in_yz = !live || (y - 1u < P.ny - 2u && z - 1u < P.nz - 2u);
+    it.inner = __all_sync(0xffffffffu, in_yz);
+}
+
+// Issue the 19 pulls of a located work item into raw[] (storage type, converted in
+// finish_item).  Unconditional: solid sources hold 0.  Warps whose cells are all away from
+// the y and z faces index through precomputed offsets (cell + pull_off[k], with a fix-up on
+// the first and last cell of a row); the others through their periodic neighbours.
+template <int STORE, int KIND, typename R>
+__device__ __forceinline__ void pull_item(const InstanceDev &I, const Par<R> &P, const typename Store<STORE>::T *fs,
+                                          const WarpItem &it, typename Store<STORE>::T (&raw)[Q])
+{
+    if (it.cell == 0xFFFFFFFFu) return;
+    if (KIND != KIND_AA_LOCAL && it.inner) {
+        const uint32_t cxm = it.x == 0 ? P.nx : 0u, cxp = it.x == P.nx - 1 ? P.nx : 0u;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            uint32_t idx = it.cell + I.pull_off[k];
+            if (ex(k) == 1) idx += cxm;   // x - 1 wraps to the end of the row
+            if (ex(k) == -1) idx -= cxp;  // x + 1 wraps to the start of the row
+            raw[k] = __ldg(fs + idx);
+        }
+    } else {
+        const Coord co = coord_of(P, it.cell);
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            uint32_t idx;
+            if constexpr (KIND == KIND_AA_LOCAL) idx = (uint32_t)k * P.ks + it.cell;
+            else if constexpr (KIND == KIND_AA_PULL) idx = (uint32_t)opp(k) * P.ks + co.pull(k);
+            else idx = (uint32_t)k * P.ks + co.pull(k);
+            raw[k] = __ldg(fs + idx);
+        }
+    }
+}
+
+// Per-lane FP64 accumulators of the reduction (RED steps).
+struct RedAcc {
+    double v[RED_F + 3];
+};
+
+// Finish one work item pulled by pull_item: convert, pressure shift of the pulls that
+// crossed the x boundary, walls, collision, stores; with RED, add the lane's moments and
+// momentum exchange to acc.
+template <int COLL, int STORE, int KIND, bool RED, typename R>
+__device__ __forceinline__ void finish_item(const InstanceDev &I, const Par<R> &P, const R *rates,
+                                            const typename Store<STORE>::T (&raw)[Q], const WarpItem &it, int lane,
+                                            const typename Store<STORE>::T *fs, typename Store<STORE>::T *fd,
+                                            unsigned *status, RedAcc &acc)
+{
+    using S = Store<STORE>;
+    using T = typename S::T;
+    if (it.cell == 0xFFFFFFFFu) return;
+    R g[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) g[k] = S::cvt(raw[k], P.isc);
+    if (it.x == 0) {
+#pragma unroll
+        for (int k = 0; k < Q; ++k)
+            if (ex(k) == 1) g[k] += R(weight(k)) * P.dshift;
+    }
+    if (it.x == P.nx - 1) {
+#pragma unroll
+        for (int k = 0; k < Q; ++k)
+            if (ex(k) == -1) g[k] -= R(weight(k)) * P.dshift;
+    }
+    uint32_t wm = 0u, off = 0u;
+    if ((it.wd.x >> lane) & 1u) {
+        const uint32_t b = it.wd.y + __popc(it.wd.x & ((1u << lane) - 1u));
+        wm = I.bmask[b];
+        off = I.boff[b];
+    }
+    R rd = R(0), rx = R(0), ry = R(0), rz = R(0);
+    R fm[3] = {R(0), R(0), R(0)};
+    finish_cell<COLL, STORE, KIND, RED, R>(g, P, rates, it.cell, it.x, it.inner ? I.push_off : nullptr, wm, off, fs,
+                                           fd, reinterpret_cast<const R *>(I.linkc),
+                                           reinterpret_cast<T *>(I.linkB), status, rd, rx, ry, rz, fm);
+    if constexpr (RED) {
+        acc.v[RED_DRHO] += (double)rd;
+        acc.v[RED_U + 0] += (double)rx;
+        acc.v[RED_U + 1] += (double)ry;
+        acc.v[RED_U + 2] += (double)rz;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) acc.v[RED_F + d] += (double)fm[d];
+    }
+}
+
+// Block sum of the lanes' accumulators of one tile (fixed shuffle tree, then the warps in
+// order) to partials[tile]; every thread of the block calls it.
+__device__ __forceinline__ void reduce_tile(const RedAcc &acc, double *partials, long long tile)
+{
+    __shared__ double red[kStepWarps][RED_F + 3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double v[RED_F + 3];
+#pragma unroll
+    for (int d = 0; d < RED_F + 3; ++d) v[d] = warp_sum(acc.v[d]);
+    if (lane == 0)
+#pragma unroll
+        for (int d = 0; d < RED_F + 3; ++d) red[warp][d] = v[d];
+    __syncthreads();
+    if (threadIdx.x < RED_F + 3) {
+        double sum = 0.0;
+        for (int w = 0; w < kStepWarps; ++w) sum += red[w][threadIdx.x];
+        partials[tile * kRedSlots + threadIdx.x] = sum;
+    }
+}
+
+template <int COLL, typename R> __device__ __forceinline__ void load_rates(const InstanceDev &I, R (&rates)[Q])
+{
+    if constexpr (COLL == COLL_MRT) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) rates[i] = R(I.s[i]) / R(mrt_norm2(i));
+    }
+}
+
+// Programmatic dependent launch (sm_90 and later): a step lets the next step's blocks be
+// scheduled as soon as all of its own blocks are running, and a step waits for the
+// previous one to complete (with its memory visible) only before its first population
+// load.  Between the two, a block reads its tile and work list, which no step writes.
+__device__ __forceinline__ void allow_next_step() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void wait_previous_step() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <bool BATCH>
 __device__ __forceinline__ const InstanceDev &instance_of(const InstanceDev *table, const InstanceDev &one, int i)
 {
@@ -287,24 +438,22 @@ __device__ __forceinline__ const InstanceDev &instance_of(const InstanceDev *tab
     else return one;
 }
 
-// The fused step.  One block per tile: kStepWarps warps, each taking kSegsPerWarp
-// consecutive entries of the instance's active-segment list.  A warp first issues the
-// pulls of all its segments, then finishes them one after the other.  Warps whose cells
-// are all away from the y and z faces use precomputed offsets (cell + pull_off[k], with a
-// fix-up on the first and last cell of a row); the others index through their periodic
-// neighbours.  flip selects the A-B buffer pair (src = f[phase ^ flip]); reduce != 0 makes
-// every tile write its FP64 partial sums (drho, u_x, u_y, u_z) and flags diverged cells in
-// status[instance].
-template <int COLL, int STORE, int KIND, bool BATCH>
+// The fused step.  One block per tile of kStepWarps work items (32 fluid cells each), one
+// item per warp.  A single instance's parameters travel by value (constant bank); a
+// batch's come from the device table (A-B layout only).  flip selects the A-B buffer pair
+// (src = f[phase ^ flip]).  The RED variant (the step that ends a chunk) also makes every
+// tile write its FP64 partial sums (the kRedSlots slots: drho, u_x, u_y, u_z and the
+// momentum exchanged with the solid) and flags diverged cells in status[instance]; the
+// other steps carry none of that code.
+template <int COLL, int STORE, int KIND, bool BATCH, bool RED>
 __global__ void __launch_bounds__(kStepWarps * 32, step_min_blocks<STORE, KIND>())
     step_kernel(const InstanceDev *__restrict__ table, const __grid_constant__ InstanceDev one,
-                const TileDev *__restrict__ tiles, int ntiles, int flip, int reduce, unsigned *__restrict__ status)
+                const TileDev *__restrict__ tiles, int ntiles, int flip, unsigned *__restrict__ status)
 {
     using S = Store<STORE>;
     using T = typename S::T;
     using R = typename S::R;
-    constexpr int NS = kSegsPerWarp;
-    __shared__ double red[kStepWarps][4];
+    allow_next_step();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int t = blockIdx.x;
     if (t >= ntiles) return;
@@ -312,118 +461,25 @@ __global__ void __launch_bounds__(kStepWarps * 32, step_min_blocks<STORE, KIND>(
     const InstanceDev &I = instance_of<BATCH>(table, one, tile.inst);
     const Par<R> P = load_par<R>(I);
     R rates[Q];
-    if constexpr (COLL == COLL_MRT) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) rates[i] = R(I.s[i]) / R(mrt_norm2(i));
-    }
-    const uint32_t KS = P.ks;
-    T *fs;  // state read this step
-    T *fd;  // state written this step
+    load_rates<COLL>(I, rates);
+    const T *fs;  // state read this step
+    T *fd;        // state written this step
     if constexpr (KIND == KIND_AB) {
         const int cur = I.phase ^ flip;
-        fs = reinterpret_cast<T *>(cur ? I.f1 : I.f0);
+        fs = reinterpret_cast<const T *>(cur ? I.f1 : I.f0);
         fd = reinterpret_cast<T *>(cur ? I.f0 : I.f1);
     } else {
-        fs = fd = reinterpret_cast<T *>(I.f0);
+        fd = reinterpret_cast<T *>(I.f0);
+        fs = fd;
     }
-
-    // descriptors of this warp's segments (entries past the list are all solid)
-    const uint32_t e0 = (uint32_t)tile.seg0 + (uint32_t)(warp * NS);
-    uint4 meta[NS];
-#pragma unroll
-    for (int s = 0; s < NS; ++s)
-        meta[s] = e0 + s < I.n_active ? I.aseg[e0 + s] : make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
-
-    // issue every pull of the warp's cells (unconditional: solid sources hold 0)
-    R g[NS][Q];
-    uint32_t cell[NS], xs[NS];
-    bool inner[NS];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-        cell[s] = meta[s].w * 32u + lane;
-        const uint32_t yz = fast_div(cell[s], P.dnx);
-        const uint32_t x = cell[s] - yz * P.nx;
-        const uint32_t z = fast_div(yz, P.dny);
-        const uint32_t y = yz - z * P.ny;
-        xs[s] = x;
-        // every lane away from the y and z faces (solid lanes do not matter)
-        const bool in_yz = ((meta[s].x >> lane) & 1u) || (y - 1u < P.ny - 2u && z - 1u < P.nz - 2u);
-        inner[s] = __all_sync(0xffffffffu, in_yz);
-        if ((meta[s].x >> lane) & 1u) continue;
-        if (KIND != KIND_AA_LOCAL && inner[s]) {
-            const uint32_t cxm = x == 0 ? P.nx : 0u, cxp = x == P.nx - 1 ? P.nx : 0u;
-#pragma unroll
-            for (int k = 0; k < Q; ++k) {
-                uint32_t idx = cell[s] + I.pull_off[k];
-                if (ex(k) == 1) idx += cxm;   // x - 1 wraps to the end of the row
-                if (ex(k) == -1) idx -= cxp;  // x + 1 wraps to the start of the row
-                g[s][k] = S::load(fs + idx, P.isc);
-            }
-        } else {
-            const Coord co = coord_of(P, cell[s]);
-#pragma unroll
-            for (int k = 0; k < Q; ++k) {
-                uint32_t idx;
-                if constexpr (KIND == KIND_AA_LOCAL) idx = (uint32_t)k * KS + cell[s];
-                else if constexpr (KIND == KIND_AA_PULL) idx = (uint32_t)opp(k) * KS + co.pull(k);
-                else idx = (uint32_t)k * KS + co.pull(k);
-                g[s][k] = S::load(fs + idx, P.isc);
-            }
-        }
-        // pressure shift of pulls that cross the x boundary
-        if (x == 0) {
-#pragma unroll
-            for (int k = 0; k < Q; ++k)
-                if (ex(k) == 1) g[s][k] += R(weight(k)) * P.dshift;
-        }
-        if (x == P.nx - 1) {
-#pragma unroll
-            for (int k = 0; k < Q; ++k)
-                if (ex(k) == -1) g[s][k] -= R(weight(k)) * P.dshift;
-        }
-    }
-
-    R rd = R(0), rx = R(0), ry = R(0), rz = R(0);
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-        if ((meta[s].x >> lane) & 1u) continue;
-        uint32_t wm = 0u, off = 0u;
-        if ((meta[s].y >> lane) & 1u) {
-            const uint32_t b = meta[s].z + __popc(meta[s].y & ((1u << lane) - 1u));
-            wm = I.bmask[b];
-            off = I.boff[b];
-        }
-        finish_cell<COLL, STORE, KIND, R>(g[s], P, rates, cell[s], xs[s], inner[s] ? I.push_off : nullptr, wm, off,
-                                          fs, fd, reinterpret_cast<const R *>(I.linkc),
-                                          reinterpret_cast<T *>(I.linkB), reduce, status + tile.inst, rd, rx, ry,
-                                          rz);
-        if (reduce) {  // lane sums over the warp's segments, in order
-            a0 += (double)rd;
-            a1 += (double)rx;
-            a2 += (double)ry;
-            a3 += (double)rz;
-        }
-    }
-
-    if (reduce) {  // deterministic: fixed shuffle tree, then the block's warps in order
-        a0 = warp_sum(a0);
-        a1 = warp_sum(a1);
-        a2 = warp_sum(a2);
-        a3 = warp_sum(a3);
-        if (lane == 0) {
-            red[warp][0] = a0;
-            red[warp][1] = a1;
-            red[warp][2] = a2;
-            red[warp][3] = a3;
-        }
-        __syncthreads();
-        if (threadIdx.x < 4) {
-            double sum = 0.0;
-            for (int w = 0; w < kStepWarps; ++w) sum += red[w][threadIdx.x];
-            I.partials[(size_t)tile.local * 4 + threadIdx.x] = sum;
-        }
-    }
+    WarpItem it;
+    locate_item<R>(I, P, (uint32_t)tile.seg0 + (uint32_t)warp, lane, it);
+    wait_previous_step();
+    T raw[Q];
+    pull_item<STORE, KIND, R>(I, P, fs, it, raw);
+    RedAcc acc{};
+    finish_item<COLL, STORE, KIND, RED, R>(I, P, rates, raw, it, lane, fs, fd, status + tile.inst, acc);
+    if constexpr (RED) reduce_tile(acc, I.partials, tile.local);
 }
 
 }  // namespace lbm

@@ -48,8 +48,12 @@ def test_bench_cell_128_fp32_against_oracle(capi, orc, layout):
         ctx.set_populations(f0)
         ctx.step(21)
         f = ctx.get_populations()
-    ref, _, _ = orc.run(solid, f0, 21, q=q, **kw)
+        o = ctx.observables()
+    Fref = np.zeros(3)
+    ref, _, _ = orc.run(solid, f0, 21, q=q, force=Fref, **kw)
     assert _rel(f, ref, solid) <= 1e-5
+    F = np.array([o["F_x"], o["F_y"], o["F_z"]])
+    assert np.abs(F - Fref).max() <= 2e-4 * np.abs(Fref).max(), (F, Fref)
 
 
 @pytest.mark.parametrize("which", ["sphere", "pack40"])
@@ -113,10 +117,13 @@ def test_time_average_and_perturbed_start(capi):
         assert abs(ua[:, fluid].mean()) < 1e-4                             # centred perturbation
         assert abs(a.moment_sums()[0]) < 1e-6 * fluid.sum()                # rho = rho0 everywhere
         # the average of 4 samples of 50 steps equals the mean of the 4 sampled U values
-        us = []
+        us, fs = [], []
         for _ in range(4):
             b.step(50)
-            us.append(b.observables()["U_sup"])
+            o = b.observables()
+            us.append(o["U_sup"])
+            fs.append(o["F_x"])
         avg = a.average(4, 50)
         assert avg["status"] == capi.OK and avg["steps"] == 200
         assert avg["U_sup"] == pytest.approx(np.mean(us), rel=1e-12, abs=0)
+        assert avg["F_x"] == pytest.approx(np.mean(fs), rel=1e-12, abs=0)

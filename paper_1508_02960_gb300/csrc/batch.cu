@@ -422,6 +422,10 @@ lbm_status Batch::init_equilibrium(int i)
         CK(ops().init(d_table_, j, in.geo.ncells, layout_, cur_of(in), in.desc.perturb_u,
                       (unsigned long long)in.desc.seed, stream_));
         ++launches_;
+        if (layout_ == LBM_LAYOUT_AB && in.geo.n_boundary > 0) {
+            CK(ops().wall_prepare(d_table_, j, in.geo.n_boundary, in.geo.bcell, cur_of(in), stream_));
+            ++launches_;
+        }
         in.have_sums = false;
         in.have_force = false;
         in.sums_pending = false;
@@ -616,6 +620,10 @@ lbm_status Batch::set_f64(int i, const double *host)
         CK(ops().import_dir(d_table_, i, n, layout_, cur_of(in), k, d_stage_, stream_));
         ++launches_;
     }
+    if (layout_ == LBM_LAYOUT_AB && in.geo.n_boundary > 0) {
+        CK(ops().wall_prepare(d_table_, i, in.geo.n_boundary, in.geo.bcell, cur_of(in), stream_));
+        ++launches_;
+    }
     in.have_sums = false;
     in.have_force = false;
     in.sums_pending = false;
@@ -734,7 +742,7 @@ lbm_status Batch::save(int i, const char *path)
     CkptHeader h;
     std::memset(&h, 0, sizeof(h));
     std::memcpy(h.magic, "LBMGB300", 8);
-    h.version = 1;
+    h.version = 2;  // 2: A-B solid slots hold the wall terms of the next step
     h.nx = in.desc.nx;
     h.ny = in.desc.ny;
     h.nz = in.desc.nz;
@@ -768,7 +776,7 @@ lbm_status Batch::load(int i, const char *path)
     FILE *f = std::fopen(path, "rb");
     if (!f) return fail(LBM_ERR_IO, std::string("cannot open ") + path);
     CkptHeader h;
-    if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 1) {
+    if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 2) {
         std::fclose(f);
         return fail(LBM_ERR_IO, "not a checkpoint of this library");
     }

@@ -121,6 +121,42 @@ __global__ void init_kernel(const InstanceDev *__restrict__ table, int inst, int
     }
 }
 
+// A-B layout: the own-cell part S of every wall rule (wall_own_part), from the stored
+// post-collision state of buffer cur, into slot k of the solid cell x - e_k, which the
+// next step's pull of direction k reads (the steps themselves leave S there for the step
+// after them).  For a state set from outside: the initial state, imported populations.
+// One thread per boundary cell; every solid slot belongs to one link only.
+template <int STORE>
+__global__ void wall_prepare_kernel(const InstanceDev *__restrict__ table, int inst, long long nb,
+                                    const long long *__restrict__ bcell, int cur)
+{
+    using S = Store<STORE>;
+    using T = typename S::T;
+    using R = typename S::R;
+    const InstanceDev &I = table[inst];
+    T *f = reinterpret_cast<T *>(cur ? I.f1 : I.f0);
+    const R *linkc = reinterpret_cast<const R *>(I.linkc);
+    const long long ks = I.ks, nx = I.nx, ny = I.ny, nz = I.nz;
+    constexpr bool sr = sizeof(T) == 2;
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
+         b += (long long)gridDim.x * blockDim.x) {
+        const long long cell = bcell[b];
+        const uint32_t wm = I.bmask[b], off = I.boff[b];
+        const long long x = cell % nx, yz = cell / nx, y = yz % ny, z = yz / ny;
+        const uint32_t h = sr ? cell_hash((uint32_t)cell) : 0u;
+#pragma unroll
+        for (int k = 1; k < Q; ++k) {
+            if (!((wm >> k) & 1u)) continue;
+            const R C = S::load(f + (long long)opp(k) * ks + cell, I.inv_scale);
+            const R B = S::load(f + (long long)k * ks + cell, I.inv_scale);
+            const R cq = I.wall == 1 ? linkc[off + __popc(wm & ((1u << k) - 1u))] : R(0);
+            const R sv = wall_own_part(I.wall, cq, C, B);
+            const long long src = (x - ex(k) + nx) % nx + nx * ((y - ey(k) + ny) % ny + ny * ((z - ez(k) + nz) % nz));
+            f[(long long)k * ks + src] = sr ? S::pack_sr(sv, I.scale, round_bits(h, k, float(sv))) : S::pack(sv, I.scale);
+        }
+    }
+}
+
 // Import direction k from FP64 f (cells of one direction): g = f - w rho0.
 template <int STORE>
 __global__ void import_kernel(const InstanceDev *__restrict__ table, int inst, int layout, int cur, int k,

@@ -99,6 +99,18 @@ __host__ __device__ constexpr int mrt_norm2(int i)
 // ------------------------------------------------------------------------------------
 enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
 
+__device__ __forceinline__ float fma_r(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_r(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// The own-cell part of the wall rule of link (x, kbar), x - e_k solid, from the cell's own
+// post-collision values C = g~_kbar(x) and B = g~_k(x): SBB S = C (Eq. noslip); CLI
+// S = C - c B, so that the new g_k = S + c g_kbar^in (Eq. CLI; c = 0 where CLI falls back
+// to SBB).
+template <typename R> __device__ __forceinline__ R wall_own_part(int wall, R cq, R C, R B)
+{
+    return (wall == 1 && cq != R(0)) ? fma_r(-cq, B, C) : C;
+}
+
 template <int S> struct Store;
 template <> struct Store<ST_F64> {
     using T = double;

@@ -129,6 +129,15 @@ cudaError_t moments(const Launch &L, int layout, int cur, int aa_phase, int mode
 }
 
 template <int STORE>
+cudaError_t wall_prepare(const InstanceDev *table, int inst, long long nb, const long long *bcell, int cur,
+                         cudaStream_t s)
+{
+    if (nb <= 0) return cudaSuccess;
+    wall_prepare_kernel<STORE><<<flat_grid(nb, 128), 128, 0, s>>>(table, inst, nb, bcell, cur);
+    return cudaGetLastError();
+}
+
+template <int STORE>
 FormatOps make_ops()
 {
     FormatOps o;
@@ -137,6 +146,7 @@ FormatOps make_ops()
     o.import_dir = &import_dir<STORE>;
     o.export_dir = &export_dir<STORE>;
     o.moments = &moments<STORE>;
+    o.wall_prepare = &wall_prepare<STORE>;
     o.step_kernel_ptr = &step_ptr<STORE>;
     return o;
 }

@@ -36,6 +36,9 @@ struct FormatOps {
                               int aa_phase, int k, double *fk, cudaStream_t s);
     cudaError_t (*moments)(const Launch &L, int layout, int cur, int aa_phase, int mode, int comp,
                            double *out);
+    // A-B layout: wall terms of the stored state into the solid slots (wall_prepare_kernel)
+    cudaError_t (*wall_prepare)(const InstanceDev *table, int inst, long long n_boundary, const long long *bcell,
+                                int cur, cudaStream_t s);
     const void *(*step_kernel_ptr)(int coll, int kind);  // for occupancy queries
 };
 
@@ -82,7 +85,7 @@ cudaError_t launch_final_reduce(const InstanceDev *table, const int *tile_begin,
 void set_error(const std::string &msg);
 
 constexpr int kMaxWarpsPerBlock = 32;
-constexpr int kMinChunkSegs = 4;       // smallest tile (segments): sizes the partial sums
+constexpr int kMinChunkSegs = kTileSegs;  // smallest tile (work items): sizes the partial sums
 constexpr long long kDirPad = 0;       // extra elements between direction arrays
 long long direction_stride(long long ncells);
 

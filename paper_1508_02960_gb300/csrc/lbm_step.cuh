@@ -4,8 +4,7 @@
 // Work decomposition.  An instance's fluid cells, in cell order, are dealt out 32 per
 // warp (solid cells cost nothing and every lane has a cell, up to the last warp); runs of
 // consecutive fluid cells keep the loads of a warp coalesced.  One block per tile of
-// kStepWarps such warps; each warp (one lane per cell) takes kSegsPerWarp of them and
-// issues all their pulls before finishing the first, for load/compute overlap.
+// kStepWarps such work items, one per warp (one lane per cell).
 //
 // Per fluid cell x and direction k (all arithmetic on deviations g = f - w rho0):
 //   pull      g_k <- g~_k(x - e_k), plus +w_k delta_rho when the pull crosses the x
@@ -17,9 +16,9 @@
 //   moments   drho = sum g_k, u = rho0^-1 sum e_k g_k (Eq. Macro);
 //   collide   SRT, TRT or MRT relaxation towards Eq. equilibrium;
 //   store     A-B: to the other buffer; AA: in place (see below).
-// The 19 pulls are issued unconditionally (a solid source slot holds 0 and is then
-// replaced by the wall rule), so no load waits on the boundary table; the wall code runs
-// only in warps whose segment holds a boundary cell.
+// The 19 pulls are issued unconditionally: a solid source slot holds the own-cell part
+// of the wall rule (A-B layout, see finish_cell) or is replaced by the wall rule (AA), so
+// no pull waits on the boundary table; the wall code runs only for boundary cells.
 //
 // AA layout (in-place, one buffer).  PULL steps read g~_k(x - e_k) from slot kbar of
 // x - e_k and push g~_k(x) into slot k of x + e_k; LOCAL steps read slot k and write
@@ -100,8 +99,12 @@ template <typename R> __device__ __forceinline__ Coord coord_of(const Par<R> &p,
     return c;
 }
 
-// Blocks per multiprocessor the register allocation is sized for.
-template <int STORE, int KIND> constexpr int step_min_blocks() { return STORE == ST_F64 ? 2 : 8; }
+// Blocks per multiprocessor the register allocation is sized for: 32 warps (64 registers a
+// thread) for the 32- and 16-bit formats, 8 warps for FP64.
+template <int STORE, int KIND> constexpr int step_min_blocks()
+{
+    return (STORE == ST_F64 ? 8 : 32) / kStepWarps;
+}
 
 // Moments of the incoming populations (Eq. Macro), in deviation form.
 template <typename R>
@@ -185,41 +188,49 @@ __device__ __forceinline__ void collide(R (&g)[Q], const Par<R> &p, const R *rat
     }
 }
 
-// Process one cell whose 19 pulled populations are in g[] (already shifted): walls,
-// moments, collision, stores.  When reduce is set, returns the moments through rd..rz and
-// the momentum the cell's wall links hand to the solid in this step through fm[3]: a link
-// (x, kbar) with x - e_k solid carries g~_kbar(x) into the wall and brings the new g_k
-// back, so the solid gains e_kbar (g~_kbar(x) + g_k).  (Deviations suffice: the 2 w rho0
-// of full populations sums to zero over a periodic domain.)
+// Process one cell whose 19 pulled populations are in g[] (already shifted, except the
+// wall directions): walls, moments, collision, stores.  When RED is set, returns the
+// moments through rd..rz and the momentum the cell's wall links hand to the solid in this
+// step through fm[3]: a link (x, kbar) with x - e_k solid carries g~_kbar(x) into the wall
+// and brings the new g_k back, so the solid gains e_kbar (g~_kbar(x) + g_k).  (Deviations
+// suffice: the 2 w rho0 of full populations sums to zero over a periodic domain.)
+//
+// Walls in the A-B layout.  The pull of a wall direction k reads slot k of the solid cell
+// x - e_k, which no fluid cell owns; every step leaves there the own-cell part S of the
+// wall rule for the next step (wall_own_part, from its post-collision values in
+// registers), so SBB needs no wall code at all and CLI adds c g_kbar^in, g_kbar^in being
+// the cell's ordinary pull from x_f2 = x + e_k.  A state set from outside (initial state,
+// imported populations) gets these slots from wall_prepare_kernel.
+// Walls in the AA layout: C is in the own slot k, B (CLI) in the link buffer linkB, and
+// the same arithmetic runs at the start of the step.
 template <int COLL, int STORE, int KIND, bool RED, typename R>
 __device__ __forceinline__ void finish_cell(R (&g)[Q], const Par<R> &P, const R *rates, uint32_t cell, uint32_t x,
-                                            const uint32_t *push_off, uint32_t wm, uint32_t off,
-                                            const typename Store<STORE>::T *fs, typename Store<STORE>::T *fd,
-                                            const R *linkc, typename Store<STORE>::T *linkB, unsigned *status,
-                                            R &rd, R &rx, R &ry, R &rz, R (&fm)[3])
+                                            bool inner, const uint32_t *pull_off, const uint32_t *push_off,
+                                            uint32_t wm, uint32_t off, const typename Store<STORE>::T *fs,
+                                            typename Store<STORE>::T *fd, const R *linkc,
+                                            typename Store<STORE>::T *linkB, unsigned *status, R &rd, R &rx, R &ry,
+                                            R &rz, R (&fm)[3])
 {
     using S = Store<STORE>;
     using T = typename S::T;
     const uint32_t KS = P.ks;
-    if (wm) {  // walls: the solid sources read for these directions held 0
+    if (wm) {
 #pragma unroll
         for (int k = 1; k < Q; ++k) {
             if (!((wm >> k) & 1u)) continue;
             const int kb = opp(k);
-            // own post-collision g~_kbar(x)
-            R C;
-            if constexpr (KIND == KIND_AB) C = S::load(fs + ((uint32_t)kb * KS + cell), P.isc);
-            else C = S::load(fs + ((uint32_t)k * KS + cell), P.isc);
-            R v = C;
-            if (P.wall == 1) {
-                const uint32_t l = off + __popc(wm & ((1u << k) - 1u));
-                const R cq = linkc[l];
-                if (cq != R(0)) {
-                    R B;  // own post-collision g~_k(x)
-                    if constexpr (KIND == KIND_AB) B = S::load(fs + ((uint32_t)k * KS + cell), P.isc);
-                    else B = S::load(linkB + l, P.isc);
-                    v = cq * (g[kb] - B) + C;
-                }
+            const uint32_t l = off + __popc(wm & ((1u << k) - 1u));
+            const R cq = P.wall == 1 ? linkc[l] : R(0);
+            R v, C;
+            if constexpr (KIND == KIND_AB) {
+                v = g[k];  // S, left by the previous step in the solid slot
+                if (cq != R(0)) v = fma_r(cq, g[kb], v);
+                if constexpr (RED) C = S::load(fs + ((uint32_t)kb * KS + cell), P.isc);
+            } else {
+                C = S::load(fs + ((uint32_t)k * KS + cell), P.isc);  // own g~_kbar(x)
+                const R B = cq != R(0) ? S::load(linkB + l, P.isc) : R(0);
+                v = wall_own_part(P.wall, cq, C, B);
+                if (cq != R(0)) v = fma_r(cq, g[kb], v);
             }
             g[k] = v;
             if constexpr (RED) {  // e_kbar = -e_k
@@ -278,6 +289,28 @@ __device__ __forceinline__ void finish_cell(R (&g)[Q], const Par<R> &P, const R 
             else fd[(uint32_t)opp(k) * KS + cell] = packed[k];
         }
     }
+    if constexpr (KIND == KIND_AB) {
+        if (wm) {  // the own-cell part of every wall rule, into the solid slot the next pull reads
+            const uint32_t cxm = x == 0 ? P.nx : 0u, cxp = x == P.nx - 1 ? P.nx : 0u;
+            Coord co;
+            if (!inner) co = coord_of(P, cell);
+#pragma unroll
+            for (int k = 1; k < Q; ++k) {
+                if (!((wm >> k) & 1u)) continue;
+                const R cq = P.wall == 1 ? linkc[off + __popc(wm & ((1u << k) - 1u))] : R(0);
+                const R sv = wall_own_part(P.wall, cq, g[opp(k)], g[k]);
+                uint32_t idx;
+                if (inner) {
+                    idx = cell + pull_off[k];
+                    if (ex(k) == 1) idx += cxm;
+                    if (ex(k) == -1) idx -= cxp;
+                } else {
+                    idx = (uint32_t)k * KS + co.pull(k);
+                }
+                fd[idx] = sr ? S::pack_sr(sv, P.sc, round_bits(h, k, float(sv))) : S::pack(sv, P.sc);
+            }
+        }
+    }
     if constexpr (KIND != KIND_AB) {
         if (wm && P.wall == 1) {
 #pragma unroll
@@ -293,13 +326,14 @@ __device__ __forceinline__ void finish_cell(R (&g)[Q], const Par<R> &P, const R 
 // values (see pull_item) and what the finish needs.
 struct WarpItem {
     uint32_t cell, x;  // this lane's cell (0xFFFFFFFF: padding lane) and its x
+    uint32_t wm, off;  // boundary cell: wall mask (bit k: x - e_k solid) and first link; else 0
     uint2 wd;          // boundary bits of the 32 lanes, first boundary-table index
     bool inner;        // every lane away from the y and z faces
 };
 
-// Locate one work item: this lane's cell and coordinates, the warp's boundary bits, and
-// whether every lane is away from the y and z faces.  Reads only the work list, which no
-// step writes.
+// Locate one work item: this lane's cell and coordinates, its wall mask and links, and
+// whether every lane is away from the y and z faces.  Reads only the work list and the
+// boundary table, which no step writes.
 template <typename R>
 __device__ __forceinline__ void locate_item(const InstanceDev &I, const Par<R> &P, uint32_t w, int lane, WarpItem &it)
 {
@@ -312,6 +346,13 @@ __device__ __forceinline__ void locate_item(const InstanceDev &I, const Par<R> &
     const uint32_t y = yz - z * P.ny;
     const bool in_yz = !live || (y - 1u < P.ny - 2u && z - 1u < P.nz - 2u);
     it.inner = __all_sync(0xffffffffu, in_yz);
+    it.wm = 0u;
+    it.off = 0u;
+    if ((it.wd.x >> lane) & 1u) {
+        const uint32_t b = it.wd.y + __popc(it.wd.x & ((1u << lane) - 1u));
+        it.wm = I.bmask[b];
+        it.off = I.boff[b];
+    }
 }
 
 // Issue the 19 pulls of a located work item into raw[] (storage type, converted in
@@ -365,27 +406,25 @@ __device__ __forceinline__ void finish_item(const InstanceDev &I, const Par<R> &
     R g[Q];
 #pragma unroll
     for (int k = 0; k < Q; ++k) g[k] = S::cvt(raw[k], P.isc);
+    // pressure shift of the pulls that crossed the x boundary (wall directions take their
+    // value from the wall rule instead)
+    const uint32_t wm = it.wm;
     if (it.x == 0) {
 #pragma unroll
         for (int k = 0; k < Q; ++k)
-            if (ex(k) == 1) g[k] += R(weight(k)) * P.dshift;
+            if (ex(k) == 1 && !((wm >> k) & 1u)) g[k] += R(weight(k)) * P.dshift;
     }
     if (it.x == P.nx - 1) {
 #pragma unroll
         for (int k = 0; k < Q; ++k)
-            if (ex(k) == -1) g[k] -= R(weight(k)) * P.dshift;
-    }
-    uint32_t wm = 0u, off = 0u;
-    if ((it.wd.x >> lane) & 1u) {
-        const uint32_t b = it.wd.y + __popc(it.wd.x & ((1u << lane) - 1u));
-        wm = I.bmask[b];
-        off = I.boff[b];
+            if (ex(k) == -1 && !((wm >> k) & 1u)) g[k] -= R(weight(k)) * P.dshift;
     }
     R rd = R(0), rx = R(0), ry = R(0), rz = R(0);
     R fm[3] = {R(0), R(0), R(0)};
-    finish_cell<COLL, STORE, KIND, RED, R>(g, P, rates, it.cell, it.x, it.inner ? I.push_off : nullptr, wm, off, fs,
-                                           fd, reinterpret_cast<const R *>(I.linkc),
-                                           reinterpret_cast<T *>(I.linkB), status, rd, rx, ry, rz, fm);
+    finish_cell<COLL, STORE, KIND, RED, R>(g, P, rates, it.cell, it.x, it.inner, I.pull_off,
+                                           it.inner ? I.push_off : nullptr, wm, it.off, fs, fd,
+                                           reinterpret_cast<const R *>(I.linkc), reinterpret_cast<T *>(I.linkB),
+                                           status, rd, rx, ry, rz, fm);
     if constexpr (RED) {
         acc.v[RED_DRHO] += (double)rd;
         acc.v[RED_U + 0] += (double)rx;

@@ -227,7 +227,19 @@ def test_half_storage_one_step(capi, orc, geom, fmt, coll, wall):
     # FP32 collision error: a few dozen roundings of operands up to max|g| (floor for
     # results so small that their storage ulp is below it)
     floor = 64 * 2.0 ** -24 * np.abs(g_ref).max()
-    assert np.all(err <= ulp(g_ref) * 1.0001 + floor)
+    bound = ulp(g_ref) * 1.0001 + floor
+    if wall == "CLI":
+        # A-B layout: the own-cell part C - c B of a cut link's rule waits one step in the
+        # solid slot, stored in the format (one more rounding of a value up to 2 max|g| of
+        # the cell), and the collision spreads that error over the cell's outputs
+        e, _, _ = orc.lattice()
+        wallcell = np.zeros(solid.shape, bool)
+        for k in range(1, 19):
+            wallcell |= np.roll(solid, shift=(e[k, 2], e[k, 1], e[k, 0]), axis=(0, 1, 2)) == 1
+        wallcell &= solid == 0
+        amax = np.abs(dev).max(axis=0)
+        bound = bound + np.where(wallcell, 4 * ulp(2 * amax), 0.0)[m][None, :]
+    assert np.all(err <= bound)
 
 
 # ---------------------------------------------------------------------------------------

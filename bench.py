@@ -307,6 +307,78 @@ def study_sweep(args):
                       "kernel_launches": stats["kernel_launches"], "alone_vs_mix": checks}), flush=True)
 
 
+def study_drag(args):
+    """Drag studies of Sec. 3 on the simple cubic array: one sphere of radius r = 0.3 L in an
+    L^3 periodic cell (reading O12), Stokes flow (delta_rho = 1e-6), FP64 storage, run to a
+    steady state (|dU|/U < 1e-10 between checks 500 steps apart).
+    E1 grid convergence (Fig. 3): C_D (momentum-exchange drag, Eq. AnalyticForce) for
+       L = 10, 15, .., 60 (r = 3 .. 18), every collision operator x {SBB, CLI}, tau = 0.8,
+       Lambda = 3/16; error against the Richardson extrapolation (second order) of TRT-CLI on
+       the two finest lattices -- C_D,ref of the series the paper cites is not printed there.
+    E3 viscosity dependence (Fig. 5): K at r = 16.5 (L = 55) for nu = 0.029 .. 0.45,
+       relative to the same scheme's K at nu = 1/6."""
+    import numpy as np
+    import torch
+
+    from paper_1508_02960_gb300 import capi
+    from paper_1508_02960_gb300 import inputs as I
+
+    def steady(L, r, coll, wall, tau):
+        g = I.centred_sphere(L, r)
+        with capi.Context(spheres=g.spheres, shape=g.shape, tau=tau, delta_rho=1e-6, magic_lambda=3 / 16,
+                          collision=getattr(capi, coll), wall=getattr(capi, wall), storage=capi.F64,
+                          stream=torch.cuda.current_stream()) as ctx:
+            ctx.init_equilibrium()
+            st, steps = ctx.run_to_convergence(1e-10, 500, max(args.study_max_steps, 200000))
+            o = ctx.observables()
+        return o, capi.STATUS.get(st, st), steps
+
+    schemes = [(c, w) for c in ("SRT", "TRT", "MRT") for w in ("SBB", "CLI")]
+    t0 = time.perf_counter()
+    e1 = {}
+    Ls = list(range(10, 61, 5))
+    for coll, wall in schemes:
+        for L in Ls:
+            o, st, steps = steady(L, 0.3 * L, coll, wall, 0.8)
+            e1[(coll, wall, L)] = dict(C_D=o["C_D"], K=o["K"], F_x=o["F_x"], status=st, steps=steps)
+    c1, c2 = e1[("TRT", "CLI", Ls[-2])]["C_D"], e1[("TRT", "CLI", Ls[-1])]["C_D"]
+    ratio = (Ls[-1] / Ls[-2]) ** 2
+    cd_ext = c2 + (c2 - c1) / (ratio - 1.0)
+    rows = []
+    for (coll, wall, L), v in e1.items():
+        rows.append(dict(scheme=f"{coll}-{wall}", L=L, r=0.3 * L, C_D=v["C_D"], err=abs(v["C_D"] / cd_ext - 1.0),
+                         status=v["status"], steps=v["steps"]))
+    indep = {}
+    for coll, wall in schemes:
+        errs = [(L, abs(e1[(coll, wall, L)]["C_D"] / cd_ext - 1.0)) for L in Ls]
+        ok = None
+        for i, (L, _) in enumerate(errs):
+            if all(e < 0.01 for _, e in errs[i:]):
+                ok = 0.3 * L
+                break
+        indep[f"{coll}-{wall}"] = ok
+    print(json.dumps({"study": "drag_grid_convergence", "C_D_extrapolated": cd_ext, "tau": 0.8,
+                      "grid_independent_r": indep, "rows": rows}), flush=True)
+
+    nus = [0.029, 0.05, 0.1, 1 / 6, 0.25, 0.35, 0.45]
+    e3 = []
+    for coll, wall in schemes:
+        Ks = {}
+        for nu in nus:
+            o, st, steps = steady(55, 16.5, coll, wall, 0.5 + 3.0 * nu)
+            Ks[nu] = (o["K"], st, steps)
+        k0 = Ks[1 / 6][0]
+        for nu in nus:
+            e3.append(dict(scheme=f"{coll}-{wall}", nu=nu, K=Ks[nu][0], K_rel=Ks[nu][0] / k0, status=Ks[nu][1],
+                           steps=Ks[nu][2]))
+    spread = {}
+    for coll, wall in schemes:
+        rel = [r["K_rel"] for r in e3 if r["scheme"] == f"{coll}-{wall}"]
+        spread[f"{coll}-{wall}"] = max(rel) - min(rel)
+    print(json.dumps({"study": "drag_viscosity", "r": 16.5, "L": 55, "K_rel_spread": spread, "rows": e3,
+                      "wall_s": time.perf_counter() - t0}), flush=True)
+
+
 def dist_setup(n_gpus: int):
     import torch
     rank, world, local = 0, 1, 0
@@ -532,7 +604,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only build the workload and run this many steps (for ncu), no timing")
-    ap.add_argument("--study", choices=["precision", "sweep"], default=None,
+    ap.add_argument("--study", choices=["precision", "sweep", "drag"], default=None,
                     help="run a study instead of the benchmark (JSON lines)")
     ap.add_argument("--study-size", type=int, default=64)
     ap.add_argument("--study-max-steps", type=int, default=60000)
@@ -547,6 +619,9 @@ def main():
         return
     if args.study == "sweep":
         study_sweep(args)
+        return
+    if args.study == "drag":
+        study_drag(args)
         return
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", 0))

@@ -27,7 +27,7 @@ _lib = None
 
 Q = 19
 SRT, TRT, MRT = 0, 1, 2
-SBB, CLI = 0, 1
+SBB, CLI, LIBB, QIBB, IEBB, MR = 0, 1, 2, 3, 4, 5
 
 
 def build(force: bool = False) -> str:

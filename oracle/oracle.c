@@ -11,7 +11,7 @@
  *
  * Every routine follows the paper's notation (k, k-bar, x_f1, x_f2, q, f-tilde) and
  * takes the steps in the order the paper states them.  Where the paper is silent or
- * ambiguous, the reading taken is stated in the comment (readings O1..O14).
+ * ambiguous, the reading taken is stated in the comment (readings O1..O17).
  *
  * Compiled as C99 with -O2 -ffp-contract=off (no fused multiply-add), optionally
  * with OpenMP over z.  All arithmetic is IEEE double.
@@ -173,7 +173,7 @@ void orc_mrt_matrix(double *m_out)
 typedef struct {
     int nx, ny, nz;
     int collision;       /* 0 = SRT, 1 = TRT, 2 = MRT */
-    int wall;            /* 0 = SBB, 1 = CLI */
+    int wall;            /* 0 = SBB, 1 = CLI, 2 = LIBB, 3 = QIBB, 4 = IEBB, 5 = MR */
     double tau;          /* omega = omega+ = s_nu = 1/tau, nu = (tau - 1/2)/3 */
     double delta_rho;    /* periodic pressure drop, Eqs. generalPeriodicRho..PeriodicfunkownRight */
     double rho0;         /* mean density (the paper sets rho0 = 1) */
@@ -375,6 +375,111 @@ static double read_pop(const double *f, int64_t n, int k, int xv, int yv, int zv
 }
 
 /* ------------------------------------------------------------------------------
+ * Interpolated bounce-back rules (Sec. 2.2.1, Eqs. LIBB, QIBB, fstar, IEBB, MR, CLI), in
+ * the paper's notation: k points from x_f1 into the wall (x_f1 + e_k solid), the unknown
+ * is f_kbar(x_f1, t+1), x_f2 = x_f1 - e_k, x_f3 = x_f1 - 2 e_k, q the link's wall
+ * distance, all f~ at time t.  wall_rule returns the unknown.  Reading O16: a rule falls
+ * back when a node it reads is solid -- to SBB when x_f2 is needed and solid, QIBB to
+ * LIBB and MR to CLI when only x_f3 is solid.  Reading O15: the density in f* (printed
+ * as Delta rho) is the density of x_f1, so that f* is the equilibrium of Eq. equilibrium
+ * at x_f1 with the first-order velocity term taken at u_bf (Mei et al.).
+ * ---------------------------------------------------------------------------- */
+typedef struct {
+    int wall;
+    double q, tau, rho0;
+    int f2_fluid, f3_fluid;
+    double fk_1, fkb_1;   /* f~_k(x_f1), f~_kbar(x_f1) */
+    double fk_2, fkb_2;   /* f~_k(x_f2), f~_kbar(x_f2) */
+    double fk_3;          /* f~_k(x_f3) */
+    double rho_1, u_1[3]; /* density and velocity of x_f1 at t */
+    double u_2[3];        /* velocity of x_f2 at t */
+    int k;                /* link direction (into the wall) */
+} wall_link;
+
+static double rule_sbb(const wall_link *L) { return L->fk_1; }
+
+static double rule_cli(const wall_link *L)
+{
+    double c = (1.0 - 2.0 * L->q) / (1.0 + 2.0 * L->q);
+    return c * L->fk_2 - c * L->fkb_1 + L->fk_1;
+}
+
+static double rule_libb(const wall_link *L)
+{
+    double q = L->q;
+    if (q < 0.5) return (1.0 - 2.0 * q) * L->fk_2 + 2.0 * q * L->fk_1;
+    return (1.0 - 1.0 / (2.0 * q)) * L->fkb_1 + 1.0 / (2.0 * q) * L->fk_1;
+}
+
+static double rule_qibb(const wall_link *L)
+{
+    double q = L->q;
+    if (q < 0.5)
+        return q * (1.0 + 2.0 * q) * L->fk_1 + (1.0 - 4.0 * q * q) * L->fk_2 - q * (1.0 - 2.0 * q) * L->fk_3;
+    return (2.0 * q - 1.0) / q * L->fkb_1 + 1.0 / (q * (2.0 * q + 1.0)) * L->fk_1 +
+           (1.0 - 2.0 * q) / (2.0 * q + 1.0) * L->fkb_2;
+}
+
+/* Reading O17: the first MR coefficient is printed over (1+2q)^2; read over (1+q)^2, as
+ * the second one.  As printed, the rule is inconsistent: it converges at first order in
+ * the plane channel, worse than SBB; read so, at second order like the other rules. */
+static double rule_mr(const wall_link *L)
+{
+    double q = L->q;
+    double a = (1.0 - 2.0 * q - 2.0 * q * q) / ((1.0 + q) * (1.0 + q));
+    double b = q * q / ((1.0 + q) * (1.0 + q));
+    return a * L->fk_2 + b * L->fk_3 - a * L->fkb_1 - b * L->fkb_2 + L->fk_1;
+}
+
+static double rule_iebb(const wall_link *L)
+{
+    double q = L->q, inv_omega = L->tau; /* 1/omega = tau for omega+ (TRT) and s_nu (MRT) */
+    double ubf[3], X;
+    if (q < 0.5) {
+        for (int a = 0; a < 3; ++a) ubf[a] = L->u_2[a];
+        X = (2.0 * q - 1.0) / (inv_omega - 2.0);
+    } else {
+        for (int a = 0; a < 3; ++a) ubf[a] = (1.0 - 3.0 / (2.0 * q)) * L->u_1[a];
+        X = (2.0 * q - 1.0) / (inv_omega + 0.5);
+    }
+    const int *e = E[L->k];
+    double eub = e[0] * ubf[0] + e[1] * ubf[1] + e[2] * ubf[2];
+    double eu1 = e[0] * L->u_1[0] + e[1] * L->u_1[1] + e[2] * L->u_1[2];
+    double uu1 = L->u_1[0] * L->u_1[0] + L->u_1[1] * L->u_1[1] + L->u_1[2] * L->u_1[2];
+    double fstar = W[L->k] * (L->rho_1 + L->rho0 * (3.0 * eub + 4.5 * eu1 * eu1 - 1.5 * uu1));
+    return (1.0 - X) * L->fk_1 + X * fstar;
+}
+
+static double wall_rule(const wall_link *L)
+{
+    switch (L->wall) {
+    case 1: return L->f2_fluid ? rule_cli(L) : rule_sbb(L);
+    case 2: return (L->q < 0.5 && !L->f2_fluid) ? rule_sbb(L) : rule_libb(L);
+    case 3:
+        if (!L->f2_fluid) return L->q < 0.5 ? rule_sbb(L) : rule_libb(L);
+        if (L->q < 0.5 && !L->f3_fluid) return rule_libb(L);
+        return rule_qibb(L);
+    case 4: return (L->q < 0.5 && !L->f2_fluid) ? rule_sbb(L) : rule_iebb(L);
+    case 5:
+        if (!L->f2_fluid) return rule_sbb(L);
+        if (!L->f3_fluid) return rule_cli(L);
+        return rule_mr(L);
+    default: return rule_sbb(L);
+    }
+}
+
+/* Density and velocity of the populations of the node at virtual position (xv, yv, zv)
+ * (periodic image, with the pressure shift of read_pop).  For post-collision values these
+ * are the node's moments at t: the collision conserves mass and momentum. */
+static void node_moments(const double *f, int64_t n, int xv, int yv, int zv, const orc_params *p, double *rho,
+                         double *u)
+{
+    double fl[Q];
+    for (int m = 0; m < Q; ++m) fl[m] = read_pop(f, n, m, xv, yv, zv, p);
+    moments(fl, p->rho0, rho, u);
+}
+
+/* ------------------------------------------------------------------------------
  * One time step, stream first then collide (Sec. 2, Eqs. collision, streaming and
  * the remark that waLBerla streams first, then collides).  Input f holds the
  * post-collision values f-tilde(t) of every fluid node; output ft holds
@@ -387,7 +492,8 @@ static double read_pop(const double *f, int64_t n, int k, int xv, int yv, int zv
  *   CLI, Eq. (CLI) with c = (1-2q)/(1+2q), q the wall distance of link (x, kbar),
  *        x_f2 = x - e_kbar = x + e_k:
  *        f_k(x,t+1) = c f~_kbar(x_f2,t) - c f~_k(x,t) + f~_kbar(x,t)
- * Reading O4: where x_f2 is solid (one-cell gap), CLI falls back to SBB.
+ * Reading O4: where x_f2 is solid (one-cell gap), CLI falls back to SBB.  LIBB, QIBB,
+ * IEBB and MR: wall_rule above.
  *
  * sums (optional, 4 doubles): sum over fluid nodes of rho, u_x, u_y, u_z of the
  * streamed moments (Eq. Macro) -- reading O9.  uvec (optional, 3*N): per-node u.
@@ -423,18 +529,39 @@ static void step_once(const orc_params *p, const uint8_t *solid, const double *q
                         fin[k] = read_pop(f, n, k, xv, yv, zv, p);
                         continue;
                     }
+                    /* the link of the paper's rules points into the wall: kk = kbar, and
+                     * the unknown is f_k = f_{kk-bar} */
                     int kb = OPP[k];
                     double own_kb = f[(int64_t)kb * n + c]; /* f~_kbar(x_f1, t) */
                     int x2 = x + E[k][0], y2 = y + E[k][1], z2 = z + E[k][2];
+                    int x3 = x + 2 * E[k][0], y3 = y + 2 * E[k][1], z3 = z + 2 * E[k][2];
                     int64_t s2 = cell_index(wrap(x2, nx), wrap(y2, ny), wrap(z2, nz), nx, ny);
-                    if (p->wall == 1 && !solid[s2]) {
-                        double qq = q[(int64_t)kb * n + c];
-                        double cq = (1.0 - 2.0 * qq) / (1.0 + 2.0 * qq);
-                        double f2 = read_pop(f, n, kb, x2, y2, z2, p); /* f~_kbar(x_f2, t) */
-                        double own_k = f[(int64_t)k * n + c];            /* f~_k(x_f1, t) */
-                        fin[k] = cq * f2 - cq * own_k + own_kb;
-                    } else {
+                    int64_t s3 = cell_index(wrap(x3, nx), wrap(y3, ny), wrap(z3, nz), nx, ny);
+                    if (p->wall == 0) {
                         fin[k] = own_kb;
+                    } else {
+                        wall_link L;
+                        memset(&L, 0, sizeof(L));
+                        L.wall = p->wall;
+                        L.q = q[(int64_t)kb * n + c];
+                        L.tau = p->tau;
+                        L.rho0 = p->rho0;
+                        L.k = kb;
+                        L.f2_fluid = !solid[s2];
+                        L.f3_fluid = L.f2_fluid && !solid[s3];
+                        L.fk_1 = own_kb;
+                        L.fkb_1 = f[(int64_t)k * n + c];
+                        if (L.f2_fluid) {
+                            L.fk_2 = read_pop(f, n, kb, x2, y2, z2, p);
+                            L.fkb_2 = read_pop(f, n, k, x2, y2, z2, p);
+                            if (p->wall == 4) {
+                                double r2;
+                                node_moments(f, n, x2, y2, z2, p, &r2, L.u_2);
+                            }
+                        }
+                        if (L.f3_fluid) L.fk_3 = read_pop(f, n, kb, x3, y3, z3, p);
+                        if (p->wall == 4) node_moments(f, n, x, y, z, p, &L.rho_1, L.u_1);
+                        fin[k] = wall_rule(&L);
                     }
                     /* momentum given to the solid through link (x, kbar) */
                     double ex_in = own_kb + fin[k];
@@ -478,7 +605,8 @@ int orc_run(const orc_params *p, const uint8_t *solid, const double *q, double *
     mrt_init();
     if (!p || p->nx <= 0 || p->ny <= 0 || p->nz <= 0 || nsteps < 0) return -1;
     if (!(p->tau > 0.5)) return -1;
-    if (p->wall == 1 && !q) return -1;
+    if (p->wall < 0 || p->wall > 5) return -1;
+    if (p->wall >= 1 && !q) return -1;
     const int64_t n = (int64_t)p->nx * p->ny * p->nz;
     double *g = (double *)malloc(sizeof(double) * Q * n);
     if (!g) return -2;

@@ -69,7 +69,7 @@ def _geometry(orc, name):
 
 
 @pytest.mark.parametrize("geom", sorted(GEOMS))
-@pytest.mark.parametrize("coll,wall", [(0, 0), (1, 0), (1, 1), (2, 1)])
+@pytest.mark.parametrize("coll,wall", [(0, 0), (1, 0), (1, 1), (2, 1), (1, 2), (1, 3), (2, 4), (1, 5)])
 def test_momentum_balance_every_step(orc, geom, coll, wall):
     solid, q = _geometry(orc, geom)
     dr = 3e-4

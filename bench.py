@@ -312,7 +312,7 @@ def study_drag(args):
     L^3 periodic cell (reading O12), Stokes flow (delta_rho = 1e-6), FP64 storage, run to a
     steady state (|dU|/U < 1e-10 between checks 500 steps apart).
     E1 grid convergence (Fig. 3): C_D (momentum-exchange drag, Eq. AnalyticForce) for
-       L = 10, 15, .., 60 (r = 3 .. 18), every collision operator x {SBB, CLI}, tau = 0.8,
+       L = 10, 15, .., 60 (r = 3 .. 18), every collision operator x every wall rule, tau = 0.8,
        Lambda = 3/16; error against the Richardson extrapolation (second order) of TRT-CLI on
        the two finest lattices -- C_D,ref of the series the paper cites is not printed there.
     E3 viscosity dependence (Fig. 5): K at r = 16.5 (L = 55) for nu = 0.029 .. 0.45,
@@ -333,7 +333,7 @@ def study_drag(args):
             o = ctx.observables()
         return o, capi.STATUS.get(st, st), steps
 
-    schemes = [(c, w) for c in ("SRT", "TRT", "MRT") for w in ("SBB", "CLI")]
+    schemes = [(c, w) for c in ("SRT", "TRT", "MRT") for w in ("SBB", "CLI", "LIBB", "QIBB", "IEBB", "MR")]
     t0 = time.perf_counter()
     e1 = {}
     Ls = list(range(10, 61, 5))

@@ -63,7 +63,13 @@ typedef enum {
 /* Collision operator (Sec. 2.1). */
 enum { LBM_SRT = 0, LBM_TRT = 1, LBM_MRT = 2 };
 /* Solid-wall rule (Sec. 2.2.1): simple bounce-back, central linear interpolation. */
-enum { LBM_SBB = 0, LBM_CLI = 1 };
+/* Wall rules of Sec. 2.2.1: simple bounce-back (Eq. noslip), central linear interpolation
+ * (Eq. CLI), linear and quadratic interpolation bounce-back (Eqs. LIBB, QIBB),
+ * interpolation/extrapolation bounce-back (Eqs. fstar, IEBB) and multi-reflection (Eq. MR).
+ * LIBB, QIBB, IEBB and MR need the A-B layout; IEBB needs tau != 2.  Where a node a rule
+ * reads is solid it falls back: to SBB when x_f2 is solid, QIBB to LIBB and MR to CLI when
+ * only x_f3 is. */
+enum { LBM_SBB = 0, LBM_CLI = 1, LBM_LIBB = 2, LBM_QIBB = 3, LBM_IEBB = 4, LBM_MR = 5 };
 /* Population storage.  All formats store the deviation f_k - w_k rho0; FP64 and FP32
  * compute in their own precision, FP16/BF16 compute in FP32.  FP16DEV stores the
  * deviation times 2^dev_scale_log2. */
@@ -94,7 +100,7 @@ typedef struct {
     double mrt_energy_ratio;    /* MRT: (1/s_nu - 1/2)/(1/s_e - 1/2); 0 means 4.6 */
     const double *mrt_rates;    /* MRT: optional 19 explicit rates s_0..s_18 (copied) */
     int32_t collision;          /* LBM_SRT / LBM_TRT / LBM_MRT */
-    int32_t wall;               /* LBM_SBB / LBM_CLI */
+    int32_t wall;               /* LBM_SBB, LBM_CLI, LBM_LIBB, LBM_QIBB, LBM_IEBB, LBM_MR */
     int32_t storage;            /* LBM_F64 / LBM_F32 / LBM_F16DEV / LBM_BF16DEV */
     int32_t layout;             /* LBM_LAYOUT_AB / LBM_LAYOUT_AA */
     int32_t dev_scale_log2;     /* FP16DEV scale exponent; LBM_DEV_SCALE_AUTO = from delta_rho */

@@ -20,7 +20,7 @@ from . import build as _build
 
 Q = 19
 SRT, TRT, MRT = 0, 1, 2
-SBB, CLI = 0, 1
+SBB, CLI, LIBB, QIBB, IEBB, MR = 0, 1, 2, 3, 4, 5
 F64, F32, F16DEV, BF16DEV = 0, 1, 2, 3
 LAYOUT_AB, LAYOUT_AA = 0, 1
 DEV_SCALE_AUTO = -1000

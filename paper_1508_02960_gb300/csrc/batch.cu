@@ -62,7 +62,11 @@ lbm_status validate_desc(const lbm_desc &d)
     if (!std::isfinite(d.delta_rho)) return fail(LBM_ERR_ARG, "delta_rho must be finite");
     if (d.rho0 < 0 || !std::isfinite(d.rho0)) return fail(LBM_ERR_ARG, "rho0 must be >= 0 (0 = 1)");
     if (d.collision < LBM_SRT || d.collision > LBM_MRT) return fail(LBM_ERR_ARG, "unknown collision operator");
-    if (d.wall < LBM_SBB || d.wall > LBM_CLI) return fail(LBM_ERR_ARG, "unknown wall rule");
+    if (d.wall < LBM_SBB || d.wall > LBM_MR) return fail(LBM_ERR_ARG, "unknown wall rule");
+    if (d.wall >= LBM_LIBB && d.layout != LBM_LAYOUT_AB)
+        return fail(LBM_ERR_ARG, "LIBB, QIBB, IEBB and MR walls need the A-B layout");
+    if (d.wall == LBM_IEBB && std::fabs(d.tau - 2.0) < 1e-12)
+        return fail(LBM_ERR_ARG, "IEBB needs tau != 2 (its q < 1/2 weight is (2q-1)/(tau-2))");
     if (d.storage < LBM_F64 || d.storage > LBM_BF16DEV) return fail(LBM_ERR_ARG, "unknown storage format");
     if (d.layout < LBM_LAYOUT_AB || d.layout > LBM_LAYOUT_AA) return fail(LBM_ERR_ARG, "unknown layout");
     if (d.n_spheres < 0) return fail(LBM_ERR_ARG, "n_spheres < 0");
@@ -145,8 +149,8 @@ lbm_status Batch::make_instance(const lbm_desc &d0, cudaStream_t s, std::unique_
     }
     std::string err;
     cudaError_t e = build_geometry(d.nx, d.ny, d.nz, sph.empty() ? nullptr : sph.data(), d0.n_spheres,
-                                   d0.n_spheres > 0 ? nullptr : d0.flags, d0.q, d.storage == LBM_F64, s, &in->geo,
-                                   &err);
+                                   d0.n_spheres > 0 ? nullptr : d0.flags, d0.q, d.storage == LBM_F64, d.wall, d.tau,
+                                   s, &in->geo, &err);
     d.spheres = nullptr;
     d.flags = nullptr;
     d.q = nullptr;
@@ -291,6 +295,7 @@ static void fill_dev(const Instance &in, InstanceDev &D)
     D.bmask = in.geo.bmask;
     D.boff = in.geo.boff;
     D.linkc = in.geo.linkc;
+    D.linkw = in.geo.linkw;
     D.linkB = in.linkB;
     D.partials = in.partials;
     D.ncells = in.geo.ncells;
@@ -439,6 +444,7 @@ struct StepQueue {
     const FormatOps *ops;
     Launch L;
     const InstanceDev *one;  // single instance: its parameters by value; else NULL
+    int wx;                  // some instance uses an interpolated wall rule
     int collision, layout;
     unsigned *status;
     int n_status;
@@ -460,7 +466,7 @@ static cudaError_t queue_steps(const StepQueue &q, cudaStream_t s, long long n, 
             if (e != cudaSuccess) return e;
         }
         const int kind = q.layout == LBM_LAYOUT_AB ? KIND_AB : (aa == 0 ? KIND_AA_PULL : KIND_AA_LOCAL);
-        cudaError_t e = q.ops->step(q.collision, kind, L, flip, red ? 1 : 0, q.status, q.one);
+        cudaError_t e = q.ops->step(q.collision, kind, L, flip, red ? 1 : 0, q.status, q.one, q.wx);
         if (e != cudaSuccess) return e;
         ++launches;
         if (q.layout == LBM_LAYOUT_AB) flip ^= 1;
@@ -482,8 +488,10 @@ lbm_status Batch::step(long long n)
         lbm_status st = rebuild();
         if (st != LBM_OK) return st;
     }
+    int wx = 0;
+    for (auto &p : inst_) wx |= p->desc.wall >= LBM_LIBB;
     StepQueue q{&ops(), Launch{d_table_, d_stiles_, nstiles_, kTileSegs, grid_, kStepWarps * 32, stream_},
-                size() == 1 ? &h_table_[0] : nullptr, collision_, layout_, d_status_,
+                size() == 1 ? &h_table_[0] : nullptr, wx, collision_, layout_, d_status_,
                 size(), d_stile_begin_, d_stile_count_, d_sums_, size()};
     const long long kChunk = 1000;
     long long left = n;

@@ -204,12 +204,93 @@ __global__ void to_u32_kernel(long long n, const unsigned long long *__restrict_
         out[i] = (uint32_t)in[i];
 }
 
+// Coefficients of the rule of one cut link (see kLinkW in lbm_device.cuh): q its wall
+// distance, f2 / f3 whether x_f2 / x_f3 are fluid, kd the link direction (into the wall).
+// The rules are Sec. 2.2.1's, rewritten for the unknown g_k (k = kbar of the paper's link
+// direction); fallbacks where a node a rule reads is solid: SBB when it needs x_f2, QIBB
+// to LIBB and MR to CLI when only x_f3 is solid.  MR's first coefficient is taken over
+// (1+q)^2, like its second: as printed over (1+2q)^2 the rule is not consistent.
+__device__ void rule_coefficients(int wall, double q, bool f2, bool f3, double tau, int kd, double *w)
+{
+    for (int i = 0; i < kLinkW; ++i) w[i] = 0.0;
+    const bool lo = q < 0.5;
+    auto sbb = [&] { w[LW_EPS] = 1.0; };
+    auto cli = [&] {
+        const double c = __ddiv_rn(__dsub_rn(1.0, 2.0 * q), __dadd_rn(1.0, 2.0 * q));
+        w[LW_EPS] = 1.0;
+        w[LW_GAMMA] = -c;
+        w[LW_ALPHA] = c;
+    };
+    auto libb = [&] {
+        if (lo) {
+            w[LW_ALPHA] = 1.0 - 2.0 * q;
+            w[LW_EPS] = 2.0 * q;
+        } else {
+            w[LW_GAMMA] = 1.0 - 1.0 / (2.0 * q);
+            w[LW_EPS] = 1.0 / (2.0 * q);
+        }
+    };
+    switch (wall) {
+    case 2:  // LIBB
+        if (lo && !f2) sbb();
+        else libb();
+        break;
+    case 3:  // QIBB
+        if (!f2) {
+            if (lo) sbb();
+            else libb();
+        } else if (lo && !f3) {
+            libb();
+        } else if (lo) {
+            w[LW_EPS] = q * (1.0 + 2.0 * q);
+            w[LW_ALPHA] = 1.0 - 4.0 * q * q;
+            w[LW_BETA] = -q * (1.0 - 2.0 * q);
+        } else {
+            w[LW_GAMMA] = (2.0 * q - 1.0) / q;
+            w[LW_EPS] = 1.0 / (q * (2.0 * q + 1.0));
+            w[LW_DELTA] = (1.0 - 2.0 * q) / (2.0 * q + 1.0);
+        }
+        break;
+    case 4:  // IEBB: (1 - X) C + X f*, f* = w {rho + rho0 [3 e.u_bf + 9/2 (e.u1)^2 - 3/2 u1.u1]}
+        if (lo && !f2) {
+            sbb();
+        } else if (lo) {  // u_bf = u(x_f2): its e.u term waits for step t+1
+            const double X = (2.0 * q - 1.0) / (tau - 2.0);
+            w[LW_X] = X;
+            w[LW_EPS] = 1.0 - X;
+            w[LW_ZETA] = 3.0 * X * weight(kd);
+        } else {  // u_bf = (1 - 3/(2q)) u(x_f1)
+            const double X = (2.0 * q - 1.0) / (tau + 0.5);
+            w[LW_X] = X;
+            w[LW_EPS] = 1.0 - X;
+            w[LW_THETA] = 3.0 * (1.0 - 3.0 / (2.0 * q));
+        }
+        break;
+    case 5:  // MR
+        if (!f2) {
+            sbb();
+        } else if (!f3) {
+            cli();
+        } else {
+            const double a = (1.0 - 2.0 * q - 2.0 * q * q) / ((1.0 + q) * (1.0 + q));
+            const double b = q * q / ((1.0 + q) * (1.0 + q));
+            w[LW_EPS] = 1.0;
+            w[LW_ALPHA] = a;
+            w[LW_GAMMA] = -a;
+            w[LW_BETA] = b;
+            w[LW_DELTA] = -b;
+        }
+        break;
+    default: sbb(); break;
+    }
+}
+
 template <typename R>
 __global__ void link_kernel(long long nb, int nx, int ny, int nz, const double4 *__restrict__ sph, int ns,
                             const double *__restrict__ qfield, const uint8_t *__restrict__ solid,
                             const uint32_t *__restrict__ bmask, const uint32_t *__restrict__ boff,
                             const long long *__restrict__ bcell, double *__restrict__ linkq, R *__restrict__ linkc,
-                            unsigned long long *__restrict__ ncli)
+                            unsigned long long *__restrict__ ncli, int wall, double tau, R *__restrict__ linkw)
 {
     const long long n = (long long)nx * ny * nz;
     for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
@@ -259,6 +340,14 @@ __global__ void link_kernel(long long nb, int nx, int ny, int nz, const double4 
             const double cq = f2 ? __ddiv_rn(__dsub_rn(1.0, 2.0 * q), __dadd_rn(1.0, 2.0 * q)) : 0.0;
             linkq[l] = q;
             linkc[l] = (R)cq;
+            if (linkw) {  // x_f3 = x + 2 e_k
+                const int x3 = (x + 2 * ex(k) + 2 * nx) % nx, y3 = (y + 2 * ey(k) + 2 * ny) % ny,
+                          z3 = (z + 2 * ez(k) + 2 * nz) % nz;
+                const bool f3 = f2 && !solid[x3 + (long long)nx * (y3 + (long long)ny * z3)];
+                double wv[kLinkW];
+                rule_coefficients(wall, q, f2, f3, tau, kd, wv);
+                for (int i = 0; i < kLinkW; ++i) linkw[(long long)l * kLinkW + i] = (R)wv[i];
+            }
             cli += f2;
             ++l;
         }
@@ -368,6 +457,7 @@ void free_geometry(GeometryDev *g)
     cudaFree(g->bcell);
     cudaFree(g->linkq);
     cudaFree(g->linkc);
+    cudaFree(g->linkw);
     *g = GeometryDev();
 }
 
@@ -381,7 +471,8 @@ void free_geometry(GeometryDev *g)
     } while (0)
 
 cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_spheres, const uint8_t *flags,
-                           const double *q_host, bool c_double, cudaStream_t s, GeometryDev *g, std::string *err)
+                           const double *q_host, bool c_double, int wall, double tau, cudaStream_t s, GeometryDev *g,
+                           std::string *err)
 {
     cudaError_t e = cudaSuccess;
     const long long n = (long long)nx * ny * nz;
@@ -490,6 +581,7 @@ cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_
         if (g->n_links > 0) {
             GEO_CHECK(cudaMalloc(&g->linkq, sizeof(double) * g->n_links));
             GEO_CHECK(cudaMalloc(&g->linkc, (c_double ? 8 : 4) * g->n_links));
+            if (wall >= 2) GEO_CHECK(cudaMalloc(&g->linkw, (c_double ? 8 : 4) * kLinkW * g->n_links));
             if (q_host && !(spheres && n_spheres > 0)) {
                 GEO_CHECK(cudaMalloc(&d_q, sizeof(double) * Q * n));
                 GEO_CHECK(cudaMemcpyAsync(d_q, q_host, sizeof(double) * Q * n, cudaMemcpyHostToDevice, s));
@@ -498,11 +590,13 @@ cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_
             if (c_double)
                 link_kernel<double><<<grid_for(nb, 128), 128, 0, s>>>(nb, nx, ny, nz, sp, n_spheres, d_q, g->solid,
                                                                       g->bmask, g->boff, g->bcell, g->linkq,
-                                                                      (double *)g->linkc, d_ctr + 1);
+                                                                      (double *)g->linkc, d_ctr + 1, wall, tau,
+                                                                      (double *)g->linkw);
             else
                 link_kernel<float><<<grid_for(nb, 128), 128, 0, s>>>(nb, nx, ny, nz, sp, n_spheres, d_q, g->solid,
                                                                      g->bmask, g->boff, g->bcell, g->linkq,
-                                                                     (float *)g->linkc, d_ctr + 1);
+                                                                     (float *)g->linkc, d_ctr + 1, wall, tau,
+                                                                     (float *)g->linkw);
             GEO_CHECK(cudaGetLastError());
         }
     }
@@ -513,7 +607,7 @@ cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_
     g->bytes = n + sizeof(uint4) * (g->nseg_padded + g->n_active_padded) +
                (sizeof(uint32_t) * 32 + sizeof(uint2)) * g->n_fwarps_padded +
                (sizeof(uint32_t) * 2 + sizeof(long long)) * g->n_boundary +
-               (sizeof(double) + (c_double ? 8 : 4)) * g->n_links;
+               (sizeof(double) + (c_double ? 8 : 4) * (wall >= 2 ? 1 + kLinkW : 1)) * g->n_links;
 
     cudaFree(d_sph);
     cudaFree(d_q);

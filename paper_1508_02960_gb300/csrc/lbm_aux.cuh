@@ -144,13 +144,41 @@ __global__ void wall_prepare_kernel(const InstanceDev *__restrict__ table, int i
         const uint32_t wm = I.bmask[b], off = I.boff[b];
         const long long x = cell % nx, yz = cell / nx, y = yz % ny, z = yz / ny;
         const uint32_t h = sr ? cell_hash((uint32_t)cell) : 0u;
+        // the cell's moments at t (for IEBB): the post-collision state conserves them
+        R drho = R(0), u[3] = {R(0), R(0), R(0)};
+        if (I.wall == 4) {
+            for (int m = 0; m < Q; ++m) {
+                const R gm = S::load(f + (long long)m * ks + cell, I.inv_scale);
+                drho += gm;
+                u[0] += R(ex(m)) * gm;
+                u[1] += R(ey(m)) * gm;
+                u[2] += R(ez(m)) * gm;
+            }
+            for (int a = 0; a < 3; ++a) u[a] /= R(I.rho0);
+        }
+        const R *linkw = reinterpret_cast<const R *>(I.linkw);
 #pragma unroll
         for (int k = 1; k < Q; ++k) {
             if (!((wm >> k) & 1u)) continue;
-            const R C = S::load(f + (long long)opp(k) * ks + cell, I.inv_scale);
+            const int kb = opp(k);
+            const R C = S::load(f + (long long)kb * ks + cell, I.inv_scale);
             const R B = S::load(f + (long long)k * ks + cell, I.inv_scale);
-            const R cq = I.wall == 1 ? linkc[off + __popc(wm & ((1u << k) - 1u))] : R(0);
-            const R sv = wall_own_part(I.wall, cq, C, B);
+            const uint32_t l = off + __popc(wm & ((1u << k) - 1u));
+            R sv;
+            if (I.wall >= 2) {  // as wall_own_part_w in the step kernel
+                const R *lw = linkw + (size_t)l * kLinkW;
+                sv = fma_r(lw[LW_GAMMA], B, lw[LW_EPS] * C);
+                const R X = lw[LW_X];
+                if (X != R(0)) {
+                    const R eu = R(ex(kb)) * u[0] + R(ey(kb)) * u[1] + R(ez(kb)) * u[2];
+                    const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+                    const R fst = drho + R(I.rho0) * (lw[LW_THETA] * eu + R(4.5) * eu * eu - R(1.5) * uu);
+                    sv = fma_r(X * R(weight(kb)), fst, sv);
+                }
+            } else {
+                const R cq = I.wall == 1 ? linkc[l] : R(0);
+                sv = wall_own_part(I.wall, cq, C, B);
+            }
             const long long src = (x - ex(k) + nx) % nx + nx * ((y - ey(k) + ny) % ny + ny * ((z - ez(k) + nz) % nz));
             f[(long long)k * ks + src] = sr ? S::pack_sr(sv, I.scale, round_bits(h, k, float(sv))) : S::pack(sv, I.scale);
         }

@@ -234,6 +234,7 @@ struct InstanceDev {
     const uint32_t *bmask;   // [n_boundary]
     const uint32_t *boff;    // [n_boundary]
     const void *linkc;       // [n_links], type R
+    const void *linkw;       // [n_links][kLinkW], type R (walls >= LBM_LIBB), else NULL
     void *linkB;             // [n_links], type T (AA layout)
     double *partials;        // [n_tiles of this instance][kRedSlots]
     long long ncells;
@@ -247,7 +248,7 @@ struct InstanceDev {
     uint32_t push_off[Q];
     FastDiv div_nx, div_ny;  // division by nx and ny
     int nx, ny, nz;
-    int wall;                // 0 = SBB, 1 = CLI
+    int wall;                // 0 = SBB, 1 = CLI, 2 = LIBB, 3 = QIBB, 4 = IEBB, 5 = MR
     int phase;               // A-B: buffer holding the current state when flip == 0
     float scale, inv_scale;  // FP16 deviation scaling
     double omega;            // SRT omega = 1/tau; TRT omega+
@@ -255,6 +256,18 @@ struct InstanceDev {
     double s[Q];             // MRT relaxation rates
     double delta_rho, rho0;
 };
+
+// Coefficients of the interpolated wall rules LIBB, QIBB, IEBB and MR (Sec. 2.2.1), one
+// row of kLinkW values per cut link (x, kbar), x - e_k solid, in the compute type.  With
+// C = g~_kbar(x), B = g~_k(x) (own post-collision values at t), P2 = g~_kbar(x_f2),
+// P3 = g~_kbar(x_f3), B2 = g~_k(x_f2) (x_f2 = x + e_k, x_f3 = x + 2 e_k, read across the x
+// faces with the pressure shift), J2 = e_kbar . sum_m e_m g~_m(x_f2) and the cell's moments
+// drho, u at t, the new g_k is
+//   S + alpha P2 + beta P3 + delta B2 + zeta J2,
+//   S = eps C + gamma B + X w_kbar (drho + rho0 (theta e_kbar.u + 9/2 (e_kbar.u)^2 - 3/2 u.u)),
+// S being the own-cell part each step leaves in the solid slot for the next.  The
+// fallbacks of a rule whose x_f2 or x_f3 is solid are folded into the coefficients.
+enum { LW_EPS = 0, LW_GAMMA, LW_ALPHA, LW_BETA, LW_DELTA, LW_X, LW_THETA, LW_ZETA, kLinkW };
 
 // A tile: consecutive entries of one instance's work list, processed by one thread block:
 // for the step kernels kTileSegs fluid warps (seg0 = the first), for the other kernels

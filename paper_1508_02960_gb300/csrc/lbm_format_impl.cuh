@@ -31,15 +31,17 @@ cudaError_t launch_step(void (*kernel)(P...), const Launch &L, A &&...args)
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
 }
 
-template <int STORE, int COLL, int KIND, bool RED>
+template <int STORE, int COLL, int KIND, bool RED, bool WX>
 cudaError_t step_red(const Launch &L, int flip, unsigned *status, const InstanceDev *one)
 {
     cudaError_t e;
     if (one) {  // a single instance: parameters travel in the constant bank
-        e = launch_step(step_kernel<COLL, STORE, KIND, false, RED>, L, L.table, *one, L.tiles, L.ntiles, flip, status);
+        e = launch_step(step_kernel<COLL, STORE, KIND, false, RED, WX>, L, L.table, *one, L.tiles, L.ntiles, flip,
+                        status);
     } else if constexpr (KIND == KIND_AB) {
         static const InstanceDev unused{};
-        e = launch_step(step_kernel<COLL, STORE, KIND, true, RED>, L, L.table, unused, L.tiles, L.ntiles, flip, status);
+        e = launch_step(step_kernel<COLL, STORE, KIND, true, RED, WX>, L, L.table, unused, L.tiles, L.ntiles, flip,
+                        status);
     } else {
         return cudaErrorInvalidValue;  // the AA layout runs single instances only
     }
@@ -47,26 +49,35 @@ cudaError_t step_red(const Launch &L, int flip, unsigned *status, const Instance
     return cudaGetLastError();
 }
 
+// wx: some instance uses an interpolated wall rule (LIBB, QIBB, IEBB, MR; A-B only)
 template <int STORE, int COLL, int KIND>
-cudaError_t step_one(const Launch &L, int flip, int reduce, unsigned *status, const InstanceDev *one)
+cudaError_t step_one(const Launch &L, int flip, int reduce, unsigned *status, const InstanceDev *one, int wx)
 {
-    return reduce ? step_red<STORE, COLL, KIND, true>(L, flip, status, one)
-                  : step_red<STORE, COLL, KIND, false>(L, flip, status, one);
+    if constexpr (KIND == KIND_AB) {
+        if (wx)
+            return reduce ? step_red<STORE, COLL, KIND, true, true>(L, flip, status, one)
+                          : step_red<STORE, COLL, KIND, false, true>(L, flip, status, one);
+    } else {
+        if (wx) return cudaErrorInvalidValue;
+    }
+    return reduce ? step_red<STORE, COLL, KIND, true, false>(L, flip, status, one)
+                  : step_red<STORE, COLL, KIND, false, false>(L, flip, status, one);
 }
 
 template <int STORE>
-cudaError_t step(int coll, int kind, const Launch &L, int flip, int reduce, unsigned *status, const InstanceDev *one)
+cudaError_t step(int coll, int kind, const Launch &L, int flip, int reduce, unsigned *status, const InstanceDev *one,
+                 int wx)
 {
     switch (coll * 3 + kind) {
-    case COLL_SRT * 3 + KIND_AB: return step_one<STORE, COLL_SRT, KIND_AB>(L, flip, reduce, status, one);
-    case COLL_SRT * 3 + KIND_AA_PULL: return step_one<STORE, COLL_SRT, KIND_AA_PULL>(L, flip, reduce, status, one);
-    case COLL_SRT * 3 + KIND_AA_LOCAL: return step_one<STORE, COLL_SRT, KIND_AA_LOCAL>(L, flip, reduce, status, one);
-    case COLL_TRT * 3 + KIND_AB: return step_one<STORE, COLL_TRT, KIND_AB>(L, flip, reduce, status, one);
-    case COLL_TRT * 3 + KIND_AA_PULL: return step_one<STORE, COLL_TRT, KIND_AA_PULL>(L, flip, reduce, status, one);
-    case COLL_TRT * 3 + KIND_AA_LOCAL: return step_one<STORE, COLL_TRT, KIND_AA_LOCAL>(L, flip, reduce, status, one);
-    case COLL_MRT * 3 + KIND_AB: return step_one<STORE, COLL_MRT, KIND_AB>(L, flip, reduce, status, one);
-    case COLL_MRT * 3 + KIND_AA_PULL: return step_one<STORE, COLL_MRT, KIND_AA_PULL>(L, flip, reduce, status, one);
-    case COLL_MRT * 3 + KIND_AA_LOCAL: return step_one<STORE, COLL_MRT, KIND_AA_LOCAL>(L, flip, reduce, status, one);
+    case COLL_SRT * 3 + KIND_AB: return step_one<STORE, COLL_SRT, KIND_AB>(L, flip, reduce, status, one, wx);
+    case COLL_SRT * 3 + KIND_AA_PULL: return step_one<STORE, COLL_SRT, KIND_AA_PULL>(L, flip, reduce, status, one, wx);
+    case COLL_SRT * 3 + KIND_AA_LOCAL: return step_one<STORE, COLL_SRT, KIND_AA_LOCAL>(L, flip, reduce, status, one, wx);
+    case COLL_TRT * 3 + KIND_AB: return step_one<STORE, COLL_TRT, KIND_AB>(L, flip, reduce, status, one, wx);
+    case COLL_TRT * 3 + KIND_AA_PULL: return step_one<STORE, COLL_TRT, KIND_AA_PULL>(L, flip, reduce, status, one, wx);
+    case COLL_TRT * 3 + KIND_AA_LOCAL: return step_one<STORE, COLL_TRT, KIND_AA_LOCAL>(L, flip, reduce, status, one, wx);
+    case COLL_MRT * 3 + KIND_AB: return step_one<STORE, COLL_MRT, KIND_AB>(L, flip, reduce, status, one, wx);
+    case COLL_MRT * 3 + KIND_AA_PULL: return step_one<STORE, COLL_MRT, KIND_AA_PULL>(L, flip, reduce, status, one, wx);
+    case COLL_MRT * 3 + KIND_AA_LOCAL: return step_one<STORE, COLL_MRT, KIND_AA_LOCAL>(L, flip, reduce, status, one, wx);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -76,15 +87,15 @@ template <int STORE>
 const void *step_ptr(int coll, int kind)
 {
     switch (coll * 3 + kind) {
-    case COLL_SRT * 3 + KIND_AB: return (const void *)step_kernel<COLL_SRT, STORE, KIND_AB, false, false>;
-    case COLL_SRT * 3 + KIND_AA_PULL: return (const void *)step_kernel<COLL_SRT, STORE, KIND_AA_PULL, false, false>;
-    case COLL_SRT * 3 + KIND_AA_LOCAL: return (const void *)step_kernel<COLL_SRT, STORE, KIND_AA_LOCAL, false, false>;
-    case COLL_TRT * 3 + KIND_AB: return (const void *)step_kernel<COLL_TRT, STORE, KIND_AB, false, false>;
-    case COLL_TRT * 3 + KIND_AA_PULL: return (const void *)step_kernel<COLL_TRT, STORE, KIND_AA_PULL, false, false>;
-    case COLL_TRT * 3 + KIND_AA_LOCAL: return (const void *)step_kernel<COLL_TRT, STORE, KIND_AA_LOCAL, false, false>;
-    case COLL_MRT * 3 + KIND_AB: return (const void *)step_kernel<COLL_MRT, STORE, KIND_AB, false, false>;
-    case COLL_MRT * 3 + KIND_AA_PULL: return (const void *)step_kernel<COLL_MRT, STORE, KIND_AA_PULL, false, false>;
-    case COLL_MRT * 3 + KIND_AA_LOCAL: return (const void *)step_kernel<COLL_MRT, STORE, KIND_AA_LOCAL, false, false>;
+    case COLL_SRT * 3 + KIND_AB: return (const void *)step_kernel<COLL_SRT, STORE, KIND_AB, false, false, false>;
+    case COLL_SRT * 3 + KIND_AA_PULL: return (const void *)step_kernel<COLL_SRT, STORE, KIND_AA_PULL, false, false, false>;
+    case COLL_SRT * 3 + KIND_AA_LOCAL: return (const void *)step_kernel<COLL_SRT, STORE, KIND_AA_LOCAL, false, false, false>;
+    case COLL_TRT * 3 + KIND_AB: return (const void *)step_kernel<COLL_TRT, STORE, KIND_AB, false, false, false>;
+    case COLL_TRT * 3 + KIND_AA_PULL: return (const void *)step_kernel<COLL_TRT, STORE, KIND_AA_PULL, false, false, false>;
+    case COLL_TRT * 3 + KIND_AA_LOCAL: return (const void *)step_kernel<COLL_TRT, STORE, KIND_AA_LOCAL, false, false, false>;
+    case COLL_MRT * 3 + KIND_AB: return (const void *)step_kernel<COLL_MRT, STORE, KIND_AB, false, false, false>;
+    case COLL_MRT * 3 + KIND_AA_PULL: return (const void *)step_kernel<COLL_MRT, STORE, KIND_AA_PULL, false, false, false>;
+    case COLL_MRT * 3 + KIND_AA_LOCAL: return (const void *)step_kernel<COLL_MRT, STORE, KIND_AA_LOCAL, false, false, false>;
     default: return nullptr;
     }
 }

@@ -25,9 +25,10 @@ struct Launch {
 
 // Per-storage-format kernel entry points (one translation unit per format).
 struct FormatOps {
-    // one: host copy of the only instance's parameters (passed by value), or NULL for a batch
+    // one: host copy of the only instance's parameters (passed by value), or NULL for a batch;
+    // wx: some instance uses LIBB, QIBB, IEBB or MR (A-B layout)
     cudaError_t (*step)(int coll, int kind, const Launch &L, int flip, int reduce, unsigned *status,
-                        const InstanceDev *one);
+                        const InstanceDev *one, int wx);
     cudaError_t (*init)(const InstanceDev *table, int inst, long long ncells, int layout, int cur,
                         double amp, unsigned long long seed, cudaStream_t s);
     cudaError_t (*import_dir)(const InstanceDev *table, int inst, long long ncells, int layout, int cur,
@@ -62,16 +63,18 @@ struct GeometryDev {
     long long *bcell = nullptr;    // [n_boundary] cell index of each boundary cell
     double *linkq = nullptr;       // [n_links] wall distance q (FP64)
     void *linkc = nullptr;         // [n_links] CLI coefficient, compute type
+    void *linkw = nullptr;         // [n_links][kLinkW] rule coefficients (LIBB, QIBB, IEBB, MR)
     size_t bytes = 0;
 };
 
 // Builds the geometry tables.  spheres (host, n*4 doubles) or flags (host [ncells]);
-// q_host optional [19][ncells] wall distances indexed by link direction.  linkc is
-// written as double when c_double, else float.  Returns a CUDA error or cudaSuccess;
+// q_host optional [19][ncells] wall distances indexed by link direction.  linkc (and, for
+// walls >= LBM_LIBB, linkw: the coefficients of the rule, see lbm_device.cuh) are written
+// as double when c_double, else float; tau enters IEBB's coefficients.  Returns a CUDA error or cudaSuccess;
 // *err receives a message on failure.
 cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_spheres,
-                           const uint8_t *flags, const double *q_host, bool c_double, cudaStream_t s,
-                           GeometryDev *g, std::string *err);
+                           const uint8_t *flags, const double *q_host, bool c_double, int wall, double tau,
+                           cudaStream_t s, GeometryDev *g, std::string *err);
 void free_geometry(GeometryDev *g);
 // Scatter link q values into qk[ncells] for link direction kdir (NaN elsewhere).
 cudaError_t export_wall_distances(const GeometryDev &g, int kdir, double *qk, cudaStream_t s);

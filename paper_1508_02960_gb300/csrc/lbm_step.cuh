@@ -188,6 +188,86 @@ __device__ __forceinline__ void collide(R (&g)[Q], const Par<R> &p, const R *rat
     }
 }
 
+// Cell index of the periodic image of x + (dx, dy, dz), |d| <= 2; xv receives the virtual
+// x coordinate (outside [0, nx) when the offset crosses an x face).
+template <typename R>
+__device__ __forceinline__ uint32_t offset_cell(const Par<R> &P, uint32_t cell, int dx, int dy, int dz, int &xv)
+{
+    const uint32_t yz = fast_div(cell, P.dnx);
+    const int x = (int)(cell - yz * P.nx);
+    const uint32_t zz = fast_div(yz, P.dny);
+    const int y = (int)(yz - zz * P.ny), z = (int)zz;
+    const int nx = (int)P.nx, ny = (int)P.ny, nz = (int)P.nz;
+    xv = x + dx;
+    const int xs = ((x + dx) % nx + nx) % nx, ys = ((y + dy) % ny + ny) % ny, zs = ((z + dz) % nz + nz) % nz;
+    return (uint32_t)xs + P.nx * ((uint32_t)ys + P.ny * (uint32_t)zs);
+}
+
+// Population of direction m read at a virtual x coordinate: the pressure shift of a value
+// that crossed an x face (Sec. 2.2.2, as for the pulls).
+template <typename R> __device__ __forceinline__ R shifted(R v, int xv, int nx, R w_dshift)
+{
+    return xv < 0 ? v + w_dshift : (xv >= nx ? v - w_dshift : v);
+}
+
+// The neighbour terms alpha P2 + beta P3 + delta B2 + zeta J2 of an interpolated wall rule
+// (kLinkW) of link (x, kbar), x - e_k solid, added to v (which holds S).
+template <int STORE, typename R>
+__device__ __forceinline__ R wall_neighbour_terms(const Par<R> &P, const R *lw, int k, uint32_t cell, const R (&g)[Q],
+                                                  const typename Store<STORE>::T *fs, R v)
+{
+    using S = Store<STORE>;
+    const int kb = opp(k);
+    const R al = lw[LW_ALPHA], be = lw[LW_BETA], de = lw[LW_DELTA], ze = lw[LW_ZETA];
+    if (al != R(0)) v = fma_r(al, g[kb], v);  // P2: the ordinary pull of kbar from x_f2
+    if (be != R(0)) {                          // P3 = g~_kbar(x_f3)
+        int xv;
+        const uint32_t c3 = offset_cell(P, cell, 2 * ex(k), 2 * ey(k), 2 * ez(k), xv);
+        const R p3 = shifted(S::load(fs + ((uint32_t)kb * P.ks + c3), P.isc), xv, (int)P.nx,
+                             R(weight(kb)) * P.dshift);
+        v = fma_r(be, p3, v);
+    }
+    if (de != R(0) || ze != R(0)) {
+        int xv;
+        const uint32_t c2 = offset_cell(P, cell, ex(k), ey(k), ez(k), xv);
+        if (de != R(0)) {  // B2 = g~_k(x_f2)
+            const R b2 = shifted(S::load(fs + ((uint32_t)k * P.ks + c2), P.isc), xv, (int)P.nx,
+                                 R(weight(k)) * P.dshift);
+            v = fma_r(de, b2, v);
+        }
+        if (ze != R(0)) {  // J2 = e_kbar . (momentum of x_f2); the shift carries none
+            R j2 = R(0);
+#pragma unroll
+            for (int m = 1; m < Q; ++m) {
+                const int d = ex(kb) * ex(m) + ey(kb) * ey(m) + ez(kb) * ez(m);
+                if (d == 0) continue;
+                const R gm = S::load(fs + ((uint32_t)m * P.ks + c2), P.isc);
+                j2 += d > 0 ? (d == 1 ? gm : R(d) * gm) : (d == -1 ? -gm : R(d) * gm);
+            }
+            v = fma_r(ze, j2, v);
+        }
+    }
+    return v;
+}
+
+// The own-cell part S of an interpolated wall rule (kLinkW) from the cell's post-collision
+// values g[] and its moments drho, u at this step.
+template <typename R>
+__device__ __forceinline__ R wall_own_part_w(const Par<R> &P, const R *lw, int k, const R (&g)[Q], R drho, R ux, R uy,
+                                             R uz)
+{
+    const int kb = opp(k);
+    R sv = fma_r(lw[LW_GAMMA], g[k], lw[LW_EPS] * g[kb]);
+    const R X = lw[LW_X];
+    if (X != R(0)) {
+        const R eu = R(ex(kb)) * ux + R(ey(kb)) * uy + R(ez(kb)) * uz;
+        const R uu = ux * ux + uy * uy + uz * uz;
+        const R fst = drho + P.rho0 * (lw[LW_THETA] * eu + R(4.5) * eu * eu - R(1.5) * uu);
+        sv = fma_r(X * R(weight(kb)), fst, sv);
+    }
+    return sv;
+}
+
 // Process one cell whose 19 pulled populations are in g[] (already shifted, except the
 // wall directions): walls, moments, collision, stores.  When RED is set, returns the
 // moments through rd..rz and the momentum the cell's wall links hand to the solid in this
@@ -203,11 +283,11 @@ __device__ __forceinline__ void collide(R (&g)[Q], const Par<R> &p, const R *rat
 // imported populations) gets these slots from wall_prepare_kernel.
 // Walls in the AA layout: C is in the own slot k, B (CLI) in the link buffer linkB, and
 // the same arithmetic runs at the start of the step.
-template <int COLL, int STORE, int KIND, bool RED, typename R>
+template <int COLL, int STORE, int KIND, bool RED, bool WX, typename R>
 __device__ __forceinline__ void finish_cell(R (&g)[Q], const Par<R> &P, const R *rates, uint32_t cell, uint32_t x,
                                             bool inner, const uint32_t *pull_off, const uint32_t *push_off,
                                             uint32_t wm, uint32_t off, const typename Store<STORE>::T *fs,
-                                            typename Store<STORE>::T *fd, const R *linkc,
+                                            typename Store<STORE>::T *fd, const R *linkc, const R *linkw,
                                             typename Store<STORE>::T *linkB, unsigned *status, R &rd, R &rx, R &ry,
                                             R &rz, R (&fm)[3])
 {
@@ -224,7 +304,8 @@ __device__ __forceinline__ void finish_cell(R (&g)[Q], const Par<R> &P, const R 
             R v, C;
             if constexpr (KIND == KIND_AB) {
                 v = g[k];  // S, left by the previous step in the solid slot
-                if (cq != R(0)) v = fma_r(cq, g[kb], v);
+                if (WX && P.wall >= 2) v = wall_neighbour_terms<STORE>(P, linkw + (size_t)l * kLinkW, k, cell, g, fs, v);
+                else if (cq != R(0)) v = fma_r(cq, g[kb], v);
                 if constexpr (RED) C = S::load(fs + ((uint32_t)kb * KS + cell), P.isc);
             } else {
                 C = S::load(fs + ((uint32_t)k * KS + cell), P.isc);  // own g~_kbar(x)
@@ -297,8 +378,14 @@ __device__ __forceinline__ void finish_cell(R (&g)[Q], const Par<R> &P, const R 
 #pragma unroll
             for (int k = 1; k < Q; ++k) {
                 if (!((wm >> k) & 1u)) continue;
-                const R cq = P.wall == 1 ? linkc[off + __popc(wm & ((1u << k) - 1u))] : R(0);
-                const R sv = wall_own_part(P.wall, cq, g[opp(k)], g[k]);
+                const uint32_t l = off + __popc(wm & ((1u << k) - 1u));
+                R sv;
+                if (WX && P.wall >= 2) {
+                    sv = wall_own_part_w(P, linkw + (size_t)l * kLinkW, k, g, drho, ux, uy, uz);
+                } else {
+                    const R cq = P.wall == 1 ? linkc[l] : R(0);
+                    sv = wall_own_part(P.wall, cq, g[opp(k)], g[k]);
+                }
                 uint32_t idx;
                 if (inner) {
                     idx = cell + pull_off[k];
@@ -394,7 +481,7 @@ struct RedAcc {
 // Finish one work item pulled by pull_item: convert, pressure shift of the pulls that
 // crossed the x boundary, walls, collision, stores; with RED, add the lane's moments and
 // momentum exchange to acc.
-template <int COLL, int STORE, int KIND, bool RED, typename R>
+template <int COLL, int STORE, int KIND, bool RED, bool WX, typename R>
 __device__ __forceinline__ void finish_item(const InstanceDev &I, const Par<R> &P, const R *rates,
                                             const typename Store<STORE>::T (&raw)[Q], const WarpItem &it, int lane,
                                             const typename Store<STORE>::T *fs, typename Store<STORE>::T *fd,
@@ -421,10 +508,11 @@ __device__ __forceinline__ void finish_item(const InstanceDev &I, const Par<R> &
     }
     R rd = R(0), rx = R(0), ry = R(0), rz = R(0);
     R fm[3] = {R(0), R(0), R(0)};
-    finish_cell<COLL, STORE, KIND, RED, R>(g, P, rates, it.cell, it.x, it.inner, I.pull_off,
-                                           it.inner ? I.push_off : nullptr, wm, it.off, fs, fd,
-                                           reinterpret_cast<const R *>(I.linkc), reinterpret_cast<T *>(I.linkB),
-                                           status, rd, rx, ry, rz, fm);
+    finish_cell<COLL, STORE, KIND, RED, WX, R>(g, P, rates, it.cell, it.x, it.inner, I.pull_off,
+                                               it.inner ? I.push_off : nullptr, wm, it.off, fs, fd,
+                                               reinterpret_cast<const R *>(I.linkc),
+                                               reinterpret_cast<const R *>(I.linkw), reinterpret_cast<T *>(I.linkB),
+                                               status, rd, rx, ry, rz, fm);
     if constexpr (RED) {
         acc.v[RED_DRHO] += (double)rd;
         acc.v[RED_U + 0] += (double)rx;
@@ -483,8 +571,9 @@ __device__ __forceinline__ const InstanceDev &instance_of(const InstanceDev *tab
 // (src = f[phase ^ flip]).  The RED variant (the step that ends a chunk) also makes every
 // tile write its FP64 partial sums (the kRedSlots slots: drho, u_x, u_y, u_z and the
 // momentum exchanged with the solid) and flags diverged cells in status[instance]; the
-// other steps carry none of that code.
-template <int COLL, int STORE, int KIND, bool BATCH, bool RED>
+// other steps carry none of that code.  The WX variant (A-B only) also runs the
+// interpolated wall rules LIBB, QIBB, IEBB and MR.
+template <int COLL, int STORE, int KIND, bool BATCH, bool RED, bool WX>
 __global__ void __launch_bounds__(kStepWarps * 32, step_min_blocks<STORE, KIND>())
     step_kernel(const InstanceDev *__restrict__ table, const __grid_constant__ InstanceDev one,
                 const TileDev *__restrict__ tiles, int ntiles, int flip, unsigned *__restrict__ status)
@@ -517,7 +606,7 @@ __global__ void __launch_bounds__(kStepWarps * 32, step_min_blocks<STORE, KIND>(
     T raw[Q];
     pull_item<STORE, KIND, R>(I, P, fs, it, raw);
     RedAcc acc{};
-    finish_item<COLL, STORE, KIND, RED, R>(I, P, rates, raw, it, lane, fs, fd, status + tile.inst, acc);
+    finish_item<COLL, STORE, KIND, RED, WX, R>(I, P, rates, raw, it, lane, fs, fd, status + tile.inst, acc);
     if constexpr (RED) reduce_tile(acc, I.partials, tile.local);
 }
 

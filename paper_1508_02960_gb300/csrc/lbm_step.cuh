@@ -188,19 +188,32 @@ __device__ __forceinline__ void collide(R (&g)[Q], const Par<R> &p, const R *rat
     }
 }
 
-// Cell index of the periodic image of x + (dx, dy, dz), |d| <= 2; xv receives the virtual
-// x coordinate (outside [0, nx) when the offset crosses an x face).
+// Periodic wrap of c + d into [0, n) for |d| <= 2 (any n >= 1).
+__device__ __forceinline__ int wrap2(int c, int n)
+{
+    if (c < 0) c += n;
+    if (c < 0) c += n;
+    if (c >= n) c -= n;
+    if (c >= n) c -= n;
+    return c;
+}
+
+// Cells of the periodic images of x + e_k and x + 2 e_k (x_f2, x_f3 of the link (x, kbar));
+// xv2 / xv3 receive their virtual x coordinates (outside [0, nx) across an x face).
 template <typename R>
-__device__ __forceinline__ uint32_t offset_cell(const Par<R> &P, uint32_t cell, int dx, int dy, int dz, int &xv)
+__device__ __forceinline__ void link_neighbours(const Par<R> &P, uint32_t cell, int k, uint32_t &c2, int &xv2,
+                                                uint32_t &c3, int &xv3)
 {
     const uint32_t yz = fast_div(cell, P.dnx);
     const int x = (int)(cell - yz * P.nx);
     const uint32_t zz = fast_div(yz, P.dny);
     const int y = (int)(yz - zz * P.ny), z = (int)zz;
     const int nx = (int)P.nx, ny = (int)P.ny, nz = (int)P.nz;
-    xv = x + dx;
-    const int xs = ((x + dx) % nx + nx) % nx, ys = ((y + dy) % ny + ny) % ny, zs = ((z + dz) % nz + nz) % nz;
-    return (uint32_t)xs + P.nx * ((uint32_t)ys + P.ny * (uint32_t)zs);
+    xv2 = x + ex(k);
+    xv3 = x + 2 * ex(k);
+    c2 = (uint32_t)wrap2(xv2, nx) + P.nx * ((uint32_t)wrap2(y + ey(k), ny) + P.ny * (uint32_t)wrap2(z + ez(k), nz));
+    c3 = (uint32_t)wrap2(xv3, nx) +
+         P.nx * ((uint32_t)wrap2(y + 2 * ey(k), ny) + P.ny * (uint32_t)wrap2(z + 2 * ez(k), nz));
 }
 
 // Population of direction m read at a virtual x coordinate: the pressure shift of a value
@@ -211,41 +224,41 @@ template <typename R> __device__ __forceinline__ R shifted(R v, int xv, int nx, 
 }
 
 // The neighbour terms alpha P2 + beta P3 + delta B2 + zeta J2 of an interpolated wall rule
-// (kLinkW) of link (x, kbar), x - e_k solid, added to v (which holds S).
+// (kLinkW) of link (x, kbar), x - e_k solid, added to v (which holds S).  The loads the
+// rule may need are issued before its coefficients arrive (a coefficient of 0 -- a
+// fallback -- multiplies a finite value read from a solid cell's slot).
 template <int STORE, typename R>
-__device__ __forceinline__ R wall_neighbour_terms(const Par<R> &P, const R *lw, int k, uint32_t cell, const R (&g)[Q],
-                                                  const typename Store<STORE>::T *fs, R v)
+__device__ __forceinline__ R wall_neighbour_terms(const Par<R> &P, int wall, const R *lw, int k, uint32_t cell,
+                                                  const R (&g)[Q], const typename Store<STORE>::T *fs, R v)
 {
     using S = Store<STORE>;
     const int kb = opp(k);
-    const R al = lw[LW_ALPHA], be = lw[LW_BETA], de = lw[LW_DELTA], ze = lw[LW_ZETA];
-    if (al != R(0)) v = fma_r(al, g[kb], v);  // P2: the ordinary pull of kbar from x_f2
-    if (be != R(0)) {                          // P3 = g~_kbar(x_f3)
-        int xv;
-        const uint32_t c3 = offset_cell(P, cell, 2 * ex(k), 2 * ey(k), 2 * ez(k), xv);
-        const R p3 = shifted(S::load(fs + ((uint32_t)kb * P.ks + c3), P.isc), xv, (int)P.nx,
+    if (wall == 3 || wall == 5) {  // QIBB, MR: P3 = g~_kbar(x_f3), B2 = g~_k(x_f2)
+        int xv2, xv3;
+        uint32_t c2, c3;
+        link_neighbours(P, cell, k, c2, xv2, c3, xv3);
+        const R b2 = shifted(S::load(fs + ((uint32_t)k * P.ks + c2), P.isc), xv2, (int)P.nx,
+                             R(weight(k)) * P.dshift);
+        const R p3 = shifted(S::load(fs + ((uint32_t)kb * P.ks + c3), P.isc), xv3, (int)P.nx,
                              R(weight(kb)) * P.dshift);
-        v = fma_r(be, p3, v);
-    }
-    if (de != R(0) || ze != R(0)) {
-        int xv;
-        const uint32_t c2 = offset_cell(P, cell, ex(k), ey(k), ez(k), xv);
-        if (de != R(0)) {  // B2 = g~_k(x_f2)
-            const R b2 = shifted(S::load(fs + ((uint32_t)k * P.ks + c2), P.isc), xv, (int)P.nx,
-                                 R(weight(k)) * P.dshift);
-            v = fma_r(de, b2, v);
-        }
-        if (ze != R(0)) {  // J2 = e_kbar . (momentum of x_f2); the shift carries none
-            R j2 = R(0);
+        v = fma_r(lw[LW_ALPHA], g[kb], v);
+        v = fma_r(lw[LW_BETA], p3, v);
+        v = fma_r(lw[LW_DELTA], b2, v);
+    } else if (wall == 4) {  // IEBB: J2 = e_kbar . (momentum of x_f2); the shift carries none
+        int xv2, xv3;
+        uint32_t c2, c3;
+        link_neighbours(P, cell, k, c2, xv2, c3, xv3);
+        R j2 = R(0);
 #pragma unroll
-            for (int m = 1; m < Q; ++m) {
-                const int d = ex(kb) * ex(m) + ey(kb) * ey(m) + ez(kb) * ez(m);
-                if (d == 0) continue;
-                const R gm = S::load(fs + ((uint32_t)m * P.ks + c2), P.isc);
-                j2 += d > 0 ? (d == 1 ? gm : R(d) * gm) : (d == -1 ? -gm : R(d) * gm);
-            }
-            v = fma_r(ze, j2, v);
+        for (int m = 1; m < Q; ++m) {
+            const int d = ex(kb) * ex(m) + ey(kb) * ey(m) + ez(kb) * ez(m);
+            if (d == 0) continue;
+            const R gm = S::load(fs + ((uint32_t)m * P.ks + c2), P.isc);
+            j2 += d > 0 ? (d == 1 ? gm : R(d) * gm) : (d == -1 ? -gm : R(d) * gm);
         }
+        v = fma_r(lw[LW_ZETA], j2, v);
+    } else {  // LIBB
+        v = fma_r(lw[LW_ALPHA], g[kb], v);
     }
     return v;
 }
@@ -304,7 +317,8 @@ __device__ __forceinline__ void finish_cell(R (&g)[Q], const Par<R> &P, const R 
             R v, C;
             if constexpr (KIND == KIND_AB) {
                 v = g[k];  // S, left by the previous step in the solid slot
-                if (WX && P.wall >= 2) v = wall_neighbour_terms<STORE>(P, linkw + (size_t)l * kLinkW, k, cell, g, fs, v);
+                if (WX && P.wall >= 2)
+                    v = wall_neighbour_terms<STORE>(P, P.wall, linkw + (size_t)l * kLinkW, k, cell, g, fs, v);
                 else if (cq != R(0)) v = fma_r(cq, g[kb], v);
                 if constexpr (RED) C = S::load(fs + ((uint32_t)kb * KS + cell), P.isc);
             } else {

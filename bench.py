@@ -379,6 +379,63 @@ def study_drag(args):
                       "wall_s": time.perf_counter() - t0}), flush=True)
 
 
+def study_kstar(args):
+    """Apparent permeability and Forchheimer coefficient over Re_p (Sec. 4) on the simple
+    cubic array (one sphere of r = 0.3 L, reading O12), TRT-CLI, FP32 storage, Lambda of
+    Table 1 by Re_p, the mean velocity held near 0.05 by the viscosity (tau >= 0.503): K_D
+    from a Stokes run, then for each Re_p a developed-flow time average (lbm_run_developed:
+    spin-up until the window drag changes < 1e-3 between flow-through times or 200
+    flow-through times have passed, then 30 flow-through times averaged (2 for the steady
+    Re_p = 1 flow) -- the paper spins up
+    400-600 and averages 100-150, at far higher resolution), K* = K_app / K_D (Eq.
+    normalizedPermeability), C_F (Eq. Forchheimer), F_K and Re_K (Eq. frictionFactor), and
+    the Barree-Conway fit (Eq. AppPer) of K*(Re_p) over the points that finished."""
+    import numpy as np
+    import torch
+
+    from paper_1508_02960_gb300 import capi
+    from paper_1508_02960_gb300 import inputs as I
+    L = args.study_size
+    r = 0.3 * L
+    g = I.centred_sphere(L, r)
+    d_p = 2 * r
+    t0 = time.perf_counter()
+
+    def ctx(tau, dr, lam):
+        return capi.Context(spheres=g.spheres, shape=g.shape, tau=tau, delta_rho=dr, magic_lambda=lam,
+                            collision=capi.TRT, wall=capi.CLI, storage=capi.F32, stream=torch.cuda.current_stream())
+
+    with ctx(0.8, 1e-6, 3 / 16) as c:
+        c.init_equilibrium()
+        st, n_darcy = c.run_to_convergence(1e-10, 500, 4000000)
+        K_D = c.observables()["K"]
+    rows = []
+    for re_t in (1.0, 5.0, 10.0, 20.0, 50.0, 80.0, 120.0, 200.0, 300.0, 500.0, 800.0, 1000.0):
+        lam = I.table1_lambda(re_t)
+        tau = min(1.0, max(0.503, 0.5 + 3.0 * 0.05 * d_p / re_t))   # U near 0.05 where tau allows
+        dr = capi.delta_rho_for_re_p(re_t, tau, d_p, L, K_D, 0.0078 if re_t > 1 else 0.0)
+        t1 = time.perf_counter()
+        with ctx(tau, dr, lam) as c:
+            c.init_equilibrium()
+            res = c.run_developed(min_spinup_ft=3, max_spinup_ft=200, drag_tol=1e-3,
+                                  average_ft=2 if re_t < 5 else 30, samples_per_ft=10, max_steps=2_000_000,
+                                  K_darcy=K_D)
+        a = res["avg"]
+        rows.append(dict(re_target=re_t, Re_p=a["Re_p"], tau=tau, Lambda=lam, delta_rho=dr, K_star=a["K_star"],
+                         C_F=a["C_F"], F_K=a["F_K"], Re_K=a["Re_K"], U=a["U_sup"], developed=res["developed"],
+                         spinup_ft=res["spinup_ft"], average_ft=res["average_ft"], drag_change=res["drag_change"],
+                         steps=res["spinup_steps"] + res["average_steps"], status=capi.STATUS.get(res["status"]),
+                         seconds=time.perf_counter() - t1))
+        print(json.dumps({"study": "kstar_point", **rows[-1]}), flush=True)
+    ok = [x for x in rows if x["status"] == "LBM_OK" and np.isfinite(x["K_star"]) and x["Re_p"] > 0]
+    fit = None
+    if len(ok) >= 4:
+        p, rms = capi.fit_barree_conway([x["Re_p"] for x in ok], [x["K_star"] for x in ok])
+        fit = dict(m=p[0], a=p[1], E=p[2], F=p[3], rms=rms, points=len(ok))
+    print(json.dumps({"study": "kstar", "L": L, "r": r, "K_D": K_D, "darcy_steps": n_darcy, "rows": rows,
+                      "barree_conway": fit, "wall_s": time.perf_counter() - t0}), flush=True)
+
+
 def dist_setup(n_gpus: int):
     import torch
     rank, world, local = 0, 1, 0
@@ -604,7 +661,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only build the workload and run this many steps (for ncu), no timing")
-    ap.add_argument("--study", choices=["precision", "sweep", "drag"], default=None,
+    ap.add_argument("--study", choices=["precision", "sweep", "drag", "kstar"], default=None,
                     help="run a study instead of the benchmark (JSON lines)")
     ap.add_argument("--study-size", type=int, default=64)
     ap.add_argument("--study-max-steps", type=int, default=60000)
@@ -622,6 +679,9 @@ def main():
         return
     if args.study == "drag":
         study_drag(args)
+        return
+    if args.study == "kstar":
+        study_kstar(args)
         return
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", 0))

@@ -132,6 +132,7 @@ typedef struct {
     double C_D;       /* F_x / (6 pi mu U_sup r), Eq. AnalyticForce; r = sum of the sphere
                          radii (NaN for a flag-field geometry) */
     double C_D_A;     /* F_x / (rho0 A U_sup^2), A = sum of pi r^2 (Sec. 4 resolution study) */
+    double K_star;    /* K_app / K_D (Eq. normalizedPermeability; needs K_D) */
     int64_t steps;    /* time steps completed */
     int64_t n_fluid;  /* fluid cells */
 } lbm_obs;
@@ -188,7 +189,50 @@ LBM_API lbm_status lbm_run_to_convergence(lbm_ctx *ctx, double tol, int64_t chec
 LBM_API lbm_status lbm_average(lbm_ctx *ctx, int64_t n_samples, int64_t sample_interval, double K_darcy,
                                lbm_obs *out);
 
-/* Observables of the last step (synchronises the stream).  K_darcy > 0 enables beta,
+/* Developed-flow time average (Sec. 4: the averaging starts once the drag on the spheres
+ * has converged and runs over 100-150 flow-through times).  A flow-through time is
+ * T = nx / U_sup steps, U_sup the volume-averaged velocity of the latest sample.
+ * Spin-up: windows of one flow-through time, sampled samples_per_ft times, until the
+ * window-averaged drag F_x changes by less than drag_tol (relative) from the previous
+ * window, after at least min_spinup_ft and at most max_spinup_ft flow-through times.
+ * Averaging: average_ft flow-through times sampled samples_per_ft times each; the moments
+ * and the drag are averaged in FP64.  max_steps caps the whole run. */
+typedef struct {
+    double min_spinup_ft, max_spinup_ft;
+    double drag_tol;
+    double average_ft;
+    int32_t samples_per_ft;
+    int32_t reserved;
+    int64_t max_steps;
+} lbm_develop_opts;
+
+typedef struct {
+    lbm_obs avg;               /* observables of the averaged U and F_D (K_darcy as given) */
+    double flow_through_steps; /* T at the averaged U */
+    double spinup_ft;          /* flow-through times of the spin-up */
+    double average_ft;         /* flow-through times averaged */
+    double drag_change;        /* relative change of the window drag when spin-up ended */
+    int64_t spinup_steps, average_steps;
+    int32_t developed;         /* 1: the drag converged within max_spinup_ft */
+    int32_t reserved;
+} lbm_develop_result;
+
+/* Returns LBM_OK (also when the drag did not converge: see developed), LBM_ERR_DIVERGED,
+ * LBM_ERR_NOT_CONVERGED when max_steps ran out before the averaging ended (out holds the
+ * average so far), LBM_ERR_ARG for bad options or a flow at rest (no flow-through time). */
+LBM_API lbm_status lbm_run_developed(lbm_ctx *ctx, const lbm_develop_opts *opts, double K_darcy,
+                                     lbm_develop_result *out);
+
+/* Least-squares fit of the Barree-Conway apparent permeability (Eq. AppPer), normalised
+ * by K_D (Eq. normalizedPermeability): K*(Re) = m + (1 - m) / (1 + (a Re)^F)^E, with
+ * m = K_min / K_D in (0, 1), a = l_T / d_p (so that a Re_p = Re_T), E, F > 0, over n >= 4
+ * points (re[i] > 0, kstar[i]).  init: starting guess [m, a, E, F] or NULL.  params_out[4]
+ * receives [m, a, E, F], rms_out (may be NULL) the RMS residual in K*.  Host code (no GPU);
+ * Levenberg-Marquardt on (logit m, ln a, ln E, ln F), deterministic. */
+LBM_API lbm_status lbm_fit_barree_conway(const double *re, const double *kstar, int32_t n, const double *init,
+                                         double *params_out, double *rms_out);
+
+/* Observables of the last step (synchronises the stream)./* Observables of the last step (synchronises the stream).  K_darcy > 0 enables beta,
  * C_F, F_K and Re_K; K_darcy = 0 leaves them NaN.  Returns LBM_ERR_DIVERGED (with *out
  * filled) when the last reduction saw a diverged cell. */
 LBM_API lbm_status lbm_observables(lbm_ctx *ctx, double K_darcy, lbm_obs *out);

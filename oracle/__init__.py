@@ -223,3 +223,34 @@ def observables(U, tau, delta_rho, lx, d_p, K_D=0.0, rho0=1.0):
     _load().orc_observables(float(U), float(tau), float(delta_rho), float(rho0), int(lx),
                             float(d_p), float(K_D), _dp(out))
     return out
+
+
+def barree_conway(re, m, a, E, F):
+    """Barree-Conway apparent permeability (Eq. AppPer) normalised by K_D (Eq.
+    normalizedPermeability): K* = m + (1 - m) / (1 + Re_T^F)^E with Re_T = a Re,
+    m = K_min / K_D."""
+    re = np.asarray(re, dtype=np.float64)
+    return m + (1.0 - m) / (1.0 + (a * re) ** F) ** E
+
+
+def fit_barree_conway(re, kstar, init=None):
+    """Least-squares fit of barree_conway to (re, kstar) with scipy's Levenberg-Marquardt
+    least_squares (a library routine), over (logit m, ln a, ln E, ln F) so that 0 < m < 1
+    and a, E, F > 0.  Returns ([m, a, E, F], rms)."""
+    from scipy.optimize import least_squares
+    re = np.asarray(re, dtype=np.float64)
+    kstar = np.asarray(kstar, dtype=np.float64)
+    if init is None:
+        init = [min(0.9, max(0.01, 0.9 * kstar.min())), 1.0 / np.median(re), 1.0, 1.0]
+    x0 = np.array([np.log(init[0] / (1.0 - init[0])), np.log(init[1]), np.log(init[2]), np.log(init[3])])
+
+    def m_of(x0):
+        return 1.0 / (1.0 + np.exp(-x0))
+
+    def res(x):
+        return barree_conway(re, m_of(x[0]), np.exp(x[1]), np.exp(x[2]), np.exp(x[3])) - kstar
+
+    sol = least_squares(res, x0, method="lm", xtol=1e-15, ftol=1e-15, gtol=1e-15, max_nfev=20000)
+    p = np.array([m_of(sol.x[0]), np.exp(sol.x[1]), np.exp(sol.x[2]), np.exp(sol.x[3])])
+    return p, float(np.sqrt(np.mean(sol.fun ** 2)))
+

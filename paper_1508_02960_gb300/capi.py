@@ -65,11 +65,29 @@ class Desc(ctypes.Structure):
 class Obs(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in
                 ("U_sup", "U_int", "mass", "porosity", "K", "K_app", "Re_p", "Re_K", "beta",
-                 "C_F", "F_K", "u_max", "F_x", "F_y", "F_z", "C_D", "C_D_A")] + \
+                 "C_F", "F_K", "u_max", "F_x", "F_y", "F_z", "C_D", "C_D_A", "K_star")] + \
                [("steps", ctypes.c_int64), ("n_fluid", ctypes.c_int64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class DevelopOpts(ctypes.Structure):
+    _fields_ = [("min_spinup_ft", ctypes.c_double), ("max_spinup_ft", ctypes.c_double),
+                ("drag_tol", ctypes.c_double), ("average_ft", ctypes.c_double),
+                ("samples_per_ft", ctypes.c_int32), ("reserved", ctypes.c_int32), ("max_steps", ctypes.c_int64)]
+
+
+class DevelopResult(ctypes.Structure):
+    _fields_ = [("avg", Obs), ("flow_through_steps", ctypes.c_double), ("spinup_ft", ctypes.c_double),
+                ("average_ft", ctypes.c_double), ("drag_change", ctypes.c_double),
+                ("spinup_steps", ctypes.c_int64), ("average_steps", ctypes.c_int64),
+                ("developed", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        d = {n: getattr(self, n) for n, _ in self._fields_ if n not in ("avg", "reserved")}
+        d["avg"] = self.avg.as_dict()
+        return d
 
 
 class Info(ctypes.Structure):
@@ -116,6 +134,8 @@ PROTOTYPES = {
     "lbm_observables": (_st, [_vp, ctypes.c_double, ctypes.POINTER(Obs)]),
     "lbm_moment_sums": (_st, [_vp, _dp]),
     "lbm_average": (_st, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(Obs)]),
+    "lbm_run_developed": (_st, [_vp, ctypes.POINTER(DevelopOpts), ctypes.c_double, ctypes.POINTER(DevelopResult)]),
+    "lbm_fit_barree_conway": (_st, [_dp, _dp, ctypes.c_int32, _dp, _dp, _dp]),
     "lbm_get_populations_f64": (_st, [_vp, _dp]),
     "lbm_set_populations_f64": (_st, [_vp, _dp]),
     "lbm_get_velocity_f64": (_st, [_vp, _dp]),
@@ -303,6 +323,20 @@ class Context:
         d["status"] = st
         return d
 
+    def run_developed(self, *, min_spinup_ft=5.0, max_spinup_ft=200.0, drag_tol=1e-4, average_ft=100.0,
+                      samples_per_ft=10, max_steps=10 ** 9, K_darcy: float = 0.0) -> dict:
+        """Spin up until the drag converges, then time-average (lbm_run_developed)."""
+        o = DevelopOpts(min_spinup_ft=float(min_spinup_ft), max_spinup_ft=float(max_spinup_ft),
+                        drag_tol=float(drag_tol), average_ft=float(average_ft), samples_per_ft=int(samples_per_ft),
+                        max_steps=int(max_steps))
+        r = DevelopResult()
+        st = lib().lbm_run_developed(self._h, ctypes.byref(o), float(K_darcy), ctypes.byref(r))
+        if st not in (OK, ERR_NOT_CONVERGED, ERR_DIVERGED):
+            check(st, "lbm_run_developed")
+        d = r.as_dict()
+        d["status"] = st
+        return d
+
     def moment_sums(self) -> np.ndarray:
         s = np.zeros(4)
         check(lib().lbm_moment_sums(self._h, _f64(s)), "lbm_moment_sums")
@@ -455,6 +489,21 @@ def moment_sums_f64_noalloc(f_dev_ptr: int, solid_dev_ptr: int | None, n_cells: 
     tensor.data_ptr()).  Queued on the stream; does not wait."""
     check(lib().lbm_moment_sums_f64_noalloc(f_dev_ptr, solid_dev_ptr, int(n_cells), float(rho0), sums_dev_ptr,
                                             _stream_handle(stream)), "lbm_moment_sums_f64_noalloc")
+
+
+def fit_barree_conway(re, kstar, init=None):
+    """Least-squares Barree-Conway fit K*(Re) = m + (1-m)/(1 + (a Re)^F)^E (lbm_fit_barree_conway).
+    Returns ([m, a, E, F], rms)."""
+    r = np.ascontiguousarray(re, dtype=np.float64)
+    k = np.ascontiguousarray(kstar, dtype=np.float64)
+    if r.shape != k.shape or r.ndim != 1:
+        raise ValueError("re and kstar must be 1-D arrays of one length")
+    out = np.zeros(4)
+    rms = ctypes.c_double(0.0)
+    ini = None if init is None else np.ascontiguousarray(init, dtype=np.float64)
+    check(lib().lbm_fit_barree_conway(_f64(r), _f64(k), int(r.size), _f64(ini) if ini is not None else None,
+                                      _f64(out), ctypes.byref(rms)), "lbm_fit_barree_conway")
+    return out, rms.value
 
 
 def delta_rho_for_re_p(re_p, tau, d_p, lx, K_D, C_F=0.0, rho0=1.0) -> float:

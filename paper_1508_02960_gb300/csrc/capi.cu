@@ -64,6 +64,7 @@ void compute_obs(const Instance &in, double K_D, lbm_obs *o)
     }
     o->C_D = in.r_sum > 0 ? o->F_x / (6.0 * M_PI * mu * U * in.r_sum) : nan;
     o->C_D_A = in.area_sum > 0 ? o->F_x / (d.rho0 * in.area_sum * U * U) : nan;
+    o->K_star = K_D > 0 ? o->K_app / K_D : nan;
     o->steps = in.steps;
     o->n_fluid = in.geo.n_fluid;
 }
@@ -214,6 +215,99 @@ lbm_status lbm_average(lbm_ctx *ctx, int64_t n_samples, int64_t sample_interval,
     }
     compute_obs(in, K_darcy, out);
     for (int d = 0; d < kRedSlots; ++d) in.sums[d] = keep[d];
+    return result;
+}
+
+lbm_status lbm_run_developed(lbm_ctx *ctx, const lbm_develop_opts *o, double K_darcy, lbm_develop_result *out)
+{
+    if (!ctx || !o || !out) return fail(LBM_ERR_ARG, "NULL argument");
+    if (o->samples_per_ft < 1 || !(o->min_spinup_ft >= 0) || !(o->max_spinup_ft >= o->min_spinup_ft) ||
+        !(o->average_ft > 0) || !(o->drag_tol > 0) || o->max_steps < 1)
+        return fail(LBM_ERR_ARG, "bad developed-average options");
+    std::memset(out, 0, sizeof(*out));
+    Instance &in = ctx->b.at(0);
+    const double nx = (double)in.desc.nx, ncell = (double)in.geo.ncells;
+    int64_t total = 0;
+    // one sample: advance n steps, reduce; the sums describe the last of them
+    auto sample = [&](int64_t n) -> lbm_status {
+        lbm_status st = ctx->b.step(n);
+        if (st != LBM_OK) return st;
+        st = ctx->b.fetch_sums();
+        if (st != LBM_OK) return st;
+        total += n;
+        if (in.status & STATUS_DIVERGED) return fail(LBM_ERR_DIVERGED, "diverged (non-finite moments or |u| > 1)");
+        return LBM_OK;
+    };
+    auto ft_steps = [&](double &T) -> lbm_status {  // T = nx / U_sup of the latest sample
+        const double U = in.sums[RED_U] / ncell;
+        if (!(std::fabs(U) > 0) || !std::isfinite(U)) return fail(LBM_ERR_ARG, "no flow: U_sup is 0");
+        T = std::max(1.0, nx / std::fabs(U));
+        return LBM_OK;
+    };
+    // spin-up: the first sample (nx steps) gives the first flow-through time
+    lbm_status st = sample(std::max<int64_t>(1, (int64_t)nx));
+    if (st != LBM_OK) return st;
+    double T = 0.0;
+    if ((st = ft_steps(T)) != LBM_OK) return st;
+    double spin_ft = 1.0 * (double)total / T, prev = std::numeric_limits<double>::quiet_NaN(), change = 1.0;
+    int64_t spin_steps = total;
+    for (;;) {
+        const int64_t sub = std::max<int64_t>(1, (int64_t)std::llround(T / o->samples_per_ft));
+        if (total + sub * o->samples_per_ft > o->max_steps) {
+            out->spinup_steps = spin_steps;
+            out->spinup_ft = spin_ft;
+            out->drag_change = change;
+            return fail(LBM_ERR_NOT_CONVERGED, "max_steps reached during the spin-up");
+        }
+        double wsum = 0.0;
+        for (int i = 0; i < o->samples_per_ft; ++i) {
+            if ((st = sample(sub)) != LBM_OK) return st;
+            wsum += in.sums[RED_F];
+        }
+        spin_steps += sub * o->samples_per_ft;
+        spin_ft += (double)(sub * o->samples_per_ft) / T;
+        const double W = wsum / o->samples_per_ft;
+        change = std::isnan(prev) ? 1.0 : std::fabs(W - prev) / std::max(std::fabs(W), 1e-300);
+        prev = W;
+        if ((st = ft_steps(T)) != LBM_OK) return st;
+        if (spin_ft >= o->min_spinup_ft && change < o->drag_tol) {
+            out->developed = 1;
+            break;
+        }
+        if (spin_ft >= o->max_spinup_ft) break;
+    }
+    out->spinup_steps = spin_steps;
+    out->spinup_ft = spin_ft;
+    out->drag_change = change;
+    // averaging over average_ft flow-through times
+    const int64_t sub = std::max<int64_t>(1, (int64_t)std::llround(T / o->samples_per_ft));
+    const int64_t n_samples = std::max<int64_t>(1, (int64_t)std::llround(o->average_ft * o->samples_per_ft));
+    double acc[kRedSlots] = {};
+    int64_t done = 0;
+    lbm_status result = LBM_OK;
+    for (int64_t i = 0; i < n_samples; ++i) {
+        if (total + sub > o->max_steps) {
+            result = fail(LBM_ERR_NOT_CONVERGED, "max_steps reached during the averaging");
+            break;
+        }
+        if ((st = sample(sub)) != LBM_OK) return st;
+        for (int d = 0; d < kRedSlots; ++d) acc[d] += in.sums[d];
+        ++done;
+    }
+    if (done == 0) return result == LBM_OK ? fail(LBM_ERR_NOT_CONVERGED, "no averaging sample") : result;
+    double keep[kRedSlots];
+    for (int d = 0; d < kRedSlots; ++d) {
+        keep[d] = in.sums[d];
+        in.sums[d] = acc[d] / (double)done;
+    }
+    const bool hf = in.have_force;
+    in.have_force = true;
+    compute_obs(in, K_darcy, &out->avg);
+    in.have_force = hf;
+    for (int d = 0; d < kRedSlots; ++d) in.sums[d] = keep[d];
+    out->average_steps = done * sub;
+    out->flow_through_steps = out->avg.U_sup != 0 ? nx / std::fabs(out->avg.U_sup) : 0.0;
+    out->average_ft = out->flow_through_steps > 0 ? (double)out->average_steps / out->flow_through_steps : 0.0;
     return result;
 }
 

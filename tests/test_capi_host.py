@@ -50,18 +50,23 @@ int main(void) {
          sizeof(lbm_server_opts), sizeof(lbm_server_stats), sizeof(lbm_sphere));
   printf("%zu %zu %zu %zu %zu\\n", offsetof(lbm_desc, tau), offsetof(lbm_desc, collision),
          offsetof(lbm_desc, d_p), offsetof(lbm_desc, seed), offsetof(lbm_info, block_cells));
+  printf("%zu %zu %zu %zu %zu\\n", sizeof(lbm_develop_opts), sizeof(lbm_develop_result),
+         offsetof(lbm_develop_result, developed), offsetof(lbm_obs, K_star), offsetof(lbm_develop_opts, max_steps));
   return 0;
 }
 """)
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
-    a, b = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
+    a, b, c = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:3]
     sizes = [int(v) for v in a.split()]
     offs = [int(v) for v in b.split()]
     assert sizes == [ctypes.sizeof(capi.Desc), ctypes.sizeof(capi.Obs), ctypes.sizeof(capi.Info),
                      ctypes.sizeof(capi.ServerOpts), ctypes.sizeof(capi.ServerStats), ctypes.sizeof(capi.Sphere)]
     assert offs == [capi.Desc.tau.offset, capi.Desc.collision.offset, capi.Desc.d_p.offset,
                     capi.Desc.seed.offset, capi.Info.block_cells.offset]
+    assert [int(v) for v in c.split()] == [ctypes.sizeof(capi.DevelopOpts), ctypes.sizeof(capi.DevelopResult),
+                                           capi.DevelopResult.developed.offset, capi.Obs.K_star.offset,
+                                           capi.DevelopOpts.max_steps.offset]
 
 
 @pytest.mark.parametrize("bad", [

@@ -104,7 +104,9 @@ typedef struct {
     int32_t storage;            /* LBM_F64 / LBM_F32 / LBM_F16DEV / LBM_BF16DEV */
     int32_t layout;             /* LBM_LAYOUT_AB / LBM_LAYOUT_AA */
     int32_t dev_scale_log2;     /* FP16DEV scale exponent; LBM_DEV_SCALE_AUTO = from delta_rho */
-    int32_t block_cells;        /* cells per thread block: 0 = default, else 64..256, /32 */
+    int32_t block_cells;        /* step kernel: 0 or 128 = tiles of 128 fluid cells (default);
+                                   256 = bricks of 32 x 2 x 4 cells staged by TMA (single A-B
+                                   instance; nx, ny, nz multiples of 32, 2, 4) */
     double d_p;                 /* particle diameter of Re_p; 0 = volume-mean sphere diameter */
     double perturb_u;           /* lbm_init_equilibrium: amplitude of a seeded random initial
                                    velocity (0 = fluid at rest) */

@@ -6,6 +6,7 @@
 // (n steps + the final FP64 reduction) and replayed on the caller's stream.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -79,8 +80,11 @@ lbm_status validate_desc(const lbm_desc &d)
     if (d.magic_lambda < 0 || !std::isfinite(d.magic_lambda)) return fail(LBM_ERR_ARG, "magic_lambda must be >= 0");
     if (d.mrt_energy_ratio < 0 || !std::isfinite(d.mrt_energy_ratio))
         return fail(LBM_ERR_ARG, "mrt_energy_ratio must be >= 0");
-    if (d.block_cells != 0 && d.block_cells != 32 * kTileSegs)
-        return fail(LBM_ERR_ARG, "block_cells is reserved: 0 (or the tile size)");
+    if (d.block_cells != 0 && d.block_cells != 32 * kTileSegs && d.block_cells != kBrickCells)
+        return fail(LBM_ERR_ARG, "block_cells: 0 or 128 (tiles of fluid cells) or 256 (TMA bricks)");
+    if (d.block_cells == kBrickCells &&
+        (d.layout != LBM_LAYOUT_AB || d.nx % kBrickX || d.ny % kBrickY || d.nz % kBrickZ))
+        return fail(LBM_ERR_ARG, "TMA bricks need the A-B layout and nx, ny, nz multiples of 32, 2, 4");
     if (d.dev_scale_log2 != LBM_DEV_SCALE_AUTO && (d.dev_scale_log2 < -60 || d.dev_scale_log2 > 60))
         return fail(LBM_ERR_ARG, "dev_scale_log2 out of [-60, 60]");
     if (!std::isfinite(d.perturb_u) || std::fabs(d.perturb_u) > 0.3) return fail(LBM_ERR_ARG, "|perturb_u| > 0.3");
@@ -212,6 +216,8 @@ Batch::~Batch()
     cudaFree(d_stiles_);
     cudaFree(d_stile_begin_);
     cudaFree(d_stile_count_);
+    cudaFree(d_bricks_);
+    cudaFree(d_tma_err_);
     cudaFree(d_sums_);
     cudaFree(d_status_);
     cudaFree(d_stage_);
@@ -259,12 +265,22 @@ lbm_status Batch::remove(int i)
 
 lbm_status Batch::set_block(int block_cells)
 {
-    if (block_cells != 32 * kTileSegs) return fail(LBM_ERR_ARG, "block_cells is reserved: 0 (or the tile size)");
-    if (block_cells != block_) {
-        block_ = block_cells;
+    int mode;
+    if (block_cells == 0) mode = 0;
+    else if (block_cells == 32 * kTileSegs) mode = 1;
+    else if (block_cells == kBrickCells) mode = 2;
+    else return fail(LBM_ERR_ARG, "block_cells: 0 or 128 (tiles of fluid cells) or 256 (TMA bricks)");
+    if (mode != step_mode_) {
+        step_mode_ = mode;
         dirty_ = true;
     }
     return LBM_OK;
+}
+
+lbm_status Batch::prepare()
+{
+    if (!dirty_ || size() == 0) return LBM_OK;
+    return rebuild();
 }
 
 long long Batch::fluid_cells() const
@@ -328,6 +344,104 @@ static void fill_dev(const Instance &in, InstanceDev &D)
     }
     D.delta_rho = d.delta_rho;
     D.rho0 = d.rho0;
+}
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link to the driver library)
+typedef CUresult (*TensorMapEncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                         const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                         CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                         CUtensorMapFloatOOBfill);
+
+static TensorMapEncodeTiled tensor_map_encoder()
+{
+    static std::mutex mu;
+    static TensorMapEncodeTiled fn = nullptr;
+    static bool tried = false;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<TensorMapEncodeTiled>(p);
+    }
+    return fn;
+}
+
+lbm_status Batch::setup_tma()
+{
+    tma_ = false;
+    cudaFree(d_bricks_);
+    d_bricks_ = nullptr;
+    // the brick kernel runs on request only (block_cells = kBrickCells): on the sphere cells
+    // measured here the tile kernel over fluid cells is faster (see lbm_tma.cuh)
+    auto not_here = [&](const char *why) { return fail(LBM_ERR_ARG, why); };
+    if (step_mode_ != 2) return LBM_OK;
+    if (size() != 1 || layout_ != LBM_LAYOUT_AB) return not_here("TMA bricks run single A-B instances only");
+    Instance &in = *inst_[0];
+    const lbm_desc &d = in.desc;
+    if (d.nx % kBrickX || d.ny % kBrickY || d.nz % kBrickZ)
+        return not_here("TMA bricks need nx, ny, nz multiples of 32, 2, 4");
+    if (d.nx / kBrickX > 1024 || d.ny / kBrickY > 2048 || d.nz / kBrickZ > 2048)
+        return not_here("box too large for the brick list (nx <= 32768, ny <= 4096, nz <= 8192)");
+    TensorMapEncodeTiled enc = tensor_map_encoder();
+    if (!enc) return not_here("cuTensorMapEncodeTiled is not available");
+    const int wx = d.wall >= LBM_LIBB;
+    const int per_sm = ops().tma_prepare(collision_, wx);
+    if (per_sm <= 0) return not_here("the TMA brick kernel does not fit on a multiprocessor");
+    // bricks holding fluid, from the 32-cell segment table
+    const long long nseg = in.geo.nseg;
+    std::vector<uint4> seg((size_t)nseg);
+    CK(cudaMemcpy(seg.data(), in.geo.seg, sizeof(uint4) * nseg, cudaMemcpyDeviceToHost));
+    const int bx_n = d.nx / kBrickX, by_n = d.ny / kBrickY, bz_n = d.nz / kBrickZ;
+    std::vector<uint32_t> list;
+    for (int bz = 0; bz < bz_n; ++bz)
+        for (int by = 0; by < by_n; ++by)
+            for (int bx = 0; bx < bx_n; ++bx) {
+                bool fluid = false;
+                for (int dz = 0; dz < kBrickZ && !fluid; ++dz)
+                    for (int dy = 0; dy < kBrickY && !fluid; ++dy) {
+                        const long long y = (long long)by * kBrickY + dy, z = (long long)bz * kBrickZ + dz;
+                        fluid = seg[(size_t)(bx + (long long)bx_n * (y + (long long)d.ny * z))].x != 0xFFFFFFFFu;
+                    }
+                if (fluid) list.push_back((uint32_t)bx | (uint32_t)by << 10 | (uint32_t)bz << 21);
+            }
+    if (list.empty()) return not_here("no fluid");
+    CK(cudaMalloc(&d_bricks_, sizeof(uint32_t) * list.size()));
+    CK(cudaMemcpy(d_bricks_, list.data(), sizeof(uint32_t) * list.size(), cudaMemcpyHostToDevice));
+    if (!d_tma_err_) {
+        CK(cudaMalloc(&d_tma_err_, sizeof(unsigned)));
+        CK(cudaMemset(d_tma_err_, 0, sizeof(unsigned)));
+    }
+    // tensor maps [nz][ny][nx] x 19 directions of both buffers, boxes kBrickX and kBrickX + 16 B wide
+    const size_t es = storage_bytes(storage_);
+    const CUtensorMapDataType dt = storage_ == LBM_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                   : storage_ == LBM_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : storage_ == LBM_F16DEV ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                            : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const cuuint64_t dims[4] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz, (cuuint64_t)Q};
+    const cuuint64_t strides[3] = {(cuuint64_t)d.nx * es, (cuuint64_t)d.nx * d.ny * es, (cuuint64_t)in.ks * es};
+    const cuuint32_t boxes[2][4] = {{(cuuint32_t)kBrickX, kBrickY, kBrickZ, 1},
+                                    {(cuuint32_t)(kBrickX + 16 / es), kBrickY, kBrickZ, 1}};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    for (int b = 0; b < 2; ++b)
+        for (int w = 0; w < 2; ++w) {
+            const CUresult r = enc(&tma_launch_.map[b][w], dt, 4, b ? in.f1 : in.f0, dims, strides, boxes[w], estr,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return not_here("cuTensorMapEncodeTiled rejected the population layout");
+        }
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    tma_launch_.bricks = d_bricks_;
+    tma_launch_.nbricks = (int)list.size();
+    tma_launch_.grid = (int)std::min<long long>((long long)list.size(), (long long)per_sm * sms);
+    tma_launch_.error = d_tma_err_;
+    tma_launch_.stream = stream_;
+    tma_ = true;
+    return LBM_OK;
 }
 
 lbm_status Batch::rebuild()
@@ -411,6 +525,8 @@ lbm_status Batch::rebuild()
     // one step block per tile; the hardware block scheduler balances the tiles
     grid_ = std::max(1, nstiles_);
     aux_grid_ = std::max(1, std::min(sms * 8, (ntiles_ + 7) / 8));
+    lbm_status st = setup_tma();
+    if (st != LBM_OK) return st;
     dirty_ = false;
     return LBM_OK;
 }
@@ -445,6 +561,7 @@ struct StepQueue {
     Launch L;
     const InstanceDev *one;  // single instance: its parameters by value; else NULL
     int wx;                  // some instance uses an interpolated wall rule
+    const TmaLaunch *tma;    // non-reducing steps on the TMA brick kernel; else NULL
     int collision, layout;
     unsigned *status;
     int n_status;
@@ -466,7 +583,14 @@ static cudaError_t queue_steps(const StepQueue &q, cudaStream_t s, long long n, 
             if (e != cudaSuccess) return e;
         }
         const int kind = q.layout == LBM_LAYOUT_AB ? KIND_AB : (aa == 0 ? KIND_AA_PULL : KIND_AA_LOCAL);
-        cudaError_t e = q.ops->step(q.collision, kind, L, flip, red ? 1 : 0, q.status, q.one, q.wx);
+        cudaError_t e;
+        if (!red && q.tma) {  // the reducing step always runs the tile kernel
+            TmaLaunch T = *q.tma;
+            T.stream = s;
+            e = q.ops->step_tma(q.collision, q.wx, T, *q.one, flip);
+        } else {
+            e = q.ops->step(q.collision, kind, L, flip, red ? 1 : 0, q.status, q.one, q.wx);
+        }
         if (e != cudaSuccess) return e;
         ++launches;
         if (q.layout == LBM_LAYOUT_AB) flip ^= 1;
@@ -491,8 +615,8 @@ lbm_status Batch::step(long long n)
     int wx = 0;
     for (auto &p : inst_) wx |= p->desc.wall >= LBM_LIBB;
     StepQueue q{&ops(), Launch{d_table_, d_stiles_, nstiles_, kTileSegs, grid_, kStepWarps * 32, stream_},
-                size() == 1 ? &h_table_[0] : nullptr, wx, collision_, layout_, d_status_,
-                size(), d_stile_begin_, d_stile_count_, d_sums_, size()};
+                size() == 1 ? &h_table_[0] : nullptr, wx, tma_ ? &tma_launch_ : nullptr, collision_, layout_,
+                d_status_, size(), d_stile_begin_, d_stile_count_, d_sums_, size()};
     const long long kChunk = 1000;
     long long left = n;
     while (left > 0) {
@@ -541,7 +665,10 @@ lbm_status Batch::fetch_sums()
     if (n == 0) return LBM_OK;
     CK(cudaMemcpyAsync(h_sums_, d_sums_, sizeof(double) * kRedSlots * n, cudaMemcpyDeviceToHost, stream_));
     CK(cudaMemcpyAsync(h_status_, d_status_, sizeof(unsigned) * n, cudaMemcpyDeviceToHost, stream_));
+    unsigned tma_err = 0;
+    if (tma_) CK(cudaMemcpyAsync(&tma_err, d_tma_err_, sizeof(unsigned), cudaMemcpyDeviceToHost, stream_));
     CK(cudaStreamSynchronize(stream_));
+    if (tma_err) return fail(LBM_ERR_TIMEOUT, "a TMA brick copy did not complete within its wait limit");
     for (int i = 0; i < n; ++i) {
         Instance &in = *inst_[i];
         for (int d = 0; d < kRedSlots; ++d) in.sums[d] = h_sums_[kRedSlots * i + d];
@@ -717,7 +844,7 @@ void Batch::fill_info(int i, lbm_info *out) const
         out->wall = in.desc.wall;
     }
     out->kernel_launches = launches_;
-    out->block_cells = block_;
+    out->block_cells = block_cells();
     out->storage = storage_;
     out->layout = layout_;
     out->collision = collision_;

@@ -64,11 +64,12 @@ public:
     lbm_status sync();
     void fill_info(int i, lbm_info *out) const;
     long long launches() const { return launches_; }
-    int block_cells() const { return block_; }
+    int block_cells() const { return tma_ ? kBrickCells : 32 * kTileSegs; }
     int aa_phase() const { return aa_phase_; }
     cudaStream_t stream() const { return stream_; }
     long long fluid_cells() const;
     lbm_status set_block(int block_cells);
+    lbm_status prepare();              // upload tables and choose the step kernel now if pending
 
 private:
     lbm_status rebuild();          // upload table and tiles, drop graphs
@@ -92,7 +93,14 @@ private:
     unsigned *h_status_ = nullptr;    // pinned [n]
     int capacity_ = 0;
     int ntiles_ = 0;
-    int block_ = 32 * kTileSegs;      // cells per tile (one step block)
+    int block_ = 32 * kTileSegs;      // cells per chunk of the state kernels
+    int step_mode_ = 0;               // 0 (default) and 1: tiles of fluid cells; 2: TMA bricks
+    // TMA brick kernel (single instance, A-B layout, box a multiple of the brick)
+    bool tma_ = false;
+    TmaLaunch tma_launch_{};
+    uint32_t *d_bricks_ = nullptr;
+    unsigned *d_tma_err_ = nullptr;
+    lbm_status setup_tma();           // decides tma_ and builds maps and brick list
     int grid_ = 0;                    // step-kernel blocks (one per step tile)
     int aux_grid_ = 1;
     int flip_ = 0;

@@ -93,8 +93,11 @@ lbm_status create_batch(Batch &b, const lbm_desc *descs, int n, cudaStream_t s)
         st = b.add(std::move(in));
         if (st != LBM_OK) return st;
     }
-    if (block) return b.set_block(block);
-    return LBM_OK;
+    if (block) {
+        st = b.set_block(block);
+        if (st != LBM_OK) return st;
+    }
+    return b.prepare();  // tables and the step kernel chosen now: errors surface at create
 }
 
 }  // namespace
@@ -350,6 +353,8 @@ lbm_status lbm_get_wall_distances(lbm_ctx *ctx, double *host_out)
 lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *out)
 {
     if (!ctx || !out) return fail(LBM_ERR_ARG, "NULL argument");
+    lbm_status st = ctx->b.prepare();
+    if (st != LBM_OK) return st;
     ctx->b.fill_info(0, out);
     return LBM_OK;
 }
@@ -453,6 +458,8 @@ lbm_status lbm_batch_set_populations_f64(lbm_batch *b, int32_t i, const double *
 lbm_status lbm_batch_get_info(lbm_batch *b, lbm_info *out)
 {
     if (!b || !out) return fail(LBM_ERR_ARG, "NULL argument");
+    lbm_status st = b->b.prepare();
+    if (st != LBM_OK) return st;
     b->b.fill_info(-1, out);
     return LBM_OK;
 }

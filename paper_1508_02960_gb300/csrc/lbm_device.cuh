@@ -280,6 +280,12 @@ struct TileDev {
 
 enum { KIND_AB = 0, KIND_AA_PULL = 1, KIND_AA_LOCAL = 2 };
 
+// TMA brick kernel (lbm_tma.cuh): bricks of kBrickX x kBrickY x kBrickZ cells, one thread
+// per cell, kBrickStages shared-memory stages per block.
+constexpr int kBrickX = 32, kBrickY = 2, kBrickZ = 4;
+constexpr int kBrickCells = kBrickX * kBrickY * kBrickZ;
+constexpr int kBrickStages = 2;
+
 // Step-kernel tiling: a tile is kStepWarps consecutive work items (32 fluid cells each),
 // one per warp of a kStepWarps-warp block.
 constexpr int kStepWarps = 4;

@@ -8,6 +8,7 @@
 #include "lbm_aux.cuh"
 #include "lbm_internal.h"
 #include "lbm_step.cuh"
+#include "lbm_tma.cuh"
 
 namespace lbm {
 namespace detail {
@@ -79,6 +80,67 @@ cudaError_t step(int coll, int kind, const Launch &L, int flip, int reduce, unsi
     case COLL_MRT * 3 + KIND_AA_PULL: return step_one<STORE, COLL_MRT, KIND_AA_PULL>(L, flip, reduce, status, one, wx);
     case COLL_MRT * 3 + KIND_AA_LOCAL: return step_one<STORE, COLL_MRT, KIND_AA_LOCAL>(L, flip, reduce, status, one, wx);
     default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int STORE, int COLL, bool WX> auto tma_kernel() { return step_kernel_tma<COLL, STORE, WX>; }
+
+template <int STORE, int COLL, bool WX>
+cudaError_t step_tma_one(const TmaLaunch &T, const InstanceDev &one, int flip)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)T.grid);
+    cfg.blockDim = dim3((unsigned)kBrickCells);
+    cfg.dynamicSmemBytes = BrickStage<STORE>::SMEM_BYTES;
+    cfg.stream = T.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, tma_kernel<STORE, COLL, WX>(), one, T.map[0][0], T.map[0][1],
+                                       T.map[1][0], T.map[1][1], T.bricks, T.nbricks, flip, T.error);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+template <int STORE>
+cudaError_t step_tma(int coll, int wx, const TmaLaunch &T, const InstanceDev &one, int flip)
+{
+    switch (coll * 2 + (wx ? 1 : 0)) {
+    case COLL_SRT * 2: return step_tma_one<STORE, COLL_SRT, false>(T, one, flip);
+    case COLL_SRT * 2 + 1: return step_tma_one<STORE, COLL_SRT, true>(T, one, flip);
+    case COLL_TRT * 2: return step_tma_one<STORE, COLL_TRT, false>(T, one, flip);
+    case COLL_TRT * 2 + 1: return step_tma_one<STORE, COLL_TRT, true>(T, one, flip);
+    case COLL_MRT * 2: return step_tma_one<STORE, COLL_MRT, false>(T, one, flip);
+    case COLL_MRT * 2 + 1: return step_tma_one<STORE, COLL_MRT, true>(T, one, flip);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int STORE, int COLL, bool WX> int tma_prepare_one()
+{
+    const int smem = BrickStage<STORE>::SMEM_BYTES;
+    if (cudaFuncSetAttribute(tma_kernel<STORE, COLL, WX>(), cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tma_kernel<STORE, COLL, WX>(), kBrickCells, smem) !=
+        cudaSuccess)
+        return 0;
+    return nb;
+}
+
+template <int STORE> int tma_prepare(int coll, int wx)
+{
+    switch (coll * 2 + (wx ? 1 : 0)) {
+    case COLL_SRT * 2: return tma_prepare_one<STORE, COLL_SRT, false>();
+    case COLL_SRT * 2 + 1: return tma_prepare_one<STORE, COLL_SRT, true>();
+    case COLL_TRT * 2: return tma_prepare_one<STORE, COLL_TRT, false>();
+    case COLL_TRT * 2 + 1: return tma_prepare_one<STORE, COLL_TRT, true>();
+    case COLL_MRT * 2: return tma_prepare_one<STORE, COLL_MRT, false>();
+    case COLL_MRT * 2 + 1: return tma_prepare_one<STORE, COLL_MRT, true>();
+    default: return 0;
     }
 }
 
@@ -158,6 +220,8 @@ FormatOps make_ops()
     o.export_dir = &export_dir<STORE>;
     o.moments = &moments<STORE>;
     o.wall_prepare = &wall_prepare<STORE>;
+    o.step_tma = &step_tma<STORE>;
+    o.tma_prepare = &tma_prepare<STORE>;
     o.step_kernel_ptr = &step_ptr<STORE>;
     return o;
 }

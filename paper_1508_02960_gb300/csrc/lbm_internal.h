@@ -1,6 +1,7 @@
 // lbm_internal.h -- host-side declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -23,6 +24,18 @@ struct Launch {
     cudaStream_t stream;
 };
 
+// Arguments of one launch of the TMA brick kernel (single instance, A-B layout): tensor
+// maps of the two population buffers (box widths kBrickX and kBrickX + 16 bytes), the
+// device list of bricks holding fluid, and an error word for bounded waits that ran out.
+struct TmaLaunch {
+    CUtensorMap map[2][2];  // [buffer f0 / f1][box narrow / wide]
+    const uint32_t *bricks;
+    int nbricks;
+    int grid;
+    unsigned *error;
+    cudaStream_t stream;
+};
+
 // Per-storage-format kernel entry points (one translation unit per format).
 struct FormatOps {
     // one: host copy of the only instance's parameters (passed by value), or NULL for a batch;
@@ -37,6 +50,11 @@ struct FormatOps {
                               int aa_phase, int k, double *fk, cudaStream_t s);
     cudaError_t (*moments)(const Launch &L, int layout, int cur, int aa_phase, int mode, int comp,
                            double *out);
+    // TMA brick step (non-reducing, single instance, A-B); one: the instance's parameters
+    cudaError_t (*step_tma)(int coll, int wx, const TmaLaunch &T, const InstanceDev &one, int flip);
+    // once per kernel, before any launch or capture: opt in to its shared memory; returns
+    // the blocks per multiprocessor it can hold (0 on error)
+    int (*tma_prepare)(int coll, int wx);
     // A-B layout: wall terms of the stored state into the solid slots (wall_prepare_kernel)
     cudaError_t (*wall_prepare)(const InstanceDev *table, int inst, long long n_boundary, const long long *bcell,
                                 int cur, cudaStream_t s);

@@ -57,7 +57,8 @@ typedef enum {
     LBM_ERR_NOT_CONVERGED = -5, /* max_steps reached before the convergence test passed */
     LBM_ERR_TIMEOUT = -6,       /* a bounded wait ran out */
     LBM_ERR_STATE = -7,         /* call not valid in the object's current state */
-    LBM_ERR_IO = -8             /* checkpoint file could not be read or written */
+    LBM_ERR_IO = -8,            /* checkpoint file could not be read or written */
+    LBM_ERR_CANCELLED = -9      /* a served request was cancelled (lbm_server_cancel) */
 } lbm_status;
 
 /* Collision operator (Sec. 2.1). */
@@ -239,6 +240,13 @@ LBM_API lbm_status lbm_fit_barree_conway(const double *re, const double *kstar, 
  * filled) when the last reduction saw a diverged cell. */
 LBM_API lbm_status lbm_observables(lbm_ctx *ctx, double K_darcy, lbm_obs *out);
 
+/* Host-side fault injection for tests (there is no device-side fault injection): after
+ * the next n device allocations made by the library succeed, the following ones fail as if
+ * the device were out of memory (cudaErrorMemoryAllocation), so that every out-of-memory
+ * path can be exercised without touching the GPU's state.  n < 0 (the default) disables it.
+ * Process-wide; not for production use. */
+LBM_API void lbm_debug_fail_alloc_after(int64_t n);
+
 /* FP64 sums over fluid cells of (rho - rho0, u_x, u_y, u_z), computed now from the
  * stored post-collision populations (synchronises).  sums: host array of 4. */
 LBM_API lbm_status lbm_moment_sums(lbm_ctx *ctx, double *sums);
@@ -317,7 +325,7 @@ typedef struct {
 } lbm_server_opts;
 
 typedef struct {
-    int64_t submitted, completed, failed, resident, queued;
+    int64_t submitted, completed, failed, resident, queued, cancelled;
     double fluid_updates;    /* total fluid-cell updates performed */
     double busy_seconds;     /* wall time with at least one resident point */
     double mlups;            /* fluid_updates / busy_seconds / 1e6 */
@@ -336,6 +344,10 @@ LBM_API lbm_status lbm_server_submit(lbm_server *s, const lbm_desc *desc, double
 LBM_API lbm_status lbm_server_poll(lbm_server *s, int64_t req_id, lbm_obs *out, double *latency_s);
 /* Block until every submitted request has finished (bounded by timeout_s; <= 0: none). */
 LBM_API lbm_status lbm_server_drain(lbm_server *s, double timeout_s);
+/* Cancel a request: a queued one is dropped at once, a resident one is retired at the next
+ * chunk boundary; its poll then returns LBM_ERR_CANCELLED (with the observables of its
+ * last chunk when it was resident).  LBM_ERR_STATE if it has already finished. */
+LBM_API lbm_status lbm_server_cancel(lbm_server *s, int64_t req_id);
 LBM_API lbm_status lbm_server_get_stats(lbm_server *s, lbm_server_stats *out);
 LBM_API void lbm_server_destroy(lbm_server *s);
 

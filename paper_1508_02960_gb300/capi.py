@@ -27,9 +27,9 @@ DEV_SCALE_AUTO = -1000
 
 STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_NO_MEMORY", -3: "LBM_ERR_CUDA",
           -4: "LBM_ERR_DIVERGED", -5: "LBM_ERR_NOT_CONVERGED", -6: "LBM_ERR_TIMEOUT",
-          -7: "LBM_ERR_STATE", -8: "LBM_ERR_IO"}
+          -7: "LBM_ERR_STATE", -8: "LBM_ERR_IO", -9: "LBM_ERR_CANCELLED"}
 OK, ERR_ARG, ERR_NO_MEMORY, ERR_CUDA, ERR_DIVERGED, ERR_NOT_CONVERGED, ERR_TIMEOUT, \
-    ERR_STATE, ERR_IO = 0, -1, -2, -3, -4, -5, -6, -7, -8
+    ERR_STATE, ERR_IO, ERR_CANCELLED = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 
 STORAGE_BYTES = {F64: 8, F32: 4, F16DEV: 2, BF16DEV: 2}
 
@@ -108,7 +108,8 @@ class ServerOpts(ctypes.Structure):
 
 
 class ServerStats(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "resident", "queued")] + \
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "resident", "queued",
+                                              "cancelled")] + \
                [(n, ctypes.c_double) for n in ("fluid_updates", "busy_seconds", "mlups")] + \
                [("kernel_launches", ctypes.c_int64)]
 
@@ -163,6 +164,8 @@ PROTOTYPES = {
     "lbm_server_poll": (_st, [_vp, ctypes.c_int64, ctypes.POINTER(Obs), _dp]),
     "lbm_server_drain": (_st, [_vp, ctypes.c_double]),
     "lbm_server_get_stats": (_st, [_vp, ctypes.POINTER(ServerStats)]),
+    "lbm_server_cancel": (_st, [_vp, ctypes.c_int64]),
+    "lbm_debug_fail_alloc_after": (None, [ctypes.c_int64]),
     "lbm_server_destroy": (None, [_vp]),
 }
 
@@ -465,6 +468,14 @@ class Server:
     def drain(self, timeout_s: float = 0.0):
         check(lib().lbm_server_drain(self._h, float(timeout_s)), "lbm_server_drain")
 
+    def cancel(self, rid: int) -> int:
+        """Cancel a request (lbm_server_cancel); returns the status (OK, or ERR_STATE if it
+        had already finished)."""
+        st = lib().lbm_server_cancel(self._h, int(rid))
+        if st not in (OK, ERR_STATE):
+            check(st, "lbm_server_cancel")
+        return st
+
     def stats(self) -> dict:
         s = ServerStats()
         check(lib().lbm_server_get_stats(self._h, ctypes.byref(s)), "lbm_server_get_stats")
@@ -489,6 +500,12 @@ def moment_sums_f64_noalloc(f_dev_ptr: int, solid_dev_ptr: int | None, n_cells: 
     tensor.data_ptr()).  Queued on the stream; does not wait."""
     check(lib().lbm_moment_sums_f64_noalloc(f_dev_ptr, solid_dev_ptr, int(n_cells), float(rho0), sums_dev_ptr,
                                             _stream_handle(stream)), "lbm_moment_sums_f64_noalloc")
+
+
+def debug_fail_alloc_after(n: int):
+    """Host-side fault injection (lbm_debug_fail_alloc_after): device allocations after the
+    next n fail as out of memory; n < 0 disables."""
+    lib().lbm_debug_fail_alloc_after(int(n))
 
 
 def fit_barree_conway(re, kstar, init=None):

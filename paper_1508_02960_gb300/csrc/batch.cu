@@ -122,6 +122,7 @@ size_t Batch::footprint(const lbm_desc &d)
 
 lbm_status Batch::make_instance(const lbm_desc &d0, cudaStream_t s, std::unique_ptr<Instance> *out)
 {
+    TraceRange trace("lbm.make_instance");
     lbm_status st = validate_desc(d0);
     if (st != LBM_OK) return st;
     std::unique_ptr<Instance> in(new Instance());
@@ -174,21 +175,21 @@ lbm_status Batch::make_instance(const lbm_desc &d0, cudaStream_t s, std::unique_
         free_geometry(&in->geo);
         return cuda_fail(ce, what);
     };
-    if ((e = cudaMalloc(&in->f0, pop)) != cudaSuccess) return cleanup(e, "cudaMalloc(populations)");
+    if ((e = dev_alloc(&in->f0, pop)) != cudaSuccess) return cleanup(e, "dev_alloc(populations)");
     if ((e = cudaMemsetAsync(in->f0, 0, pop, s)) != cudaSuccess) return cleanup(e, "cudaMemset");
     if (d.layout == LBM_LAYOUT_AB) {
-        if ((e = cudaMalloc(&in->f1, pop)) != cudaSuccess) return cleanup(e, "cudaMalloc(populations)");
+        if ((e = dev_alloc(&in->f1, pop)) != cudaSuccess) return cleanup(e, "dev_alloc(populations)");
         if ((e = cudaMemsetAsync(in->f1, 0, pop, s)) != cudaSuccess) return cleanup(e, "cudaMemset");
     }
     if (d.layout == LBM_LAYOUT_AA && d.wall == LBM_CLI && in->geo.n_links > 0) {
-        if ((e = cudaMalloc(&in->linkB, es * in->geo.n_links)) != cudaSuccess) return cleanup(e, "cudaMalloc(linkB)");
+        if ((e = dev_alloc(&in->linkB, es * in->geo.n_links)) != cudaSuccess) return cleanup(e, "dev_alloc(linkB)");
         if ((e = cudaMemsetAsync(in->linkB, 0, es * in->geo.n_links, s)) != cudaSuccess)
             return cleanup(e, "cudaMemset");
     }
     // partial sums: one row of kRedSlots doubles per work chunk at the smallest chunk size
     in->partial_capacity = std::max(1ll, (in->geo.n_active + kMinChunkSegs - 1) / kMinChunkSegs);
-    if ((e = cudaMalloc(&in->partials, sizeof(double) * kRedSlots * in->partial_capacity)) != cudaSuccess)
-        return cleanup(e, "cudaMalloc(partials)");
+    if ((e = dev_alloc(&in->partials, sizeof(double) * kRedSlots * in->partial_capacity)) != cudaSuccess)
+        return cleanup(e, "dev_alloc(partials)");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cleanup(e, "cudaStreamSynchronize");
     in->bytes_pop = pop * (d.layout == LBM_LAYOUT_AB ? 2 : 1);
     *out = std::move(in);
@@ -408,10 +409,10 @@ lbm_status Batch::setup_tma()
                 if (fluid) list.push_back((uint32_t)bx | (uint32_t)by << 10 | (uint32_t)bz << 21);
             }
     if (list.empty()) return not_here("no fluid");
-    CK(cudaMalloc(&d_bricks_, sizeof(uint32_t) * list.size()));
+    CK(dev_alloc(&d_bricks_, sizeof(uint32_t) * list.size()));
     CK(cudaMemcpy(d_bricks_, list.data(), sizeof(uint32_t) * list.size(), cudaMemcpyHostToDevice));
     if (!d_tma_err_) {
-        CK(cudaMalloc(&d_tma_err_, sizeof(unsigned)));
+        CK(dev_alloc(&d_tma_err_, sizeof(unsigned)));
         CK(cudaMemset(d_tma_err_, 0, sizeof(unsigned)));
     }
     // tensor maps [nz][ny][nx] x 19 directions of both buffers, boxes kBrickX and kBrickX + 16 B wide
@@ -488,22 +489,22 @@ lbm_status Batch::rebuild()
     d_tiles_ = d_stiles_ = nullptr;
     d_tile_begin_ = d_tile_count_ = d_stile_begin_ = d_stile_count_ = nullptr;
     h_table_ = table;
-    CK(cudaMalloc(&d_table_, sizeof(InstanceDev) * table.size()));
+    CK(dev_alloc(&d_table_, sizeof(InstanceDev) * table.size()));
     CK(cudaMemcpy(d_table_, table.data(), sizeof(InstanceDev) * table.size(), cudaMemcpyHostToDevice));
     if (ntiles_ > 0) {
-        CK(cudaMalloc(&d_tiles_, sizeof(TileDev) * tiles.size()));
+        CK(dev_alloc(&d_tiles_, sizeof(TileDev) * tiles.size()));
         CK(cudaMemcpy(d_tiles_, tiles.data(), sizeof(TileDev) * tiles.size(), cudaMemcpyHostToDevice));
     }
-    CK(cudaMalloc(&d_tile_begin_, sizeof(int) * tb.size()));
-    CK(cudaMalloc(&d_tile_count_, sizeof(int) * tc.size()));
+    CK(dev_alloc(&d_tile_begin_, sizeof(int) * tb.size()));
+    CK(dev_alloc(&d_tile_count_, sizeof(int) * tc.size()));
     CK(cudaMemcpy(d_tile_begin_, tb.data(), sizeof(int) * tb.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_tile_count_, tc.data(), sizeof(int) * tc.size(), cudaMemcpyHostToDevice));
     if (nstiles_ > 0) {
-        CK(cudaMalloc(&d_stiles_, sizeof(TileDev) * stiles.size()));
+        CK(dev_alloc(&d_stiles_, sizeof(TileDev) * stiles.size()));
         CK(cudaMemcpy(d_stiles_, stiles.data(), sizeof(TileDev) * stiles.size(), cudaMemcpyHostToDevice));
     }
-    CK(cudaMalloc(&d_stile_begin_, sizeof(int) * sb.size()));
-    CK(cudaMalloc(&d_stile_count_, sizeof(int) * sc.size()));
+    CK(dev_alloc(&d_stile_begin_, sizeof(int) * sb.size()));
+    CK(dev_alloc(&d_stile_count_, sizeof(int) * sc.size()));
     CK(cudaMemcpy(d_stile_begin_, sb.data(), sizeof(int) * sb.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_stile_count_, sc.data(), sizeof(int) * sc.size(), cudaMemcpyHostToDevice));
     if (n > capacity_) {
@@ -516,8 +517,8 @@ lbm_status Batch::rebuild()
         h_sums_ = nullptr;
         h_status_ = nullptr;
         capacity_ = std::max(n, 2 * capacity_);
-        CK(cudaMalloc(&d_sums_, sizeof(double) * kRedSlots * capacity_));
-        CK(cudaMalloc(&d_status_, sizeof(unsigned) * capacity_));
+        CK(dev_alloc(&d_sums_, sizeof(double) * kRedSlots * capacity_));
+        CK(dev_alloc(&d_status_, sizeof(unsigned) * capacity_));
         CK(cudaMemset(d_status_, 0, sizeof(unsigned) * capacity_));
         CK(cudaMallocHost(&h_sums_, sizeof(double) * kRedSlots * capacity_));
         CK(cudaMallocHost(&h_status_, sizeof(unsigned) * capacity_));
@@ -606,6 +607,7 @@ static cudaError_t queue_steps(const StepQueue &q, cudaStream_t s, long long n, 
 
 lbm_status Batch::step(long long n)
 {
+    TraceRange trace("lbm.step");
     if (n < 0) return fail(LBM_ERR_ARG, "n_steps < 0");
     if (n == 0 || size() == 0) return LBM_OK;
     if (dirty_) {
@@ -715,7 +717,7 @@ static cudaError_t ensure_stage(double **buf, long long *cap, long long n)
     cudaFree(*buf);
     *buf = nullptr;
     *cap = 0;
-    cudaError_t e = cudaMalloc(buf, sizeof(double) * n);
+    cudaError_t e = dev_alloc(buf, sizeof(double) * n);
     if (e == cudaSuccess) *cap = n;
     return e;
 }

@@ -223,6 +223,7 @@ lbm_status lbm_average(lbm_ctx *ctx, int64_t n_samples, int64_t sample_interval,
 
 lbm_status lbm_run_developed(lbm_ctx *ctx, const lbm_develop_opts *o, double K_darcy, lbm_develop_result *out)
 {
+    TraceRange trace("lbm.run_developed");
     if (!ctx || !o || !out) return fail(LBM_ERR_ARG, "NULL argument");
     if (o->samples_per_ft < 1 || !(o->min_spinup_ft >= 0) || !(o->max_spinup_ft >= o->min_spinup_ft) ||
         !(o->average_ft > 0) || !(o->drag_tol > 0) || o->max_steps < 1)

@@ -417,12 +417,12 @@ cudaError_t exclusive_scan(const unsigned long long *in, unsigned long long *out
     if (n <= 0) return cudaSuccess;
     const long long nb = (n + 1023) / 1024;
     unsigned long long *bsum = nullptr, *bscan = nullptr;
-    cudaError_t e = cudaMalloc(&bsum, sizeof(unsigned long long) * nb);
+    cudaError_t e = dev_alloc(&bsum, sizeof(unsigned long long) * nb);
     if (e != cudaSuccess) return e;
     scan_block_kernel<<<(unsigned)nb, 1024, 0, s>>>(in, out, bsum, n);
     e = cudaGetLastError();
     if (e == cudaSuccess && nb > 1) {
-        e = cudaMalloc(&bscan, sizeof(unsigned long long) * nb);
+        e = dev_alloc(&bscan, sizeof(unsigned long long) * nb);
         if (e == cudaSuccess) e = exclusive_scan(bsum, bscan, nb, s);
         if (e == cudaSuccess) {
             scan_add_kernel<<<(unsigned)nb, 1024, 0, s>>>(out, bscan, n);
@@ -487,16 +487,16 @@ cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_
     g->nseg = (n + 31) / 32;
     g->nseg_padded = (g->nseg + kMaxWarpsPerBlock - 1) / kMaxWarpsPerBlock * kMaxWarpsPerBlock;
 
-    GEO_CHECK(cudaMalloc(&g->solid, n));
-    GEO_CHECK(cudaMalloc(&g->seg, sizeof(uint4) * g->nseg_padded));
-    GEO_CHECK(cudaMalloc(&d_wm, sizeof(uint32_t) * n));
-    GEO_CHECK(cudaMalloc(&d_cnt, sizeof(unsigned long long) * g->nseg_padded));
-    GEO_CHECK(cudaMalloc(&d_base, sizeof(unsigned long long) * g->nseg_padded));
-    GEO_CHECK(cudaMalloc(&d_ctr, sizeof(unsigned long long) * 2));
+    GEO_CHECK(dev_alloc(&g->solid, n));
+    GEO_CHECK(dev_alloc(&g->seg, sizeof(uint4) * g->nseg_padded));
+    GEO_CHECK(dev_alloc(&d_wm, sizeof(uint32_t) * n));
+    GEO_CHECK(dev_alloc(&d_cnt, sizeof(unsigned long long) * g->nseg_padded));
+    GEO_CHECK(dev_alloc(&d_base, sizeof(unsigned long long) * g->nseg_padded));
+    GEO_CHECK(dev_alloc(&d_ctr, sizeof(unsigned long long) * 2));
     GEO_CHECK(cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long) * 2, s));
 
     if (spheres && n_spheres > 0) {
-        GEO_CHECK(cudaMalloc(&d_sph, sizeof(double4) * n_spheres));
+        GEO_CHECK(dev_alloc(&d_sph, sizeof(double4) * n_spheres));
         GEO_CHECK(cudaMemcpyAsync(d_sph, spheres, sizeof(double4) * n_spheres, cudaMemcpyHostToDevice, s));
         voxelize_kernel<<<grid_for(n, 256), 256, 0, s>>>(nx, ny, nz, d_sph, n_spheres, g->solid);
         GEO_CHECK(cudaGetLastError());
@@ -531,7 +531,7 @@ cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_
     g->n_active = (long long)(h_last[0] + h_last[1]);
     g->n_active_padded = std::max<long long>(kMaxWarpsPerBlock,
         (g->n_active + kMaxWarpsPerBlock - 1) / kMaxWarpsPerBlock * kMaxWarpsPerBlock);
-    GEO_CHECK(cudaMalloc(&g->aseg, sizeof(uint4) * g->n_active_padded));
+    GEO_CHECK(dev_alloc(&g->aseg, sizeof(uint4) * g->n_active_padded));
     active_scatter_kernel<<<grid_for(g->nseg_padded, 256), 256, 0, s>>>(g->nseg_padded, g->n_active_padded, g->seg,
                                                                          d_cnt, d_base, g->aseg, g->n_active);
     GEO_CHECK(cudaGetLastError());
@@ -549,8 +549,8 @@ cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_
         g->n_fwarps_padded = std::max<long long>(kMaxWarpsPerBlock,
             (g->n_fwarps + kMaxWarpsPerBlock - 1) / kMaxWarpsPerBlock * kMaxWarpsPerBlock);
     }
-    GEO_CHECK(cudaMalloc(&g->fcell, sizeof(uint32_t) * 32 * g->n_fwarps_padded));
-    GEO_CHECK(cudaMalloc(&g->fwarp, sizeof(uint2) * g->n_fwarps_padded));
+    GEO_CHECK(dev_alloc(&g->fcell, sizeof(uint32_t) * 32 * g->n_fwarps_padded));
+    GEO_CHECK(dev_alloc(&g->fwarp, sizeof(uint2) * g->n_fwarps_padded));
     GEO_CHECK(cudaMemsetAsync(g->fcell, 0xFF, sizeof(uint32_t) * 32 * g->n_fwarps_padded, s));
     fluid_scatter_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, g->seg, d_base, g->fcell);
     GEO_CHECK(cudaGetLastError());
@@ -560,11 +560,11 @@ cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_
 
     if (g->n_boundary > 0) {
         const long long nb = g->n_boundary;
-        GEO_CHECK(cudaMalloc(&g->bmask, sizeof(uint32_t) * nb));
-        GEO_CHECK(cudaMalloc(&g->boff, sizeof(uint32_t) * nb));
-        GEO_CHECK(cudaMalloc(&g->bcell, sizeof(long long) * nb));
-        GEO_CHECK(cudaMalloc(&d_nl, sizeof(unsigned long long) * nb));
-        GEO_CHECK(cudaMalloc(&d_lbase, sizeof(unsigned long long) * nb));
+        GEO_CHECK(dev_alloc(&g->bmask, sizeof(uint32_t) * nb));
+        GEO_CHECK(dev_alloc(&g->boff, sizeof(uint32_t) * nb));
+        GEO_CHECK(dev_alloc(&g->bcell, sizeof(long long) * nb));
+        GEO_CHECK(dev_alloc(&d_nl, sizeof(unsigned long long) * nb));
+        GEO_CHECK(dev_alloc(&d_lbase, sizeof(unsigned long long) * nb));
         boundary_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, g->seg, d_wm, g->bmask, g->bcell, d_nl);
         GEO_CHECK(cudaGetLastError());
         GEO_CHECK(exclusive_scan(d_nl, d_lbase, nb, s));
@@ -579,11 +579,11 @@ cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_
         to_u32_kernel<<<grid_for(nb, 256), 256, 0, s>>>(nb, d_lbase, g->boff);
         GEO_CHECK(cudaGetLastError());
         if (g->n_links > 0) {
-            GEO_CHECK(cudaMalloc(&g->linkq, sizeof(double) * g->n_links));
-            GEO_CHECK(cudaMalloc(&g->linkc, (c_double ? 8 : 4) * g->n_links));
-            if (wall >= 2) GEO_CHECK(cudaMalloc(&g->linkw, (c_double ? 8 : 4) * kLinkW * g->n_links));
+            GEO_CHECK(dev_alloc(&g->linkq, sizeof(double) * g->n_links));
+            GEO_CHECK(dev_alloc(&g->linkc, (c_double ? 8 : 4) * g->n_links));
+            if (wall >= 2) GEO_CHECK(dev_alloc(&g->linkw, (c_double ? 8 : 4) * kLinkW * g->n_links));
             if (q_host && !(spheres && n_spheres > 0)) {
-                GEO_CHECK(cudaMalloc(&d_q, sizeof(double) * Q * n));
+                GEO_CHECK(dev_alloc(&d_q, sizeof(double) * Q * n));
                 GEO_CHECK(cudaMemcpyAsync(d_q, q_host, sizeof(double) * Q * n, cudaMemcpyHostToDevice, s));
             }
             const double4 *sp = (spheres && n_spheres > 0) ? d_sph : nullptr;

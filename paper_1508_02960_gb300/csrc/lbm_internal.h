@@ -13,6 +13,20 @@
 
 namespace lbm {
 
+// Every device buffer the library owns is allocated here, so that the fault injection of
+// lbm_debug_fail_alloc_after reaches every out-of-memory path.
+cudaError_t dev_alloc(void **p, size_t bytes);
+template <typename T> cudaError_t dev_alloc(T **p, size_t bytes)
+{
+    return dev_alloc(reinterpret_cast<void **>(p), bytes);
+}
+
+// NVTX range for profilers (a no-op unless a tool is attached).
+struct TraceRange {
+    explicit TraceRange(const char *name);
+    ~TraceRange();
+};
+
 // Arguments of one launch over a tile list (each tile: up to chunk_segs consecutive
 // entries of one instance's active-segment list).
 struct Launch {

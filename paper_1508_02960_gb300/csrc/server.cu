@@ -32,6 +32,7 @@ struct Request {
     int64_t max_steps = 0;
     Clock::time_point t_submit, t_done;
     enum { QUEUED, RUNNING, DONE } state = QUEUED;
+    bool cancel = false;      // retire at the next chunk boundary
     lbm_status result = LBM_OK;
     lbm_obs obs{};
     size_t bytes = 0;
@@ -70,6 +71,7 @@ void lbm_server::finish(Request &r, lbm_status st, const Instance *in)
     r.t_done = Clock::now();
     used -= r.bytes;
     if (st == LBM_OK) ++stats.completed;
+    else if (st == LBM_ERR_CANCELLED) ++stats.cancelled;
     else ++stats.failed;
 }
 
@@ -127,6 +129,7 @@ void lbm_server::run()
             continue;
         }
         lk.unlock();
+        TraceRange trace("lbm.server.chunk");
         const auto t0 = Clock::now();
         double updates = 0.0;
         for (auto &kv : groups) {
@@ -149,7 +152,8 @@ void lbm_server::run()
                 Instance &in = b.at(i);
                 const double U = in.sums[1] / (double)in.geo.ncells;
                 lbm_status st = LBM_ERR_STATE;
-                if (in.status & STATUS_DIVERGED) st = LBM_ERR_DIVERGED;
+                if (r.cancel) st = LBM_ERR_CANCELLED;
+                else if (in.status & STATUS_DIVERGED) st = LBM_ERR_DIVERGED;
                 else if (r.have_U && std::fabs(U - r.U_old) < r.tol * std::fabs(U)) st = LBM_OK;
                 else if (in.steps >= r.max_steps) st = LBM_ERR_NOT_CONVERGED;
                 r.U_old = U;
@@ -234,7 +238,8 @@ lbm_status lbm_server_poll(lbm_server *s, int64_t req_id, lbm_obs *out, double *
     if (r.state != Request::DONE) return fail(LBM_ERR_STATE, "request still queued or running");
     if (out) *out = r.obs;
     if (latency_s) *latency_s = std::chrono::duration<double>(r.t_done - r.t_submit).count();
-    if (r.result != LBM_OK) set_error("request finished without converging");
+    if (r.result == LBM_ERR_CANCELLED) set_error("request cancelled");
+    else if (r.result != LBM_OK) set_error("request finished without converging");
     return r.result;
 }
 
@@ -253,6 +258,31 @@ lbm_status lbm_server_drain(lbm_server *s, double timeout_s)
     } else {
         s->cv_done.wait(lk, all_done);
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_server_cancel(lbm_server *s, int64_t req_id)
+{
+    if (!s) return fail(LBM_ERR_ARG, "server is NULL");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(req_id);
+    if (it == s->reqs.end()) return fail(LBM_ERR_ARG, "unknown request id");
+    Request &r = it->second;
+    if (r.state == Request::DONE) return fail(LBM_ERR_STATE, "request already finished");
+    if (r.state == Request::QUEUED) {  // never admitted: holds no memory
+        for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+            if (*q == req_id) {
+                s->queue.erase(q);
+                break;
+            }
+        r.result = LBM_ERR_CANCELLED;
+        r.state = Request::DONE;
+        r.t_done = Clock::now();
+        ++s->stats.cancelled;
+        s->cv_done.notify_all();
+        return LBM_OK;
+    }
+    r.cancel = true;  // resident: the worker retires it after the current chunk
     return LBM_OK;
 }
 

@@ -58,7 +58,8 @@ typedef enum {
     LBM_ERR_TIMEOUT = -6,       /* a bounded wait ran out */
     LBM_ERR_STATE = -7,         /* call not valid in the object's current state */
     LBM_ERR_IO = -8,            /* checkpoint file could not be read or written */
-    LBM_ERR_CANCELLED = -9      /* a served request was cancelled (lbm_server_cancel) */
+    LBM_ERR_CANCELLED = -9,     /* a served request was cancelled (lbm_server_cancel) */
+    LBM_ERR_BOUNDS = -10        /* checked build: a kernel met an index outside its arrays */
 } lbm_status;
 
 /* Collision operator (Sec. 2.1). */
@@ -79,6 +80,7 @@ enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16DEV = 2, LBM_BF16DEV = 3 };
 enum { LBM_LAYOUT_AB = 0, LBM_LAYOUT_AA = 1 };
 
 #define LBM_DEV_SCALE_AUTO (-1000)
+#define LBM_BLOCK_AUTO (-1)
 
 typedef struct {
     double cx, cy, cz, r; /* centre and radius in lattice units */
@@ -107,7 +109,9 @@ typedef struct {
     int32_t dev_scale_log2;     /* FP16DEV scale exponent; LBM_DEV_SCALE_AUTO = from delta_rho */
     int32_t block_cells;        /* step kernel: 0 or 128 = tiles of 128 fluid cells (default);
                                    256 = bricks of 32 x 2 x 4 cells staged by TMA (single A-B
-                                   instance; nx, ny, nz multiples of 32, 2, 4) */
+                                   instance; nx, ny, nz multiples of 32, 2, 4);
+                                   LBM_BLOCK_AUTO = the faster of the two, measured at
+                                   creation (see lbm_create) */
     double d_p;                 /* particle diameter of Re_p; 0 = volume-mean sphere diameter */
     double perturb_u;           /* lbm_init_equilibrium: amplitude of a seeded random initial
                                    velocity (0 = fluid at rest) */
@@ -148,6 +152,11 @@ typedef struct {
     int64_t kernel_launches;   /* library kernels launched so far (graph nodes counted) */
     int32_t block_cells, storage, layout, collision, wall, dev_scale_log2;
     int64_t steps;
+    int32_t autotune;          /* how block_cells was chosen: 0 given, 1 measured at creation,
+                                  2 taken from the autotuner cache */
+    int32_t pad_;
+    double tune_ms_tiles;      /* autotuner: ms per step of the tile kernel (0 = not timed) */
+    double tune_ms_bricks;     /* autotuner: ms per step of the brick kernel (0 = not timed) */
 } lbm_info;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -164,7 +173,13 @@ LBM_API const char *lbm_version(void);
  * for every cut link, the wall distance q of Sec. 2.2.1 (computed once, as in Sec. 3),
  * and allocates the populations.  The populations are left uninitialised: call
  * lbm_init_equilibrium or lbm_set_populations_f64 next.  cuda_stream: a cudaStream_t
- * or NULL.  On failure *out is NULL. */
+ * or NULL.  On failure *out is NULL.
+ * With desc.block_cells = LBM_BLOCK_AUTO the step kernel is chosen by measurement. The
+ * tile and brick kernels each run a few hundred steps on a temporary copy of the
+ * instance, which takes as much device memory again for the duration.  The choice is
+ * cached per box, fluid-cell count, storage, collision, wall, layout and device.  The
+ * cache lives for the process, and also in the file named by the environment variable
+ * LBM_AUTOTUNE_CACHE when it is set.  lbm_get_info reports the choice and the times. */
 LBM_API lbm_status lbm_create(const lbm_desc *desc, void *cuda_stream, lbm_ctx **out);
 LBM_API void lbm_destroy(lbm_ctx *ctx);
 
@@ -235,7 +250,7 @@ LBM_API lbm_status lbm_run_developed(lbm_ctx *ctx, const lbm_develop_opts *opts,
 LBM_API lbm_status lbm_fit_barree_conway(const double *re, const double *kstar, int32_t n, const double *init,
                                          double *params_out, double *rms_out);
 
-/* Observables of the last step (synchronises the stream)./* Observables of the last step (synchronises the stream).  K_darcy > 0 enables beta,
+/* Observables of the last step (synchronises the stream).  K_darcy > 0 enables beta,
  * C_F, F_K and Re_K; K_darcy = 0 leaves them NaN.  Returns LBM_ERR_DIVERGED (with *out
  * filled) when the last reduction saw a diverged cell. */
 LBM_API lbm_status lbm_observables(lbm_ctx *ctx, double K_darcy, lbm_obs *out);
@@ -246,6 +261,21 @@ LBM_API lbm_status lbm_observables(lbm_ctx *ctx, double K_darcy, lbm_obs *out);
  * path can be exercised without touching the GPU's state.  n < 0 (the default) disables it.
  * Process-wide; not for production use. */
 LBM_API void lbm_debug_fail_alloc_after(int64_t n);
+
+/* Features the library was compiled with.  LBM_BUILD_CHECKED: the bounds-checked build
+ * (compiled with LBM_CHECKED).  There every index the step kernels use is tested against
+ * the extent of its array. A failing test skips the access and sets a sticky error word,
+ * and the next call that reads the reductions returns LBM_ERR_BOUNDS.  The default
+ * build returns 0. */
+#define LBM_BUILD_CHECKED 1u
+LBM_API unsigned lbm_build_flags(void);
+
+/* Checked build only, for tests of the checks: overwrites the first entry of the
+ * context's fluid-cell work list with the index one past the last cell.  The next
+ * reduction then reports LBM_ERR_BOUNDS.  The context's results are meaningless
+ * afterwards; destroy it.  The default build returns LBM_ERR_STATE and changes nothing,
+ * since its kernels would use such an index. */
+LBM_API lbm_status lbm_debug_corrupt_worklist(lbm_ctx *ctx);
 
 /* FP64 sums over fluid cells of (rho - rho0, u_x, u_y, u_z), computed now from the
  * stored post-collision populations (synchronises).  sums: host array of 4. */

@@ -24,12 +24,14 @@ SBB, CLI, LIBB, QIBB, IEBB, MR = 0, 1, 2, 3, 4, 5
 F64, F32, F16DEV, BF16DEV = 0, 1, 2, 3
 LAYOUT_AB, LAYOUT_AA = 0, 1
 DEV_SCALE_AUTO = -1000
+BLOCK_AUTO = -1
 
 STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_NO_MEMORY", -3: "LBM_ERR_CUDA",
           -4: "LBM_ERR_DIVERGED", -5: "LBM_ERR_NOT_CONVERGED", -6: "LBM_ERR_TIMEOUT",
-          -7: "LBM_ERR_STATE", -8: "LBM_ERR_IO", -9: "LBM_ERR_CANCELLED"}
+          -7: "LBM_ERR_STATE", -8: "LBM_ERR_IO", -9: "LBM_ERR_CANCELLED", -10: "LBM_ERR_BOUNDS"}
 OK, ERR_ARG, ERR_NO_MEMORY, ERR_CUDA, ERR_DIVERGED, ERR_NOT_CONVERGED, ERR_TIMEOUT, \
-    ERR_STATE, ERR_IO, ERR_CANCELLED = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+    ERR_STATE, ERR_IO, ERR_CANCELLED, ERR_BOUNDS = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10
+BUILD_CHECKED = 1
 
 STORAGE_BYTES = {F64: 8, F32: 4, F16DEV: 2, BF16DEV: 2}
 
@@ -96,10 +98,11 @@ class Info(ctypes.Structure):
                  "bytes_populations", "bytes_geometry", "kernel_launches")] + \
                [(n, ctypes.c_int32) for n in
                 ("block_cells", "storage", "layout", "collision", "wall", "dev_scale_log2")] + \
-               [("steps", ctypes.c_int64)]
+               [("steps", ctypes.c_int64), ("autotune", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("tune_ms_tiles", ctypes.c_double), ("tune_ms_bricks", ctypes.c_double)]
 
     def as_dict(self):
-        return {n: getattr(self, n) for n, _ in self._fields_}
+        return {n: getattr(self, n) for n, _ in self._fields_ if n != "pad_"}
 
 
 class ServerOpts(ctypes.Structure):
@@ -166,12 +169,20 @@ PROTOTYPES = {
     "lbm_server_get_stats": (_st, [_vp, ctypes.POINTER(ServerStats)]),
     "lbm_server_cancel": (_st, [_vp, ctypes.c_int64]),
     "lbm_debug_fail_alloc_after": (None, [ctypes.c_int64]),
+    "lbm_build_flags": (ctypes.c_uint, []),
+    "lbm_debug_corrupt_worklist": (ctypes.c_int, [ctypes.c_void_p]),
     "lbm_server_destroy": (None, [_vp]),
 }
 
 
+def library_variant() -> str:
+    """The library variant this process loads: LBM_GB300_VARIANT ("" = the default build,
+    "checked" = the bounds-checked build)."""
+    return os.environ.get("LBM_GB300_VARIANT", "")
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.lib_path(library_variant())
 
 
 def lib(build_if_missing: bool = False):
@@ -179,11 +190,12 @@ def lib(build_if_missing: bool = False):
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB
+            variant = library_variant()
+            path = _build.lib_path(variant)
             if not os.path.exists(path):
                 if not build_if_missing:
                     raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
-                _build.build()
+                _build.build(variant=variant)
             L = ctypes.CDLL(path)
             for name, (res, args) in PROTOTYPES.items():
                 fn = getattr(L, name)
@@ -506,6 +518,17 @@ def debug_fail_alloc_after(n: int):
     """Host-side fault injection (lbm_debug_fail_alloc_after): device allocations after the
     next n fail as out of memory; n < 0 disables."""
     lib().lbm_debug_fail_alloc_after(int(n))
+
+
+def build_flags() -> int:
+    """Features the loaded library was compiled with (lbm_build_flags; BUILD_CHECKED)."""
+    return int(lib().lbm_build_flags())
+
+
+def debug_corrupt_worklist(ctx: "Context"):
+    """Checked build only: plant an out-of-range cell index in the context's work list
+    (lbm_debug_corrupt_worklist); the next reduction reports ERR_BOUNDS."""
+    check(lib().lbm_debug_corrupt_worklist(ctx.handle), "lbm_debug_corrupt_worklist")
 
 
 def fit_barree_conway(re, kstar, init=None):

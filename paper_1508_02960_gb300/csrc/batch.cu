@@ -80,8 +80,9 @@ lbm_status validate_desc(const lbm_desc &d)
     if (d.magic_lambda < 0 || !std::isfinite(d.magic_lambda)) return fail(LBM_ERR_ARG, "magic_lambda must be >= 0");
     if (d.mrt_energy_ratio < 0 || !std::isfinite(d.mrt_energy_ratio))
         return fail(LBM_ERR_ARG, "mrt_energy_ratio must be >= 0");
-    if (d.block_cells != 0 && d.block_cells != 32 * kTileSegs && d.block_cells != kBrickCells)
-        return fail(LBM_ERR_ARG, "block_cells: 0 or 128 (tiles of fluid cells) or 256 (TMA bricks)");
+    if (d.block_cells != 0 && d.block_cells != LBM_BLOCK_AUTO && d.block_cells != 32 * kTileSegs &&
+        d.block_cells != kBrickCells)
+        return fail(LBM_ERR_ARG, "block_cells: 0 or 128 (tiles of fluid cells), 256 (TMA bricks) or -1 (autotune)");
     if (d.block_cells == kBrickCells &&
         (d.layout != LBM_LAYOUT_AB || d.nx % kBrickX || d.ny % kBrickY || d.nz % kBrickZ))
         return fail(LBM_ERR_ARG, "TMA bricks need the A-B layout and nx, ny, nz multiples of 32, 2, 4");
@@ -175,11 +176,20 @@ lbm_status Batch::make_instance(const lbm_desc &d0, cudaStream_t s, std::unique_
         free_geometry(&in->geo);
         return cuda_fail(ce, what);
     };
+    // Canaries: the padding after each direction's ncells values (and the slack) holds
+    // all-ones bytes, a NaN in every storage format, so that a kernel reading there by
+    // mistake turns its results non-finite (the divergence flag, the parity tests).
+    auto clear = [&](void *f) {
+        cudaError_t ce = cudaMemsetAsync(f, 0xFF, pop, s);
+        for (int k = 0; k < Q && ce == cudaSuccess; ++k)
+            ce = cudaMemsetAsync(static_cast<char *>(f) + (size_t)k * in->ks * es, 0, (size_t)n * es, s);
+        return ce;
+    };
     if ((e = dev_alloc(&in->f0, pop)) != cudaSuccess) return cleanup(e, "dev_alloc(populations)");
-    if ((e = cudaMemsetAsync(in->f0, 0, pop, s)) != cudaSuccess) return cleanup(e, "cudaMemset");
+    if ((e = clear(in->f0)) != cudaSuccess) return cleanup(e, "cudaMemset");
     if (d.layout == LBM_LAYOUT_AB) {
         if ((e = dev_alloc(&in->f1, pop)) != cudaSuccess) return cleanup(e, "dev_alloc(populations)");
-        if ((e = cudaMemsetAsync(in->f1, 0, pop, s)) != cudaSuccess) return cleanup(e, "cudaMemset");
+        if ((e = clear(in->f1)) != cudaSuccess) return cleanup(e, "cudaMemset");
     }
     if (d.layout == LBM_LAYOUT_AA && d.wall == LBM_CLI && in->geo.n_links > 0) {
         if ((e = dev_alloc(&in->linkB, es * in->geo.n_links)) != cudaSuccess) return cleanup(e, "dev_alloc(linkB)");
@@ -218,7 +228,7 @@ Batch::~Batch()
     cudaFree(d_stile_begin_);
     cudaFree(d_stile_count_);
     cudaFree(d_bricks_);
-    cudaFree(d_tma_err_);
+    cudaFree(d_error_);
     cudaFree(d_sums_);
     cudaFree(d_status_);
     cudaFree(d_stage_);
@@ -303,6 +313,9 @@ static void fill_dev(const Instance &in, InstanceDev &D)
     D.fcell = in.geo.fcell;
     D.fwarp = in.geo.fwarp;
     D.n_fwarps = (uint32_t)in.geo.n_fwarps;
+    D.n_fwarps_padded = (uint32_t)in.geo.n_fwarps_padded;
+    D.n_boundary = (uint32_t)in.geo.n_boundary;
+    D.n_links = (uint32_t)in.geo.n_links;
     for (int k = 0; k < Q; ++k) {
         const long long dk = ex(k) + (long long)ey(k) * d.nx + (long long)ez(k) * d.nx * d.ny;  // e_k as an offset
         const long long arr = d.layout == LBM_LAYOUT_AA ? opp(k) : k;
@@ -411,10 +424,6 @@ lbm_status Batch::setup_tma()
     if (list.empty()) return not_here("no fluid");
     CK(dev_alloc(&d_bricks_, sizeof(uint32_t) * list.size()));
     CK(cudaMemcpy(d_bricks_, list.data(), sizeof(uint32_t) * list.size(), cudaMemcpyHostToDevice));
-    if (!d_tma_err_) {
-        CK(dev_alloc(&d_tma_err_, sizeof(unsigned)));
-        CK(cudaMemset(d_tma_err_, 0, sizeof(unsigned)));
-    }
     // tensor maps [nz][ny][nx] x 19 directions of both buffers, boxes kBrickX and kBrickX + 16 B wide
     const size_t es = storage_bytes(storage_);
     const CUtensorMapDataType dt = storage_ == LBM_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
@@ -439,7 +448,7 @@ lbm_status Batch::setup_tma()
     tma_launch_.bricks = d_bricks_;
     tma_launch_.nbricks = (int)list.size();
     tma_launch_.grid = (int)std::min<long long>((long long)list.size(), (long long)per_sm * sms);
-    tma_launch_.error = d_tma_err_;
+    tma_launch_.error = d_error_;
     tma_launch_.stream = stream_;
     tma_ = true;
     return LBM_OK;
@@ -455,12 +464,17 @@ lbm_status Batch::rebuild()
     int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (!d_error_) {  // the batch's sticky error word (bounded waits, checked build)
+        CK(dev_alloc(&d_error_, sizeof(unsigned)));
+        CK(cudaMemset(d_error_, 0, sizeof(unsigned)));
+    }
     std::vector<InstanceDev> table(std::max(n, 1));
     std::vector<TileDev> tiles, stiles;
     std::vector<int> tb(std::max(n, 1)), tc(std::max(n, 1)), sb(std::max(n, 1)), sc(std::max(n, 1));
     for (int i = 0; i < n; ++i) {
         Instance &in = *inst_[i];
         fill_dev(in, table[i]);
+        table[i].error = d_error_;
         // state kernels: chunks of the active-segment list
         const long long nt = std::max(1ll, (in.geo.n_active + CS - 1) / CS);
         // step kernels: kTileSegs fluid warps per tile (the list is padded to whole tiles)
@@ -667,10 +681,12 @@ lbm_status Batch::fetch_sums()
     if (n == 0) return LBM_OK;
     CK(cudaMemcpyAsync(h_sums_, d_sums_, sizeof(double) * kRedSlots * n, cudaMemcpyDeviceToHost, stream_));
     CK(cudaMemcpyAsync(h_status_, d_status_, sizeof(unsigned) * n, cudaMemcpyDeviceToHost, stream_));
-    unsigned tma_err = 0;
-    if (tma_) CK(cudaMemcpyAsync(&tma_err, d_tma_err_, sizeof(unsigned), cudaMemcpyDeviceToHost, stream_));
+    unsigned err = 0;
+    if (d_error_) CK(cudaMemcpyAsync(&err, d_error_, sizeof(unsigned), cudaMemcpyDeviceToHost, stream_));
     CK(cudaStreamSynchronize(stream_));
-    if (tma_err) return fail(LBM_ERR_TIMEOUT, "a TMA brick copy did not complete within its wait limit");
+    if (err & STATUS_TIMEOUT) return fail(LBM_ERR_TIMEOUT, "a TMA brick copy did not complete within its wait limit");
+    if (err & STATUS_BOUNDS)
+        return fail(LBM_ERR_BOUNDS, "checked build: a step kernel met an index outside its arrays (access skipped)");
     for (int i = 0; i < n; ++i) {
         Instance &in = *inst_[i];
         for (int d = 0; d < kRedSlots; ++d) in.sums[d] = h_sums_[kRedSlots * i + d];
@@ -850,6 +866,9 @@ void Batch::fill_info(int i, lbm_info *out) const
     out->storage = storage_;
     out->layout = layout_;
     out->collision = collision_;
+    out->autotune = tune_src_;
+    out->tune_ms_tiles = tune_ms_[0];
+    out->tune_ms_bricks = tune_ms_[1];
 }
 
 // ------------------------------------------------------------------------------------

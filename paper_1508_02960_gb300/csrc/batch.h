@@ -69,6 +69,14 @@ public:
     cudaStream_t stream() const { return stream_; }
     long long fluid_cells() const;
     lbm_status set_block(int block_cells);
+    // how the step kernel was chosen (0 = given, 1 = measured now, 2 = from the autotuner
+    // cache) and the ms per step measured for the tiles and the bricks
+    void set_tuning(int source, double ms_tiles, double ms_bricks)
+    {
+        tune_src_ = source;
+        tune_ms_[0] = ms_tiles;
+        tune_ms_[1] = ms_bricks;
+    }
     lbm_status prepare();              // upload tables and choose the step kernel now if pending
 
 private:
@@ -77,6 +85,8 @@ private:
     const FormatOps &ops() const { return format_ops(storage_); }
 
     std::vector<std::unique_ptr<Instance>> inst_;
+    int tune_src_ = 0;
+    double tune_ms_[2] = {0.0, 0.0};
     int storage_ = 0, collision_ = 0, layout_ = 0;
     cudaStream_t stream_ = nullptr;   // user stream (launches)
     cudaStream_t cap_ = nullptr;      // private stream for graph capture
@@ -99,7 +109,7 @@ private:
     bool tma_ = false;
     TmaLaunch tma_launch_{};
     uint32_t *d_bricks_ = nullptr;
-    unsigned *d_tma_err_ = nullptr;
+    unsigned *d_error_ = nullptr;
     lbm_status setup_tma();           // decides tma_ and builds maps and brick list
     int grid_ = 0;                    // step-kernel blocks (one per step tile)
     int aux_grid_ = 1;
@@ -117,6 +127,8 @@ lbm_status fail(lbm_status st, const std::string &msg);
 lbm_status validate_desc(const lbm_desc &d);
 // Observables of an instance's last reduction (Eqs. Darcy, Forchheimer, frictionFactor).
 void compute_obs(const Instance &in, double K_D, lbm_obs *out);
+// Step kernel of a single-instance batch chosen by measurement (block_cells = LBM_BLOCK_AUTO).
+lbm_status autotune_block(Batch &b, const lbm_desc &d, cudaStream_t s);
 lbm_status cuda_fail(cudaError_t e, const char *what);
 
 }  // namespace lbm

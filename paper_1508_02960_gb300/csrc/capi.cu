@@ -85,15 +85,20 @@ lbm_status create_batch(Batch &b, const lbm_desc *descs, int n, cudaStream_t s)
     lbm_status st = b.init(s, descs[0].storage, descs[0].collision, descs[0].layout);
     if (st != LBM_OK) return st;
     int block = 0;
+    bool tune = false;
     for (int i = 0; i < n; ++i) {
         std::unique_ptr<Instance> in;
         st = Batch::make_instance(descs[i], s, &in);
         if (st != LBM_OK) return st;
-        if (descs[i].block_cells) block = descs[i].block_cells;
+        if (descs[i].block_cells == LBM_BLOCK_AUTO) tune = true;
+        else if (descs[i].block_cells) block = descs[i].block_cells;
         st = b.add(std::move(in));
         if (st != LBM_OK) return st;
     }
-    if (block) {
+    if (tune && !block) {
+        st = autotune_block(b, descs[0], s);
+        if (st != LBM_OK) return st;
+    } else if (block) {
         st = b.set_block(block);
         if (st != LBM_OK) return st;
     }
@@ -106,6 +111,20 @@ extern "C" {
 
 const char *lbm_last_error(void) { return last_error_cstr(); }
 const char *lbm_version(void) { return "lbm_gb300 0.1 (sm_103a)"; }
+
+unsigned lbm_build_flags(void) { return kChecked ? LBM_BUILD_CHECKED : 0u; }
+
+lbm_status lbm_debug_corrupt_worklist(lbm_ctx *ctx)
+{
+    if (!ctx || ctx->b.size() != 1) return fail(LBM_ERR_ARG, "ctx is NULL");
+    if (!kChecked) return fail(LBM_ERR_STATE, "only the checked build (LBM_CHECKED) tests its indices");
+    const Instance &in = ctx->b.at(0);
+    if (!in.geo.fcell || in.geo.n_fwarps < 1) return fail(LBM_ERR_STATE, "no fluid cells");
+    const uint32_t bad = (uint32_t)in.geo.ncells;  // one past the last cell
+    cudaError_t e = cudaMemcpyAsync(in.geo.fcell, &bad, sizeof(bad), cudaMemcpyHostToDevice, ctx->b.stream());
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->b.stream());
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "cudaMemcpyAsync");
+}
 
 lbm_status lbm_create(const lbm_desc *desc, void *cuda_stream, lbm_ctx **out)
 {

@@ -208,6 +208,10 @@ __host__ __device__ __forceinline__ uint32_t fast_div(uint32_t n, const FastDiv 
     return (t + ((n - t) >> f.sh1)) >> f.sh2;
 }
 
+// Status word bits: a reduction saw a diverged cell; a bounded wait ran out; (checked
+// build) a kernel met an index outside its arrays and skipped the access.
+enum { STATUS_DIVERGED = 1u, STATUS_TIMEOUT = 2u, STATUS_BOUNDS = 4u };
+
 // ------------------------------------------------------------------------------------
 // Per-instance parameters, read by every kernel from a device table so that one launch
 // can advance many independent cells (the batched sweep) or just one.
@@ -255,7 +259,31 @@ struct InstanceDev {
     double omega_m;          // TRT omega-
     double s[Q];             // MRT relaxation rates
     double delta_rho, rho0;
+    // sizes the checked build tests indices against, and the batch's sticky error word
+    // (STATUS_BOUNDS, STATUS_TIMEOUT), which the host reads with the reductions
+    uint32_t n_fwarps_padded, n_boundary, n_links;
+    unsigned *error;
 };
+
+#ifdef LBM_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
+// Index test of the checked build (LBM_CHECKED): true when i < n; otherwise it sets
+// STATUS_BOUNDS in the batch error word and returns false, and the caller skips the
+// access.  The default build compiles it to true.
+__device__ __forceinline__ bool checked(const InstanceDev &I, uint32_t i, uint32_t n)
+{
+    if constexpr (kChecked) {
+        if (i >= n) {
+            atomicOr(I.error, STATUS_BOUNDS);
+            return false;
+        }
+    }
+    return true;
+}
 
 // Coefficients of the interpolated wall rules LIBB, QIBB, IEBB and MR (Sec. 2.2.1), one
 // row of kLinkW values per cut link (x, kbar), x - e_k solid, in the compute type.  With
@@ -291,9 +319,6 @@ constexpr int kBrickStages = 2;
 constexpr int kStepWarps = 4;
 constexpr int kTileSegs = kStepWarps;
 enum { COLL_SRT = 0, COLL_TRT = 1, COLL_MRT = 2 };
-
-// Status word bits: a reduction saw a diverged cell; a bounded wait ran out.
-enum { STATUS_DIVERGED = 1u, STATUS_TIMEOUT = 2u };
 
 // FP64 reduction slots per tile and per instance: sum of (rho - rho0), of u_x, u_y, u_z
 // over fluid cells, then the x, y, z momentum exchanged with the solid in the step

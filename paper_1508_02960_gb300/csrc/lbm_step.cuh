@@ -99,11 +99,16 @@ template <typename R> __device__ __forceinline__ Coord coord_of(const Par<R> &p,
     return c;
 }
 
-// Blocks per multiprocessor the register allocation is sized for: 32 warps (64 registers a
-// thread) for the 32- and 16-bit formats, 8 warps for FP64.
-template <int STORE, int KIND> constexpr int step_min_blocks()
+// Blocks per multiprocessor the register allocation is sized for.  The plain step of the
+// 32- and 16-bit formats: 36 warps (56 registers a thread; measured 1-5 % faster than 32
+// warps at 64 registers, and 40 warps spill).  The reducing and interpolated-wall variants
+// keep 32 warps (64 registers), where 56 would spill.  FP64: 8 warps.
+#ifndef LBM_STEP_WARPS_PER_SM
+#define LBM_STEP_WARPS_PER_SM 36
+#endif
+template <int STORE, bool RED, bool WX> constexpr int step_min_blocks()
 {
-    return (STORE == ST_F64 ? 8 : 32) / kStepWarps;
+    return (STORE == ST_F64 ? 8 : (RED || WX) ? 32 : LBM_STEP_WARPS_PER_SM) / kStepWarps;
 }
 
 // Moments of the incoming populations (Eq. Macro), in deviation form.
@@ -297,7 +302,8 @@ __device__ __forceinline__ R wall_own_part_w(const Par<R> &P, const R *lw, int k
 // Walls in the AA layout: C is in the own slot k, B (CLI) in the link buffer linkB, and
 // the same arithmetic runs at the start of the step.
 template <int COLL, int STORE, int KIND, bool RED, bool WX, typename R>
-__device__ __forceinline__ void finish_cell(R (&g)[Q], const Par<R> &P, const R *rates, uint32_t cell, uint32_t x,
+__device__ __forceinline__ void finish_cell(const InstanceDev &I, R (&g)[Q], const Par<R> &P, const R *rates,
+                                            uint32_t cell, uint32_t x,
                                             bool inner, const uint32_t *pull_off, const uint32_t *push_off,
                                             uint32_t wm, uint32_t off, const typename Store<STORE>::T *fs,
                                             typename Store<STORE>::T *fd, const R *linkc, const R *linkw,
@@ -366,8 +372,9 @@ __device__ __forceinline__ void finish_cell(R (&g)[Q], const Par<R> &P, const R 
                 if (ex(k) == 1) idx -= cxp;
                 if (ex(k) == -1) idx += cxm;
                 // push to x + e_k, or bounce into the own slot kbar when x + e_k is solid
-                if ((wm >> opp(k)) & 1u) idx = (uint32_t)opp(k) * KS + cell;
-                fd[idx] = packed[k];
+                const bool bounce = (wm >> opp(k)) & 1u;
+                if (bounce) idx = (uint32_t)opp(k) * KS + cell;
+                if (checked(I, idx - (uint32_t)(bounce ? opp(k) : k) * KS, I.n32)) fd[idx] = packed[k];
             }
         } else {
             const Coord co = coord_of(P, cell);
@@ -408,7 +415,8 @@ __device__ __forceinline__ void finish_cell(R (&g)[Q], const Par<R> &P, const R 
                 } else {
                     idx = (uint32_t)k * KS + co.pull(k);
                 }
-                fd[idx] = sr ? S::pack_sr(sv, P.sc, round_bits(h, k, float(sv))) : S::pack(sv, P.sc);
+                if (checked(I, idx - (uint32_t)k * KS, I.n32))
+                    fd[idx] = sr ? S::pack_sr(sv, P.sc, round_bits(h, k, float(sv))) : S::pack(sv, P.sc);
             }
         }
     }
@@ -438,8 +446,10 @@ struct WarpItem {
 template <typename R>
 __device__ __forceinline__ void locate_item(const InstanceDev &I, const Par<R> &P, uint32_t w, int lane, WarpItem &it)
 {
-    it.wd = I.fwarp[w];
-    it.cell = I.fcell[w * 32u + (uint32_t)lane];
+    const bool w_ok = checked(I, w, I.n_fwarps_padded);
+    it.wd = w_ok ? I.fwarp[w] : make_uint2(0u, 0u);
+    it.cell = w_ok ? I.fcell[w * 32u + (uint32_t)lane] : 0xFFFFFFFFu;
+    if (it.cell != 0xFFFFFFFFu && !checked(I, it.cell, I.n32)) it.cell = 0xFFFFFFFFu;
     const bool live = it.cell != 0xFFFFFFFFu;
     const uint32_t yz = fast_div(it.cell, P.dnx);
     it.x = it.cell - yz * P.nx;
@@ -451,8 +461,12 @@ __device__ __forceinline__ void locate_item(const InstanceDev &I, const Par<R> &
     it.off = 0u;
     if ((it.wd.x >> lane) & 1u) {
         const uint32_t b = it.wd.y + __popc(it.wd.x & ((1u << lane) - 1u));
-        it.wm = I.bmask[b];
-        it.off = I.boff[b];
+        if (checked(I, b, I.n_boundary)) {
+            it.wm = I.bmask[b];
+            it.off = I.boff[b];
+            // every link of the cell within the link tables
+            if (!checked(I, it.off + __popc(it.wm), I.n_links + 1u)) it.wm = 0u;
+        }
     }
 }
 
@@ -472,7 +486,8 @@ __device__ __forceinline__ void pull_item(const InstanceDev &I, const Par<R> &P,
             uint32_t idx = it.cell + I.pull_off[k];
             if (ex(k) == 1) idx += cxm;   // x - 1 wraps to the end of the row
             if (ex(k) == -1) idx -= cxp;  // x + 1 wraps to the start of the row
-            raw[k] = __ldg(fs + idx);
+            const uint32_t d = KIND == KIND_AA_PULL ? (uint32_t)opp(k) : (uint32_t)k;
+            raw[k] = checked(I, idx - d * P.ks, I.n32) ? __ldg(fs + idx) : typename Store<STORE>::T{};
         }
     } else {
         const Coord co = coord_of(P, it.cell);
@@ -482,7 +497,8 @@ __device__ __forceinline__ void pull_item(const InstanceDev &I, const Par<R> &P,
             if constexpr (KIND == KIND_AA_LOCAL) idx = (uint32_t)k * P.ks + it.cell;
             else if constexpr (KIND == KIND_AA_PULL) idx = (uint32_t)opp(k) * P.ks + co.pull(k);
             else idx = (uint32_t)k * P.ks + co.pull(k);
-            raw[k] = __ldg(fs + idx);
+            const uint32_t d = KIND == KIND_AA_PULL ? (uint32_t)opp(k) : (uint32_t)k;
+            raw[k] = checked(I, idx - d * P.ks, I.n32) ? __ldg(fs + idx) : typename Store<STORE>::T{};
         }
     }
 }
@@ -522,7 +538,7 @@ __device__ __forceinline__ void finish_item(const InstanceDev &I, const Par<R> &
     }
     R rd = R(0), rx = R(0), ry = R(0), rz = R(0);
     R fm[3] = {R(0), R(0), R(0)};
-    finish_cell<COLL, STORE, KIND, RED, WX, R>(g, P, rates, it.cell, it.x, it.inner, I.pull_off,
+    finish_cell<COLL, STORE, KIND, RED, WX, R>(I, g, P, rates, it.cell, it.x, it.inner, I.pull_off,
                                                it.inner ? I.push_off : nullptr, wm, it.off, fs, fd,
                                                reinterpret_cast<const R *>(I.linkc),
                                                reinterpret_cast<const R *>(I.linkw), reinterpret_cast<T *>(I.linkB),
@@ -588,7 +604,7 @@ __device__ __forceinline__ const InstanceDev &instance_of(const InstanceDev *tab
 // other steps carry none of that code.  The WX variant (A-B only) also runs the
 // interpolated wall rules LIBB, QIBB, IEBB and MR.
 template <int COLL, int STORE, int KIND, bool BATCH, bool RED, bool WX>
-__global__ void __launch_bounds__(kStepWarps * 32, step_min_blocks<STORE, KIND>())
+__global__ void __launch_bounds__(kStepWarps * 32, step_min_blocks<STORE, RED, WX>())
     step_kernel(const InstanceDev *__restrict__ table, const __grid_constant__ InstanceDev one,
                 const TileDev *__restrict__ tiles, int ntiles, int flip, unsigned *__restrict__ status)
 {

@@ -143,7 +143,9 @@ __global__ void __launch_bounds__(kBrickCells, tma_min_blocks<STORE>())
         brick_origin(bricks[brick], x0, y0, z0);
         const uint32_t x = (uint32_t)(x0 + cx), y = (uint32_t)(y0 + cy), z = (uint32_t)(z0 + cz);
         const uint32_t cell = x + P.nx * (y + P.ny * z);
-        const uint4 sg = I.seg[cell >> 5];  // solid, boundary bits, boundary-table base of the row
+        const bool in_box = checked(I, cell, I.n32);
+        // solid, boundary bits, boundary-table base of the row
+        const uint4 sg = in_box ? I.seg[cell >> 5] : make_uint4(~0u, 0u, 0u, 0u);
         const bool live = !((sg.x >> cx) & 1u);
         m.cell = live ? cell : 0xFFFFFFFFu;
         m.x = x;
@@ -153,8 +155,11 @@ __global__ void __launch_bounds__(kBrickCells, tma_min_blocks<STORE>())
         m.wd = make_uint2(y, z);
         if (live && ((sg.y >> cx) & 1u)) {
             const uint32_t bi = sg.z + __popc(sg.y & ((1u << cx) - 1u));
-            m.wm = I.bmask[bi];
-            m.off = I.boff[bi];
+            if (checked(I, bi, I.n_boundary)) {
+                m.wm = I.bmask[bi];
+                m.off = I.boff[bi];
+                if (!checked(I, m.off + __popc(m.wm), I.n_links + 1u)) m.wm = 0u;
+            }
         }
     };
 

@@ -50,8 +50,9 @@ int main(void) {
          sizeof(lbm_server_opts), sizeof(lbm_server_stats), sizeof(lbm_sphere));
   printf("%zu %zu %zu %zu %zu\\n", offsetof(lbm_desc, tau), offsetof(lbm_desc, collision),
          offsetof(lbm_desc, d_p), offsetof(lbm_desc, seed), offsetof(lbm_info, block_cells));
-  printf("%zu %zu %zu %zu %zu\\n", sizeof(lbm_develop_opts), sizeof(lbm_develop_result),
-         offsetof(lbm_develop_result, developed), offsetof(lbm_obs, K_star), offsetof(lbm_develop_opts, max_steps));
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(lbm_develop_opts), sizeof(lbm_develop_result),
+         offsetof(lbm_develop_result, developed), offsetof(lbm_obs, K_star), offsetof(lbm_develop_opts, max_steps),
+         offsetof(lbm_info, autotune), offsetof(lbm_info, tune_ms_bricks));
   return 0;
 }
 """)
@@ -66,13 +67,15 @@ int main(void) {
                     capi.Desc.seed.offset, capi.Info.block_cells.offset]
     assert [int(v) for v in c.split()] == [ctypes.sizeof(capi.DevelopOpts), ctypes.sizeof(capi.DevelopResult),
                                            capi.DevelopResult.developed.offset, capi.Obs.K_star.offset,
-                                           capi.DevelopOpts.max_steps.offset]
+                                           capi.DevelopOpts.max_steps.offset, capi.Info.autotune.offset,
+                                           capi.Info.tune_ms_bricks.offset]
 
 
 @pytest.mark.parametrize("bad", [
     dict(tau=0.5), dict(tau=float("nan")), dict(nx=0), dict(collision=7), dict(wall=6), dict(wall=-1),
     dict(wall=2, layout=1), dict(wall=5, layout=1), dict(wall=4, tau=2.0), dict(storage=9),
-    dict(layout=3), dict(block_cells=100), dict(block_cells=64), dict(block_cells=2048), dict(block_cells=512), dict(perturb_u=0.5),
+    dict(layout=3), dict(block_cells=100), dict(block_cells=64), dict(block_cells=2048), dict(block_cells=512),
+    dict(block_cells=-2), dict(perturb_u=0.5),
     dict(spheres=[[1, 1, 1, -2.0]]), dict(dev_scale_log2=99), dict(magic_lambda=-1.0),
 ])
 def test_invalid_descriptor_rejected_before_gpu(L, bad):

@@ -287,6 +287,21 @@ LBM_API lbm_status lbm_moment_sums(lbm_ctx *ctx, double *sums);
 LBM_API lbm_status lbm_get_populations_f64(lbm_ctx *ctx, double *host_out);
 LBM_API lbm_status lbm_set_populations_f64(lbm_ctx *ctx, const double *host_in);
 
+/* The stored state of the fluid cells, bit for bit, in the context's storage type.
+ * Layout: host[k * n_fluid + j] is the post-collision deviation g~_k = f_k - w_k rho0 of
+ * the j-th fluid cell in cell order (x fastest; n_fluid from lbm_get_info).  The values are
+ * as stored: double (LBM_F64), float (LBM_F32), or the 16-bit pattern of an IEEE half
+ * times 2^dev_scale_log2 (LBM_F16DEV) or of a bfloat16 (LBM_BF16DEV).
+ * bytes must equal 19 * n_fluid * element size, else LBM_ERR_ARG.  The host buffer stays
+ * the caller's; pinned memory transfers faster, and pageable memory also works.  The copy
+ * of one direction overlaps the device-side gather or scatter of the other.
+ * A state read with lbm_get_state and written back with lbm_set_state continues bit for bit
+ * as the original would (the wall terms of the A-B layout are rebuilt from it, as by
+ * lbm_set_populations_f64).  It carries 19 values per fluid cell in the storage type.
+ * lbm_set_populations_f64 carries 19 FP64 values per cell of the box.  Both synchronise. */
+LBM_API lbm_status lbm_get_state(lbm_ctx *ctx, void *host_out, size_t bytes);
+LBM_API lbm_status lbm_set_state(lbm_ctx *ctx, const void *host_in, size_t bytes);
+
 /* Velocity u = rho0^-1 sum e_k f_k of the stored state, FP64 [3][nz][ny][nx] (0 in solid). */
 LBM_API lbm_status lbm_get_velocity_f64(lbm_ctx *ctx, double *host_out);
 /* Solid flags [nz][ny][nx] (1 = solid) as built on the device. */

@@ -142,6 +142,8 @@ PROTOTYPES = {
     "lbm_fit_barree_conway": (_st, [_dp, _dp, ctypes.c_int32, _dp, _dp, _dp]),
     "lbm_get_populations_f64": (_st, [_vp, _dp]),
     "lbm_set_populations_f64": (_st, [_vp, _dp]),
+    "lbm_get_state": (_st, [_vp, _vp, ctypes.c_size_t]),
+    "lbm_set_state": (_st, [_vp, _vp, ctypes.c_size_t]),
     "lbm_get_velocity_f64": (_st, [_vp, _dp]),
     "lbm_get_flags": (_st, [_vp, ctypes.POINTER(ctypes.c_uint8)]),
     "lbm_get_wall_distances": (_st, [_vp, _dp]),
@@ -367,6 +369,26 @@ class Context:
         f = np.ascontiguousarray(f, dtype=np.float64)
         assert f.size == Q * self.n_cells
         check(lib().lbm_set_populations_f64(self._h, _f64(f)), "lbm_set_populations_f64")
+
+    def state_dtype(self):
+        """numpy dtype of the stored state (16-bit formats as their raw uint16 patterns)."""
+        return {F64: np.float64, F32: np.float32, F16DEV: np.uint16, BF16DEV: np.uint16}[self.storage]
+
+    def get_state(self, out=None) -> np.ndarray:
+        """The stored fluid-cell state, bit for bit: [19][n_fluid] in the storage type
+        (lbm_get_state).  out: an optional C-contiguous array of that shape and dtype
+        (e.g. a pinned buffer)."""
+        nf = self.info()["n_fluid"]
+        s = out if out is not None else np.empty((Q, nf), dtype=self.state_dtype())
+        assert s.dtype == self.state_dtype() and s.flags.c_contiguous and s.size == Q * nf
+        check(lib().lbm_get_state(self._h, s.ctypes.data, s.nbytes), "lbm_get_state")
+        return s
+
+    def set_state(self, s):
+        """Set the fluid-cell state from get_state's layout (lbm_set_state)."""
+        s = np.ascontiguousarray(s)
+        assert s.dtype == self.state_dtype()
+        check(lib().lbm_set_state(self._h, s.ctypes.data, s.nbytes), "lbm_set_state")
 
     def get_velocity(self) -> np.ndarray:
         u = np.empty((3,) + self.shape)

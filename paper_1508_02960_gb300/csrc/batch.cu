@@ -235,6 +235,11 @@ Batch::~Batch()
     if (h_sums_) cudaFreeHost(h_sums_);
     if (h_status_) cudaFreeHost(h_status_);
     if (cap_) cudaStreamDestroy(cap_);
+    cudaFree(d_sstage_[0]);
+    cudaFree(d_sstage_[1]);
+    if (copy_) cudaStreamDestroy(copy_);
+    for (cudaEvent_t e : ev_)
+        if (e) cudaEventDestroy(e);
 }
 
 lbm_status Batch::init(cudaStream_t user_stream, int storage, int collision, int layout)
@@ -772,6 +777,71 @@ lbm_status Batch::set_f64(int i, const double *host)
         CK(cudaMemcpyAsync(d_stage_, host + (long long)k * n, sizeof(double) * n, cudaMemcpyHostToDevice, stream_));
         CK(ops().import_dir(d_table_, i, n, layout_, cur_of(in), k, d_stage_, stream_));
         ++launches_;
+    }
+    if (layout_ == LBM_LAYOUT_AB && in.geo.n_boundary > 0) {
+        CK(ops().wall_prepare(d_table_, i, in.geo.n_boundary, in.geo.bcell, cur_of(in), stream_));
+        ++launches_;
+    }
+    in.have_sums = false;
+    in.have_force = false;
+    in.sums_pending = false;
+    CK(cudaStreamSynchronize(stream_));
+    return LBM_OK;
+}
+
+lbm_status Batch::state_io(int i, void *host, size_t bytes, bool to_host)
+{
+    if (i < 0 || i >= size() || !host) return fail(LBM_ERR_ARG, "bad instance index or NULL buffer");
+    if (dirty_) {
+        lbm_status st = rebuild();
+        if (st != LBM_OK) return st;
+    }
+    Instance &in = *inst_[i];
+    const long long nf = in.geo.n_fluid;
+    const size_t dir_bytes = (size_t)nf * storage_bytes(storage_);
+    if (bytes != (size_t)Q * dir_bytes) return fail(LBM_ERR_ARG, "state buffer must hold 19 * n_fluid elements");
+    if (!to_host && layout_ == LBM_LAYOUT_AA) aa_phase_ = 0;
+    if (nf > 0) {
+        if (!copy_) CK(cudaStreamCreateWithFlags(&copy_, cudaStreamNonBlocking));
+        for (cudaEvent_t &e : ev_)
+            if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        if (sstage_bytes_ < dir_bytes) {
+            cudaFree(d_sstage_[0]);
+            cudaFree(d_sstage_[1]);
+            d_sstage_[0] = d_sstage_[1] = nullptr;
+            sstage_bytes_ = 0;
+            CK(dev_alloc(&d_sstage_[0], dir_bytes));
+            CK(dev_alloc(&d_sstage_[1], dir_bytes));
+            sstage_bytes_ = dir_bytes;
+        }
+        const int cur = cur_of(in);
+        char *h = static_cast<char *>(host);
+        // direction k through staging buffer k % 2: the copy of one direction overlaps the
+        // gather or scatter of the other
+        for (int k = 0; k < Q; ++k) {
+            const int b = k & 1;
+            void *st = d_sstage_[b];
+            if (to_host) {
+                if (k >= 2) CK(cudaStreamWaitEvent(stream_, ev_[2 + b], 0));
+                CK(ops().state_dir(d_table_, i, nf, layout_, cur, aa_phase_, k, st, 1, stream_));
+                CK(cudaEventRecord(ev_[b], stream_));
+                CK(cudaStreamWaitEvent(copy_, ev_[b], 0));
+                CK(cudaMemcpyAsync(h + k * dir_bytes, st, dir_bytes, cudaMemcpyDeviceToHost, copy_));
+                CK(cudaEventRecord(ev_[2 + b], copy_));
+            } else {
+                if (k >= 2) CK(cudaStreamWaitEvent(copy_, ev_[2 + b], 0));
+                CK(cudaMemcpyAsync(st, h + k * dir_bytes, dir_bytes, cudaMemcpyHostToDevice, copy_));
+                CK(cudaEventRecord(ev_[b], copy_));
+                CK(cudaStreamWaitEvent(stream_, ev_[b], 0));
+                CK(ops().state_dir(d_table_, i, nf, layout_, cur, aa_phase_, k, st, 0, stream_));
+                CK(cudaEventRecord(ev_[2 + b], stream_));
+            }
+            ++launches_;
+        }
+    }
+    if (to_host) {
+        if (copy_) CK(cudaStreamSynchronize(copy_));
+        return LBM_OK;
     }
     if (layout_ == LBM_LAYOUT_AB && in.geo.n_boundary > 0) {
         CK(ops().wall_prepare(d_table_, i, in.geo.n_boundary, in.geo.bcell, cur_of(in), stream_));

@@ -56,6 +56,8 @@ public:
     lbm_status fetch_sums();                           // copy last reduction to host (synchronises)
     lbm_status get_f64(int i, double *host);
     lbm_status set_f64(int i, const double *host);
+    // fluid-cell state in the storage type, bit for bit ([19][n_fluid]; see lbm_get_state)
+    lbm_status state_io(int i, void *host, size_t bytes, bool to_host);
     lbm_status get_velocity(int i, double *host);
     lbm_status get_flags(int i, uint8_t *host);
     lbm_status get_q(int i, double *host);
@@ -120,6 +122,12 @@ private:
     std::map<std::tuple<long long, int, int>, cudaGraphExec_t> graphs_;
     double *d_stage_ = nullptr;       // FP64 staging for import/export (one direction)
     long long stage_cells_ = 0;
+    // state transfers: two staging buffers of one direction each, a copy stream, and
+    // events: ev_[b] buffer b filled, ev_[2 + b] buffer b free again
+    void *d_sstage_[2] = {nullptr, nullptr};
+    size_t sstage_bytes_ = 0;
+    cudaStream_t copy_ = nullptr;
+    cudaEvent_t ev_[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 lbm_status fail(lbm_status st, const std::string &msg);

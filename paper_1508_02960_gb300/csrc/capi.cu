@@ -352,6 +352,18 @@ lbm_status lbm_set_populations_f64(lbm_ctx *ctx, const double *host_in)
     return ctx->b.set_f64(0, host_in);
 }
 
+lbm_status lbm_get_state(lbm_ctx *ctx, void *host_out, size_t bytes)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "ctx is NULL");
+    return ctx->b.state_io(0, host_out, bytes, true);
+}
+
+lbm_status lbm_set_state(lbm_ctx *ctx, const void *host_in, size_t bytes)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "ctx is NULL");
+    return ctx->b.state_io(0, const_cast<void *>(host_in), bytes, false);
+}
+
 lbm_status lbm_get_velocity_f64(lbm_ctx *ctx, double *host_out)
 {
     if (!ctx) return fail(LBM_ERR_ARG, "ctx is NULL");

@@ -243,6 +243,55 @@ __global__ void export_kernel(const InstanceDev *__restrict__ table, int inst, i
     }
 }
 
+// The stored state of direction k of the fluid cells, bit for bit, in the storage type:
+// out[j] = the stored g~_k of fluid cell j (cells in cell order, from the work list), read
+// where the layout keeps it (as export_kernel).
+template <int STORE>
+__global__ void state_gather_kernel(const InstanceDev *__restrict__ table, int inst, int layout, int cur,
+                                    int aa_phase, int k, long long nf, typename Store<STORE>::T *__restrict__ out)
+{
+    using T = typename Store<STORE>::T;
+    const InstanceDev &I = table[inst];
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < nf;
+         j += (long long)gridDim.x * blockDim.x) {
+        const long long cell = I.fcell[j];
+        const int lane = (int)(cell & 31);
+        CellGeom c;
+        cell_geom(I, cell, I.seg[cell >> 5], lane, c);
+        int buf;
+        const long long idx = canonical_index<STORE>(I, layout, aa_phase, cur, cell, k, c.wm, c.X, c.Y, c.Z, buf);
+        out[j] = reinterpret_cast<const T *>(buf ? I.f1 : I.f0)[idx];
+    }
+}
+
+// The inverse for a state set from outside (as import_kernel, without conversion): direction
+// k of fluid cell j from in[j] into its slot of the step-0 arrangement; in the AA layout
+// also into the link buffer of its CLI links.  Solid cells are left alone (the A-B solid
+// slots are rebuilt by wall_prepare_kernel).
+template <int STORE>
+__global__ void state_scatter_kernel(const InstanceDev *__restrict__ table, int inst, int layout, int cur, int k,
+                                     long long nf, const typename Store<STORE>::T *__restrict__ in)
+{
+    using T = typename Store<STORE>::T;
+    const InstanceDev &I = table[inst];
+    T *f = reinterpret_cast<T *>(layout == 0 ? (cur ? I.f1 : I.f0) : I.f0);
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < nf;
+         j += (long long)gridDim.x * blockDim.x) {
+        const long long cell = I.fcell[j];
+        const T v = in[j];
+        f[(long long)(layout == 0 ? k : opp(k)) * I.ks + cell] = v;
+        if (layout == 1 && I.linkB) {
+            const uint4 meta = I.seg[cell >> 5];
+            const int lane = (int)(cell & 31);
+            if ((meta.y >> lane) & 1u) {
+                const uint32_t b = meta.z + __popc(meta.y & ((1u << lane) - 1u));
+                const uint32_t wm = I.bmask[b];
+                if ((wm >> k) & 1u) reinterpret_cast<T *>(I.linkB)[I.boff[b] + __popc(wm & ((1u << k) - 1u))] = v;
+            }
+        }
+    }
+}
+
 // Moments of the stored post-collision state of every fluid cell, one warp per work
 // chunk.  mode 0: write the velocity component `comp` to out[cell] of fluid cells (the
 // caller clears out first).  mode 1: chunk partial sums (drho, u_x, u_y, u_z) into

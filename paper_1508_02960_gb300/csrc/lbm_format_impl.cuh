@@ -194,6 +194,21 @@ cudaError_t export_dir(const InstanceDev *table, int inst, long long n, int layo
 }
 
 template <int STORE>
+cudaError_t state_dir(const InstanceDev *table, int inst, long long nf, int layout, int cur, int aa_phase, int k,
+                      void *buf, int to_host, cudaStream_t s)
+{
+    if (nf <= 0) return cudaSuccess;
+    using T = typename Store<STORE>::T;
+    if (to_host)
+        state_gather_kernel<STORE>
+            <<<flat_grid(nf, 256), 256, 0, s>>>(table, inst, layout, cur, aa_phase, k, nf, static_cast<T *>(buf));
+    else
+        state_scatter_kernel<STORE>
+            <<<flat_grid(nf, 256), 256, 0, s>>>(table, inst, layout, cur, k, nf, static_cast<const T *>(buf));
+    return cudaGetLastError();
+}
+
+template <int STORE>
 cudaError_t moments(const Launch &L, int layout, int cur, int aa_phase, int mode, int comp, double *out)
 {
     moments_kernel<STORE><<<L.grid, L.block, 0, L.stream>>>(L.table, L.tiles, L.ntiles, L.chunk_segs, layout, cur,
@@ -218,6 +233,7 @@ FormatOps make_ops()
     o.init = &init<STORE>;
     o.import_dir = &import_dir<STORE>;
     o.export_dir = &export_dir<STORE>;
+    o.state_dir = &state_dir<STORE>;
     o.moments = &moments<STORE>;
     o.wall_prepare = &wall_prepare<STORE>;
     o.step_tma = &step_tma<STORE>;

@@ -39,6 +39,16 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// Loads of population values.  An A-B step reads a buffer that no thread of the step
+// writes, through the read-only (non-coherent) path.  The AA steps update their buffer, and
+// the CLI link buffer, in place: a non-coherent load there is not allowed (the compiler may
+// then order it after a store of the same thread), so they load plainly.
+template <int KIND, typename T> __device__ __forceinline__ T ld_pop(const T *p)
+{
+    if constexpr (KIND == KIND_AB) return __ldg(p);
+    else return *p;
+}
+
 // The step kernel uses no dynamic shared memory.
 inline size_t step_smem_bytes(int, int) { return 0; }
 
@@ -99,16 +109,17 @@ template <typename R> __device__ __forceinline__ Coord coord_of(const Par<R> &p,
     return c;
 }
 
-// Blocks per multiprocessor the register allocation is sized for.  The plain step of the
-// 32- and 16-bit formats: 36 warps (56 registers a thread; measured 1-5 % faster than 32
-// warps at 64 registers, and 40 warps spill).  The reducing and interpolated-wall variants
-// keep 32 warps (64 registers), where 56 would spill.  FP64: 8 warps.
+// Blocks per multiprocessor the register allocation is sized for.  The plain SRT and TRT
+// step of the 32- and 16-bit formats: 36 warps (56 registers a thread; measured 1-6 %
+// faster than 32 warps at 64 registers, and 40 warps spill).  MRT and the reducing and
+// interpolated-wall variants keep 32 warps (64 registers), where 56 would spill (MRT at 56
+// spills 136 bytes and ran 3 % slower).  FP64: 8 warps.
 #ifndef LBM_STEP_WARPS_PER_SM
 #define LBM_STEP_WARPS_PER_SM 36
 #endif
-template <int STORE, bool RED, bool WX> constexpr int step_min_blocks()
+template <int STORE, int COLL, bool RED, bool WX> constexpr int step_min_blocks()
 {
-    return (STORE == ST_F64 ? 8 : (RED || WX) ? 32 : LBM_STEP_WARPS_PER_SM) / kStepWarps;
+    return (STORE == ST_F64 ? 8 : (RED || WX || COLL == COLL_MRT) ? 32 : LBM_STEP_WARPS_PER_SM) / kStepWarps;
 }
 
 // Moments of the incoming populations (Eq. Macro), in deviation form.
@@ -328,8 +339,8 @@ __device__ __forceinline__ void finish_cell(const InstanceDev &I, R (&g)[Q], con
                 else if (cq != R(0)) v = fma_r(cq, g[kb], v);
                 if constexpr (RED) C = S::load(fs + ((uint32_t)kb * KS + cell), P.isc);
             } else {
-                C = S::load(fs + ((uint32_t)k * KS + cell), P.isc);  // own g~_kbar(x)
-                const R B = cq != R(0) ? S::load(linkB + l, P.isc) : R(0);
+                C = S::cvt(ld_pop<KIND>(fs + ((uint32_t)k * KS + cell)), P.isc);  // own g~_kbar(x)
+                const R B = cq != R(0) ? S::cvt(ld_pop<KIND>(linkB + l), P.isc) : R(0);
                 v = wall_own_part(P.wall, cq, C, B);
                 if (cq != R(0)) v = fma_r(cq, g[kb], v);
             }
@@ -487,7 +498,7 @@ __device__ __forceinline__ void pull_item(const InstanceDev &I, const Par<R> &P,
             if (ex(k) == 1) idx += cxm;   // x - 1 wraps to the end of the row
             if (ex(k) == -1) idx -= cxp;  // x + 1 wraps to the start of the row
             const uint32_t d = KIND == KIND_AA_PULL ? (uint32_t)opp(k) : (uint32_t)k;
-            raw[k] = checked(I, idx - d * P.ks, I.n32) ? __ldg(fs + idx) : typename Store<STORE>::T{};
+            raw[k] = checked(I, idx - d * P.ks, I.n32) ? ld_pop<KIND>(fs + idx) : typename Store<STORE>::T{};
         }
     } else {
         const Coord co = coord_of(P, it.cell);
@@ -498,7 +509,7 @@ __device__ __forceinline__ void pull_item(const InstanceDev &I, const Par<R> &P,
             else if constexpr (KIND == KIND_AA_PULL) idx = (uint32_t)opp(k) * P.ks + co.pull(k);
             else idx = (uint32_t)k * P.ks + co.pull(k);
             const uint32_t d = KIND == KIND_AA_PULL ? (uint32_t)opp(k) : (uint32_t)k;
-            raw[k] = checked(I, idx - d * P.ks, I.n32) ? __ldg(fs + idx) : typename Store<STORE>::T{};
+            raw[k] = checked(I, idx - d * P.ks, I.n32) ? ld_pop<KIND>(fs + idx) : typename Store<STORE>::T{};
         }
     }
 }
@@ -604,7 +615,7 @@ __device__ __forceinline__ const InstanceDev &instance_of(const InstanceDev *tab
 // other steps carry none of that code.  The WX variant (A-B only) also runs the
 // interpolated wall rules LIBB, QIBB, IEBB and MR.
 template <int COLL, int STORE, int KIND, bool BATCH, bool RED, bool WX>
-__global__ void __launch_bounds__(kStepWarps * 32, step_min_blocks<STORE, RED, WX>())
+__global__ void __launch_bounds__(kStepWarps * 32, step_min_blocks<STORE, COLL, RED, WX>())
     step_kernel(const InstanceDev *__restrict__ table, const __grid_constant__ InstanceDev one,
                 const TileDev *__restrict__ tiles, int ntiles, int flip, unsigned *__restrict__ status)
 {

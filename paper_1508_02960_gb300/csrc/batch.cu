@@ -237,6 +237,8 @@ Batch::~Batch()
     if (cap_) cudaStreamDestroy(cap_);
     cudaFree(d_sstage_[0]);
     cudaFree(d_sstage_[1]);
+    cudaFree(d_fscratch_);
+    cudaFree(d_fcount_);
     if (copy_) cudaStreamDestroy(copy_);
     for (cudaEvent_t e : ev_)
         if (e) cudaEventDestroy(e);
@@ -529,6 +531,10 @@ lbm_status Batch::rebuild()
     if (n > capacity_) {
         cudaFree(d_sums_);
         cudaFree(d_status_);
+        cudaFree(d_fscratch_);
+        cudaFree(d_fcount_);
+        d_fscratch_ = nullptr;
+        d_fcount_ = nullptr;
         if (h_sums_) cudaFreeHost(h_sums_);
         if (h_status_) cudaFreeHost(h_status_);
         d_sums_ = nullptr;
@@ -539,6 +545,9 @@ lbm_status Batch::rebuild()
         CK(dev_alloc(&d_sums_, sizeof(double) * kRedSlots * capacity_));
         CK(dev_alloc(&d_status_, sizeof(unsigned) * capacity_));
         CK(cudaMemset(d_status_, 0, sizeof(unsigned) * capacity_));
+        CK(dev_alloc(&d_fscratch_, sizeof(double) * (RED_F + 3) * kFinalSlices * capacity_));
+        CK(dev_alloc(&d_fcount_, sizeof(unsigned) * capacity_));
+        CK(cudaMemset(d_fcount_, 0, sizeof(unsigned) * capacity_));
         CK(cudaMallocHost(&h_sums_, sizeof(double) * kRedSlots * capacity_));
         CK(cudaMallocHost(&h_status_, sizeof(unsigned) * capacity_));
     }
@@ -588,6 +597,8 @@ struct StepQueue {
     const int *tile_begin, *tile_count;
     double *sums;
     int n_inst;
+    double *fscratch;
+    unsigned *fcount;
 };
 
 // Queue n steps on stream s starting from (flip, aa); returns launches queued.
@@ -617,7 +628,7 @@ static cudaError_t queue_steps(const StepQueue &q, cudaStream_t s, long long n, 
         else aa ^= 1;
     }
     if (reduce_last && n > 0) {
-        cudaError_t e = launch_final_reduce(q.L.table, q.tile_begin, q.tile_count, q.n_inst, q.sums, s);
+        cudaError_t e = launch_final_reduce(q.L.table, q.tile_count, q.n_inst, q.sums, q.fscratch, q.fcount, s);
         if (e != cudaSuccess) return e;
         ++launches;
     }
@@ -637,7 +648,7 @@ lbm_status Batch::step(long long n)
     for (auto &p : inst_) wx |= p->desc.wall >= LBM_LIBB;
     StepQueue q{&ops(), Launch{d_table_, d_stiles_, nstiles_, kTileSegs, grid_, kStepWarps * 32, stream_},
                 size() == 1 ? &h_table_[0] : nullptr, wx, tma_ ? &tma_launch_ : nullptr, collision_, layout_,
-                d_status_, size(), d_stile_begin_, d_stile_count_, d_sums_, size()};
+                d_status_, size(), d_stile_begin_, d_stile_count_, d_sums_, size(), d_fscratch_, d_fcount_};
     const long long kChunk = 1000;
     long long left = n;
     while (left > 0) {
@@ -724,7 +735,8 @@ lbm_status Batch::moment_sums_now(int i, double *sums)
     CK(ops().moments(L, layout_, cur_of(in), aa_phase_, 1, 0, nullptr));
     double *ds = d_sums_ + (size_t)kRedSlots * i;
     double *hs = h_sums_ + (size_t)kRedSlots * i;
-    CK(launch_final_reduce(d_table_ + i, d_tile_begin_ + i, d_tile_count_ + i, 1, ds, stream_));
+    CK(launch_final_reduce(d_table_ + i, d_tile_count_ + i, 1, ds, d_fscratch_ + (size_t)i * kFinalSlices * (RED_F + 3),
+                           d_fcount_ + i, stream_));
     launches_ += 2;
     CK(cudaMemcpyAsync(hs, ds, sizeof(double) * 4, cudaMemcpyDeviceToHost, stream_));
     CK(cudaStreamSynchronize(stream_));

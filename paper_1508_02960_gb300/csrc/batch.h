@@ -125,6 +125,9 @@ private:
     // state transfers: two staging buffers of one direction each, a copy stream, and
     // events: ev_[b] buffer b filled, ev_[2 + b] buffer b free again
     void *d_sstage_[2] = {nullptr, nullptr};
+    // final reduction: per instance kFinalSlices rows of partial sums and a block counter
+    double *d_fscratch_ = nullptr;
+    unsigned *d_fcount_ = nullptr;
     size_t sstage_bytes_ = 0;
     cudaStream_t copy_ = nullptr;
     cudaEvent_t ev_[4] = {nullptr, nullptr, nullptr, nullptr};

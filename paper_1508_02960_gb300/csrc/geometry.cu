@@ -643,33 +643,57 @@ cudaError_t export_wall_distances(const GeometryDev &g, int kdir, double *qk, cu
 }
 
 // ---- deterministic final reduction of tile partials ---------------------------------------
-__global__ void final_reduce_kernel(const InstanceDev *__restrict__ table, const int *__restrict__ tile_begin,
-                                    const int *__restrict__ tile_count, double *__restrict__ out)
+// kFinalSlices blocks per instance each sum one fixed, contiguous range of the instance's
+// tile partials (strided over the threads, then a fixed tree) into scratch; the last of
+// them to finish (the instance's counter) adds the slices in order into out and resets the
+// counter.  The result depends only on the partials and their count, never on timing;
+// spreading the FP64 additions over many SMs matters on GB300, whose FP64 rate made one
+// block per instance the cost of the check.
+__global__ void final_reduce_kernel(const InstanceDev *__restrict__ table, const int *__restrict__ tile_count,
+                                    double *__restrict__ out, double *__restrict__ scratch,
+                                    unsigned *__restrict__ counter)
 {
     constexpr int D = RED_F + 3;  // slots in use
     __shared__ double sm[256][D];
-    const int inst = blockIdx.x;
+    __shared__ bool last;
+    const int inst = blockIdx.x / kFinalSlices, slice = blockIdx.x % kFinalSlices;
     const double *p = table[inst].partials;
     const int nt = tile_count[inst];
-    (void)tile_begin;
+    const int per = (nt + kFinalSlices - 1) / kFinalSlices;
+    const int t0 = slice * per, t1 = min(nt, t0 + per);
     double a[D];
     for (int d = 0; d < D; ++d) a[d] = 0.0;
-    for (int t = threadIdx.x; t < nt; t += blockDim.x)
+    for (int t = t0 + (int)threadIdx.x; t < t1; t += blockDim.x)
         for (int d = 0; d < D; ++d) a[d] += p[(long long)t * kRedSlots + d];
     for (int d = 0; d < D; ++d) sm[threadIdx.x][d] = a[d];
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w)
+        if ((int)threadIdx.x < w)
             for (int d = 0; d < D; ++d) sm[threadIdx.x][d] += sm[threadIdx.x + w][d];
         __syncthreads();
     }
-    if (threadIdx.x < kRedSlots) out[(long long)inst * kRedSlots + threadIdx.x] = threadIdx.x < D ? sm[0][threadIdx.x] : 0.0;
+    double *row = scratch + ((long long)inst * kFinalSlices + slice) * D;
+    if (threadIdx.x < D) row[threadIdx.x] = sm[0][threadIdx.x];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&counter[inst], 1u) == (unsigned)kFinalSlices - 1u;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < kRedSlots) {
+        double sum = 0.0;
+        if (threadIdx.x < D)
+            for (int k = 0; k < kFinalSlices; ++k)
+                sum += __ldcg(scratch + ((long long)inst * kFinalSlices + k) * D + threadIdx.x);
+        out[(long long)inst * kRedSlots + threadIdx.x] = sum;
+    }
+    if (threadIdx.x == 0) counter[inst] = 0u;
 }
 
-cudaError_t launch_final_reduce(const InstanceDev *table, const int *tile_begin, const int *tile_count, int n_inst,
-                                double *out, cudaStream_t s)
+cudaError_t launch_final_reduce(const InstanceDev *table, const int *tile_count, int n_inst, double *out,
+                                double *scratch, unsigned *counter, cudaStream_t s)
 {
-    final_reduce_kernel<<<n_inst, 256, 0, s>>>(table, tile_begin, tile_count, out);
+    final_reduce_kernel<<<n_inst * kFinalSlices, 256, 0, s>>>(table, tile_count, out, scratch, counter);
     return cudaGetLastError();
 }
 

@@ -295,8 +295,8 @@ __global__ void state_scatter_kernel(const InstanceDev *__restrict__ table, int 
 // Moments of the stored post-collision state of every fluid cell, one warp per work
 // chunk.  mode 0: write the velocity component `comp` to out[cell] of fluid cells (the
 // caller clears out first).  mode 1: chunk partial sums (drho, u_x, u_y, u_z) into
-// I.partials, in the same fixed order as the step kernel's; the force slots, which only a
-// step defines, are written as 0.
+// I.partials, in FP64 in a fixed order; the force slots, which only a step defines, are
+// written as 0.
 template <int STORE>
 __global__ void __launch_bounds__(256) moments_kernel(const InstanceDev *__restrict__ table,
                                                       const TileDev *__restrict__ chunks, int nchunks, int chunk_segs,

@@ -115,10 +115,13 @@ void free_geometry(GeometryDev *g);
 // Scatter link q values into qk[ncells] for link direction kdir (NaN elsewhere).
 cudaError_t export_wall_distances(const GeometryDev &g, int kdir, double *qk, cudaStream_t s);
 
-// Deterministic final sum of an instance's tile partials: out[kRedSlots] = sum over
-// tiles t0 .. t0+nt-1 of partials[t][...], in a fixed order.  One block per instance.
-cudaError_t launch_final_reduce(const InstanceDev *table, const int *tile_begin, const int *tile_count,
-                                int n_inst, double *out, cudaStream_t s);
+// Deterministic final sum of each instance's tile partials: out[kRedSlots] = the sum over
+// its tile_count tiles of partials[t][...], in a fixed order.  kFinalSlices blocks per
+// instance; scratch: kFinalSlices * (RED_F + 3) doubles and counter: one zeroed word per
+// instance (the kernel leaves it zero again).
+constexpr int kFinalSlices = 32;
+cudaError_t launch_final_reduce(const InstanceDev *table, const int *tile_count, int n_inst, double *out,
+                                double *scratch, unsigned *counter, cudaStream_t s);
 
 // Error helpers
 void set_error(const std::string &msg);

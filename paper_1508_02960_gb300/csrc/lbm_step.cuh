@@ -109,6 +109,40 @@ template <typename R> __device__ __forceinline__ Coord coord_of(const Par<R> &p,
     return c;
 }
 
+// The static tables a step reads (work list, boundary table, CLI coefficients) are small
+// next to the populations streaming through L2 every step; they are loaded with an
+// evict-last L2 policy so that they stay resident from one step to the next.
+__device__ __forceinline__ uint64_t l2_keep_policy()
+{
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint32_t ld_keep(const uint32_t *a, uint64_t pol)
+{
+    uint32_t v;
+    asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float ld_keep(const float *a, uint64_t pol)
+{
+    float v;
+    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double ld_keep(const double *a, uint64_t pol)
+{
+    double v;
+    asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ uint2 ld_keep(const uint2 *a, uint64_t pol)
+{
+    uint2 v;
+    asm("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(a), "l"(pol));
+    return v;
+}
+
 // Blocks per multiprocessor the register allocation is sized for.  The plain SRT and TRT
 // step of the 32- and 16-bit formats: 36 warps (56 registers a thread; measured 1-6 %
 // faster than 32 warps at 64 registers, and 40 warps spill).  MRT and the reducing and
@@ -330,7 +364,7 @@ __device__ __forceinline__ void finish_cell(const InstanceDev &I, R (&g)[Q], con
             if (!((wm >> k) & 1u)) continue;
             const int kb = opp(k);
             const uint32_t l = off + __popc(wm & ((1u << k) - 1u));
-            const R cq = P.wall == 1 ? linkc[l] : R(0);
+            const R cq = P.wall == 1 ? ld_keep(linkc + l, l2_keep_policy()) : R(0);
             R v, C;
             if constexpr (KIND == KIND_AB) {
                 v = g[k];  // S, left by the previous step in the solid slot
@@ -415,7 +449,7 @@ __device__ __forceinline__ void finish_cell(const InstanceDev &I, R (&g)[Q], con
                 if (WX && P.wall >= 2) {
                     sv = wall_own_part_w(P, linkw + (size_t)l * kLinkW, k, g, drho, ux, uy, uz);
                 } else {
-                    const R cq = P.wall == 1 ? linkc[l] : R(0);
+                    const R cq = P.wall == 1 ? ld_keep(linkc + l, l2_keep_policy()) : R(0);
                     sv = wall_own_part(P.wall, cq, g[opp(k)], g[k]);
                 }
                 uint32_t idx;
@@ -457,9 +491,10 @@ struct WarpItem {
 template <typename R>
 __device__ __forceinline__ void locate_item(const InstanceDev &I, const Par<R> &P, uint32_t w, int lane, WarpItem &it)
 {
+    const uint64_t keep = l2_keep_policy();
     const bool w_ok = checked(I, w, I.n_fwarps_padded);
-    it.wd = w_ok ? I.fwarp[w] : make_uint2(0u, 0u);
-    it.cell = w_ok ? I.fcell[w * 32u + (uint32_t)lane] : 0xFFFFFFFFu;
+    it.wd = w_ok ? ld_keep(I.fwarp + w, keep) : make_uint2(0u, 0u);
+    it.cell = w_ok ? ld_keep(I.fcell + (w * 32u + (uint32_t)lane), keep) : 0xFFFFFFFFu;
     if (it.cell != 0xFFFFFFFFu && !checked(I, it.cell, I.n32)) it.cell = 0xFFFFFFFFu;
     const bool live = it.cell != 0xFFFFFFFFu;
     const uint32_t yz = fast_div(it.cell, P.dnx);
@@ -473,8 +508,8 @@ __device__ __forceinline__ void locate_item(const InstanceDev &I, const Par<R> &
     if ((it.wd.x >> lane) & 1u) {
         const uint32_t b = it.wd.y + __popc(it.wd.x & ((1u << lane) - 1u));
         if (checked(I, b, I.n_boundary)) {
-            it.wm = I.bmask[b];
-            it.off = I.boff[b];
+            it.wm = ld_keep(I.bmask + b, keep);
+            it.off = ld_keep(I.boff + b, keep);
             // every link of the cell within the link tables
             if (!checked(I, it.off + __popc(it.wm), I.n_links + 1u)) it.wm = 0u;
         }
@@ -514,9 +549,9 @@ __device__ __forceinline__ void pull_item(const InstanceDev &I, const Par<R> &P,
     }
 }
 
-// Per-lane FP64 accumulators of the reduction (RED steps).
-struct RedAcc {
-    double v[RED_F + 3];
+// Per-lane values of the reduction (RED steps) in the compute type: one cell a lane.
+template <typename R> struct RedAcc {
+    R v[RED_F + 3];
 };
 
 // Finish one work item pulled by pull_item: convert, pressure shift of the pulls that
@@ -526,7 +561,7 @@ template <int COLL, int STORE, int KIND, bool RED, bool WX, typename R>
 __device__ __forceinline__ void finish_item(const InstanceDev &I, const Par<R> &P, const R *rates,
                                             const typename Store<STORE>::T (&raw)[Q], const WarpItem &it, int lane,
                                             const typename Store<STORE>::T *fs, typename Store<STORE>::T *fd,
-                                            unsigned *status, RedAcc &acc)
+                                            unsigned *status, RedAcc<R> &acc)
 {
     using S = Store<STORE>;
     using T = typename S::T;
@@ -555,24 +590,59 @@ __device__ __forceinline__ void finish_item(const InstanceDev &I, const Par<R> &
                                                reinterpret_cast<const R *>(I.linkw), reinterpret_cast<T *>(I.linkB),
                                                status, rd, rx, ry, rz, fm);
     if constexpr (RED) {
-        acc.v[RED_DRHO] += (double)rd;
-        acc.v[RED_U + 0] += (double)rx;
-        acc.v[RED_U + 1] += (double)ry;
-        acc.v[RED_U + 2] += (double)rz;
+        acc.v[RED_DRHO] = rd;
+        acc.v[RED_U + 0] = rx;
+        acc.v[RED_U + 1] = ry;
+        acc.v[RED_U + 2] = rz;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) acc.v[RED_F + d] += (double)fm[d];
+        for (int d = 0; d < 3; ++d) acc.v[RED_F + d] = fm[d];
     }
 }
 
-// Block sum of the lanes' accumulators of one tile (fixed shuffle tree, then the warps in
-// order) to partials[tile]; every thread of the block calls it.
-__device__ __forceinline__ void reduce_tile(const RedAcc &acc, double *partials, long long tile)
+// Error-free sum (Knuth's TwoSum): s + e == a + b exactly, s = fl(a + b).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Warp sum of float-float values hi + lo (fixed butterfly; every lane ends with the same
+// pair, the exact TwoSum error being unique).  Each addition keeps its rounding error, so
+// hi + lo is the sum to about 2^-48 of the magnitudes added, close to an FP64 sum, on the
+// FP32 pipes (GB300's FP64 rate made the FP64 butterfly the cost of the reducing step).
+__device__ __forceinline__ void warp_sum_ff(float &hi, float &lo)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        float sh, se;
+        two_sum(hi, h2, sh, se);
+        se = __fadd_rn(se, __fadd_rn(lo, l2));
+        two_sum(sh, se, hi, lo);
+    }
+}
+
+// Block sum of the lanes' values of one tile (fixed shuffle tree, then the warps in order)
+// to partials[tile] in FP64; every thread of the block calls it.  FP64 lanes sum in FP64;
+// FP32 lanes sum in float-float within the warp, then in FP64.
+template <typename R>
+__device__ __forceinline__ void reduce_tile(const RedAcc<R> &acc, double *partials, long long tile)
 {
     __shared__ double red[kStepWarps][RED_F + 3];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double v[RED_F + 3];
 #pragma unroll
-    for (int d = 0; d < RED_F + 3; ++d) v[d] = warp_sum(acc.v[d]);
+    for (int d = 0; d < RED_F + 3; ++d) {
+        if constexpr (sizeof(R) == sizeof(double)) {
+            v[d] = warp_sum((double)acc.v[d]);
+        } else {
+            float hi = (float)acc.v[d], lo = 0.0f;
+            warp_sum_ff(hi, lo);
+            v[d] = (double)hi + (double)lo;
+        }
+    }
     if (lane == 0)
 #pragma unroll
         for (int d = 0; d < RED_F + 3; ++d) red[warp][d] = v[d];
@@ -646,7 +716,7 @@ __global__ void __launch_bounds__(kStepWarps * 32, step_min_blocks<STORE, COLL, 
     wait_previous_step();
     T raw[Q];
     pull_item<STORE, KIND, R>(I, P, fs, it, raw);
-    RedAcc acc{};
+    RedAcc<R> acc{};
     finish_item<COLL, STORE, KIND, RED, WX, R>(I, P, rates, raw, it, lane, fs, fd, status + tile.inst, acc);
     if constexpr (RED) reduce_tile(acc, I.partials, tile.local);
 }

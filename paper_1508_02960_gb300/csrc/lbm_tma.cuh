@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kBrickCells, tma_min_blocks<STORE>())
         }
         const WarpItem now = meta;
         if (brick + (int)gridDim.x < nbricks) locate(brick + (int)gridDim.x, meta);
-        RedAcc acc{};
+        RedAcc<R> acc{};
         finish_item<COLL, STORE, KIND_AB, false, WX, R>(I, P, rates, raw, now, cx, fs, fd, nullptr, acc);
     }
 }

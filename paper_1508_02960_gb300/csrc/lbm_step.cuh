@@ -109,8 +109,8 @@ template <typename R> __device__ __forceinline__ Coord coord_of(const Par<R> &p,
     return c;
 }
 
-// The static tables a step reads (work list, boundary table, CLI coefficients) are small
-// next to the populations streaming through L2 every step; they are loaded with an
+// The static tables a step reads (work list, boundary table, wall-rule coefficients) are
+// small next to the populations streaming through L2 every step; they are loaded with an
 // evict-last L2 policy so that they stay resident from one step to the next.
 __device__ __forceinline__ uint64_t l2_keep_policy()
 {
@@ -283,6 +283,7 @@ __device__ __forceinline__ R wall_neighbour_terms(const Par<R> &P, int wall, con
 {
     using S = Store<STORE>;
     const int kb = opp(k);
+    const uint64_t keep = l2_keep_policy();
     if (wall == 3 || wall == 5) {  // QIBB, MR: P3 = g~_kbar(x_f3), B2 = g~_k(x_f2)
         int xv2, xv3;
         uint32_t c2, c3;
@@ -291,9 +292,9 @@ __device__ __forceinline__ R wall_neighbour_terms(const Par<R> &P, int wall, con
                              R(weight(k)) * P.dshift);
         const R p3 = shifted(S::load(fs + ((uint32_t)kb * P.ks + c3), P.isc), xv3, (int)P.nx,
                              R(weight(kb)) * P.dshift);
-        v = fma_r(lw[LW_ALPHA], g[kb], v);
-        v = fma_r(lw[LW_BETA], p3, v);
-        v = fma_r(lw[LW_DELTA], b2, v);
+        v = fma_r(ld_keep(lw + LW_ALPHA, keep), g[kb], v);
+        v = fma_r(ld_keep(lw + LW_BETA, keep), p3, v);
+        v = fma_r(ld_keep(lw + LW_DELTA, keep), b2, v);
     } else if (wall == 4) {  // IEBB: J2 = e_kbar . (momentum of x_f2); the shift carries none
         int xv2, xv3;
         uint32_t c2, c3;
@@ -306,9 +307,9 @@ __device__ __forceinline__ R wall_neighbour_terms(const Par<R> &P, int wall, con
             const R gm = S::load(fs + ((uint32_t)m * P.ks + c2), P.isc);
             j2 += d > 0 ? (d == 1 ? gm : R(d) * gm) : (d == -1 ? -gm : R(d) * gm);
         }
-        v = fma_r(lw[LW_ZETA], j2, v);
+        v = fma_r(ld_keep(lw + LW_ZETA, keep), j2, v);
     } else {  // LIBB
-        v = fma_r(lw[LW_ALPHA], g[kb], v);
+        v = fma_r(ld_keep(lw + LW_ALPHA, keep), g[kb], v);
     }
     return v;
 }
@@ -320,12 +321,13 @@ __device__ __forceinline__ R wall_own_part_w(const Par<R> &P, const R *lw, int k
                                              R uz)
 {
     const int kb = opp(k);
-    R sv = fma_r(lw[LW_GAMMA], g[k], lw[LW_EPS] * g[kb]);
-    const R X = lw[LW_X];
+    const uint64_t keep = l2_keep_policy();
+    R sv = fma_r(ld_keep(lw + LW_GAMMA, keep), g[k], ld_keep(lw + LW_EPS, keep) * g[kb]);
+    const R X = ld_keep(lw + LW_X, keep);
     if (X != R(0)) {
         const R eu = R(ex(kb)) * ux + R(ey(kb)) * uy + R(ez(kb)) * uz;
         const R uu = ux * ux + uy * uy + uz * uz;
-        const R fst = drho + P.rho0 * (lw[LW_THETA] * eu + R(4.5) * eu * eu - R(1.5) * uu);
+        const R fst = drho + P.rho0 * (ld_keep(lw + LW_THETA, keep) * eu + R(4.5) * eu * eu - R(1.5) * uu);
         sv = fma_r(X * R(weight(kb)), fst, sv);
     }
     return sv;

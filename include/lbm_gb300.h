@@ -302,6 +302,18 @@ LBM_API lbm_status lbm_set_populations_f64(lbm_ctx *ctx, const double *host_in);
 LBM_API lbm_status lbm_get_state(lbm_ctx *ctx, void *host_out, size_t bytes);
 LBM_API lbm_status lbm_set_state(lbm_ctx *ctx, const void *host_in, size_t bytes);
 
+/* Prefetched state input, for streams of states: lbm_stage_state starts the copy of
+ * host_in (lbm_set_state's layout and size) into one of two device staging buffers, on a
+ * copy stream of the context's own, and returns at once.  The copy can then overlap the
+ * steps queued meanwhile.  host_in must stay unchanged until the lbm_apply_staged_state
+ * that consumes it has returned (pinned memory, or the copy is not asynchronous).  At most
+ * two states are staged: a third call returns LBM_ERR_STATE.  Wrong bytes: LBM_ERR_ARG.
+ * lbm_apply_staged_state makes the oldest staged state the current state, as
+ * lbm_set_state does.  It is queued on the context's stream after that state's copy and
+ * returns without waiting.  With nothing staged it returns LBM_ERR_STATE. */
+LBM_API lbm_status lbm_stage_state(lbm_ctx *ctx, const void *host_in, size_t bytes);
+LBM_API lbm_status lbm_apply_staged_state(lbm_ctx *ctx);
+
 /* Velocity u = rho0^-1 sum e_k f_k of the stored state, FP64 [3][nz][ny][nx] (0 in solid). */
 LBM_API lbm_status lbm_get_velocity_f64(lbm_ctx *ctx, double *host_out);
 /* Solid flags [nz][ny][nx] (1 = solid) as built on the device. */

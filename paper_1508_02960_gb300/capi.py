@@ -144,6 +144,8 @@ PROTOTYPES = {
     "lbm_set_populations_f64": (_st, [_vp, _dp]),
     "lbm_get_state": (_st, [_vp, _vp, ctypes.c_size_t]),
     "lbm_set_state": (_st, [_vp, _vp, ctypes.c_size_t]),
+    "lbm_stage_state": (_st, [_vp, _vp, ctypes.c_size_t]),
+    "lbm_apply_staged_state": (_st, [_vp]),
     "lbm_get_velocity_f64": (_st, [_vp, _dp]),
     "lbm_get_flags": (_st, [_vp, ctypes.POINTER(ctypes.c_uint8)]),
     "lbm_get_wall_distances": (_st, [_vp, _dp]),
@@ -389,6 +391,18 @@ class Context:
         s = np.ascontiguousarray(s)
         assert s.dtype == self.state_dtype()
         check(lib().lbm_set_state(self._h, s.ctypes.data, s.nbytes), "lbm_set_state")
+
+    def stage_state(self, s):
+        """Start copying a state (get_state's layout) into a staging buffer and return
+        (lbm_stage_state); s must stay unchanged, and referenced, until the
+        apply_staged_state that consumes it has returned.  Returns s."""
+        assert s.dtype == self.state_dtype() and s.flags.c_contiguous
+        check(lib().lbm_stage_state(self._h, s.ctypes.data, s.nbytes), "lbm_stage_state")
+        return s
+
+    def apply_staged_state(self):
+        """Make the oldest staged state current, queued on the stream (lbm_apply_staged_state)."""
+        check(lib().lbm_apply_staged_state(self._h), "lbm_apply_staged_state")
 
     def get_velocity(self) -> np.ndarray:
         u = np.empty((3,) + self.shape)

@@ -235,8 +235,15 @@ Batch::~Batch()
     if (h_sums_) cudaFreeHost(h_sums_);
     if (h_status_) cudaFreeHost(h_status_);
     if (cap_) cudaStreamDestroy(cap_);
+    if (copy_) cudaStreamSynchronize(copy_);  // no copy still reads a caller's buffer
     cudaFree(d_sstage_[0]);
     cudaFree(d_sstage_[1]);
+    cudaFree(d_pstage_[0]);
+    cudaFree(d_pstage_[1]);
+    for (int b = 0; b < 2; ++b) {
+        if (ev_staged_[b]) cudaEventDestroy(ev_staged_[b]);
+        if (ev_free_[b]) cudaEventDestroy(ev_free_[b]);
+    }
     cudaFree(d_fscratch_);
     cudaFree(d_fcount_);
     if (copy_) cudaStreamDestroy(copy_);
@@ -814,9 +821,8 @@ lbm_status Batch::state_io(int i, void *host, size_t bytes, bool to_host)
     if (bytes != (size_t)Q * dir_bytes) return fail(LBM_ERR_ARG, "state buffer must hold 19 * n_fluid elements");
     if (!to_host && layout_ == LBM_LAYOUT_AA) aa_phase_ = 0;
     if (nf > 0) {
-        if (!copy_) CK(cudaStreamCreateWithFlags(&copy_, cudaStreamNonBlocking));
-        for (cudaEvent_t &e : ev_)
-            if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        lbm_status cs = ensure_copy_stream();
+        if (cs != LBM_OK) return cs;
         if (sstage_bytes_ < dir_bytes) {
             cudaFree(d_sstage_[0]);
             cudaFree(d_sstage_[1]);
@@ -863,6 +869,83 @@ lbm_status Batch::state_io(int i, void *host, size_t bytes, bool to_host)
     in.have_force = false;
     in.sums_pending = false;
     CK(cudaStreamSynchronize(stream_));
+    return LBM_OK;
+}
+
+lbm_status Batch::ensure_copy_stream()
+{
+    if (!copy_) CK(cudaStreamCreateWithFlags(&copy_, cudaStreamNonBlocking));
+    for (cudaEvent_t &e : ev_)
+        if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    for (int b = 0; b < 2; ++b) {
+        if (!ev_staged_[b]) CK(cudaEventCreateWithFlags(&ev_staged_[b], cudaEventDisableTiming));
+        if (!ev_free_[b]) CK(cudaEventCreateWithFlags(&ev_free_[b], cudaEventDisableTiming));
+    }
+    return LBM_OK;
+}
+
+lbm_status Batch::stage_state(int i, const void *host, size_t bytes)
+{
+    if (i < 0 || i >= size() || !host) return fail(LBM_ERR_ARG, "bad instance index or NULL buffer");
+    const Instance &in = *inst_[i];
+    const size_t total = (size_t)Q * (size_t)in.geo.n_fluid * storage_bytes(storage_);
+    if (bytes != total) return fail(LBM_ERR_ARG, "state buffer must hold 19 * n_fluid elements");
+    if (n_staged_ == 2) return fail(LBM_ERR_STATE, "two states are staged already: apply one first");
+    lbm_status cs = ensure_copy_stream();
+    if (cs != LBM_OK) return cs;
+    if (pstage_bytes_ < total) {
+        if (n_staged_ > 0) return fail(LBM_ERR_STATE, "a staged state of another size is pending");
+        CK(cudaStreamSynchronize(stream_));  // no scatter still reads the old buffers
+        cudaFree(d_pstage_[0]);
+        cudaFree(d_pstage_[1]);
+        d_pstage_[0] = d_pstage_[1] = nullptr;
+        pstage_bytes_ = 0;
+        pstage_used_[0] = pstage_used_[1] = false;
+        CK(dev_alloc(&d_pstage_[0], total));
+        CK(dev_alloc(&d_pstage_[1], total));
+        pstage_bytes_ = total;
+    }
+    const int b = (head_ + n_staged_) & 1;
+    if (pstage_used_[b]) CK(cudaStreamWaitEvent(copy_, ev_free_[b], 0));  // its last scatter is done
+    if (total > 0) CK(cudaMemcpyAsync(d_pstage_[b], host, total, cudaMemcpyHostToDevice, copy_));
+    CK(cudaEventRecord(ev_staged_[b], copy_));
+    staged_inst_[b] = i;
+    ++n_staged_;
+    return LBM_OK;
+}
+
+lbm_status Batch::apply_staged_state(int i)
+{
+    if (i < 0 || i >= size()) return fail(LBM_ERR_ARG, "bad instance index");
+    if (n_staged_ == 0) return fail(LBM_ERR_STATE, "no state is staged");
+    const int b = head_;
+    if (staged_inst_[b] != i) return fail(LBM_ERR_STATE, "the oldest staged state belongs to another instance");
+    if (dirty_) {
+        lbm_status st = rebuild();
+        if (st != LBM_OK) return st;
+    }
+    Instance &in = *inst_[i];
+    const long long nf = in.geo.n_fluid;
+    const size_t dir_bytes = (size_t)nf * storage_bytes(storage_);
+    if (layout_ == LBM_LAYOUT_AA) aa_phase_ = 0;
+    CK(cudaStreamWaitEvent(stream_, ev_staged_[b], 0));
+    const int cur = cur_of(in);
+    for (int k = 0; k < Q && nf > 0; ++k) {
+        CK(ops().state_dir(d_table_, i, nf, layout_, cur, aa_phase_, k,
+                           static_cast<char *>(d_pstage_[b]) + k * dir_bytes, 0, stream_));
+        ++launches_;
+    }
+    if (layout_ == LBM_LAYOUT_AB && in.geo.n_boundary > 0) {
+        CK(ops().wall_prepare(d_table_, i, in.geo.n_boundary, in.geo.bcell, cur, stream_));
+        ++launches_;
+    }
+    CK(cudaEventRecord(ev_free_[b], stream_));
+    pstage_used_[b] = true;
+    head_ = (head_ + 1) & 1;
+    --n_staged_;
+    in.have_sums = false;
+    in.have_force = false;
+    in.sums_pending = false;
     return LBM_OK;
 }
 

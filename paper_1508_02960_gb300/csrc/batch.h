@@ -58,6 +58,9 @@ public:
     lbm_status set_f64(int i, const double *host);
     // fluid-cell state in the storage type, bit for bit ([19][n_fluid]; see lbm_get_state)
     lbm_status state_io(int i, void *host, size_t bytes, bool to_host);
+    // prefetched states ([19][n_fluid] each): copy into staging now, apply later
+    lbm_status stage_state(int i, const void *host, size_t bytes);
+    lbm_status apply_staged_state(int i);
     lbm_status get_velocity(int i, double *host);
     lbm_status get_flags(int i, uint8_t *host);
     lbm_status get_q(int i, double *host);
@@ -131,6 +134,14 @@ private:
     size_t sstage_bytes_ = 0;
     cudaStream_t copy_ = nullptr;
     cudaEvent_t ev_[4] = {nullptr, nullptr, nullptr, nullptr};
+    // prefetched states: two full staging buffers used in turn; ev_staged_[b] copy into b
+    // done, ev_free_[b] the scatter out of b done; n_staged_ states waiting from slot head_
+    void *d_pstage_[2] = {nullptr, nullptr};
+    size_t pstage_bytes_ = 0;
+    cudaEvent_t ev_staged_[2] = {nullptr, nullptr}, ev_free_[2] = {nullptr, nullptr};
+    bool pstage_used_[2] = {false, false};
+    int n_staged_ = 0, head_ = 0, staged_inst_[2] = {0, 0};
+    lbm_status ensure_copy_stream();
 };
 
 lbm_status fail(lbm_status st, const std::string &msg);

@@ -364,6 +364,18 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *host_in, size_t bytes)
     return ctx->b.state_io(0, const_cast<void *>(host_in), bytes, false);
 }
 
+lbm_status lbm_stage_state(lbm_ctx *ctx, const void *host_in, size_t bytes)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "ctx is NULL");
+    return ctx->b.stage_state(0, host_in, bytes);
+}
+
+lbm_status lbm_apply_staged_state(lbm_ctx *ctx)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "ctx is NULL");
+    return ctx->b.apply_staged_state(0);
+}
+
 lbm_status lbm_get_velocity_f64(lbm_ctx *ctx, double *host_out)
 {
     if (!ctx) return fail(LBM_ERR_ARG, "ctx is NULL");

@@ -94,3 +94,35 @@ def test_pinned_buffers_and_size_check(capi):
         ctx.set_state(pinned)
         assert capi.lib().lbm_set_state(ctx.handle, pinned.ctypes.data, pinned.nbytes - 4) == capi.ERR_ARG
         assert capi.lib().lbm_get_state(ctx.handle, pinned.ctypes.data, pinned.nbytes + 4) == capi.ERR_ARG
+
+
+@pytest.mark.parametrize("layout", ["AB", "AA"])
+def test_staged_states_apply_in_order(capi, layout):
+    """Two states staged ahead are applied in order; each applied state steps exactly as the
+    same state set with set_state; a third stage and an apply with nothing staged are refused."""
+    with _ctx(capi, "F32", layout, "CLI") as a:
+        a.init_equilibrium()
+        a.step(5)
+        s1 = a.get_state()
+        a.step(7)
+        s2 = a.get_state()
+    with _ctx(capi, "F32", layout, "CLI") as b, _ctx(capi, "F32", layout, "CLI") as c:
+        b.stage_state(s1)
+        b.stage_state(s2)
+        with pytest.raises(capi.LBMError) as e:
+            b.stage_state(s1)
+        assert e.value.status == capi.ERR_STATE
+        b.apply_staged_state()
+        b.step(3)
+        c.set_state(s1)
+        c.step(3)
+        assert np.array_equal(b.get_state(), c.get_state())
+        assert b.observables()["U_sup"] == c.observables()["U_sup"]
+        b.apply_staged_state()
+        assert np.array_equal(b.get_state(), s2)
+        with pytest.raises(capi.LBMError) as e:
+            b.apply_staged_state()
+        assert e.value.status == capi.ERR_STATE
+        b.stage_state(s1)                                  # the buffers are reused in turn
+        b.apply_staged_state()
+        assert np.array_equal(b.get_state(), s1)

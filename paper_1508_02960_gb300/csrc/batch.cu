@@ -841,7 +841,7 @@ lbm_status Batch::state_io(int i, void *host, size_t bytes, bool to_host)
             void *st = d_sstage_[b];
             if (to_host) {
                 if (k >= 2) CK(cudaStreamWaitEvent(stream_, ev_[2 + b], 0));
-                CK(ops().state_dir(d_table_, i, nf, layout_, cur, aa_phase_, k, st, 1, stream_));
+                CK(ops().state_dir(d_table_, i, nf, layout_, cur, aa_phase_, k, 1, st, 1, stream_));
                 CK(cudaEventRecord(ev_[b], stream_));
                 CK(cudaStreamWaitEvent(copy_, ev_[b], 0));
                 CK(cudaMemcpyAsync(h + k * dir_bytes, st, dir_bytes, cudaMemcpyDeviceToHost, copy_));
@@ -851,7 +851,7 @@ lbm_status Batch::state_io(int i, void *host, size_t bytes, bool to_host)
                 CK(cudaMemcpyAsync(st, h + k * dir_bytes, dir_bytes, cudaMemcpyHostToDevice, copy_));
                 CK(cudaEventRecord(ev_[b], copy_));
                 CK(cudaStreamWaitEvent(stream_, ev_[b], 0));
-                CK(ops().state_dir(d_table_, i, nf, layout_, cur, aa_phase_, k, st, 0, stream_));
+                CK(ops().state_dir(d_table_, i, nf, layout_, cur, aa_phase_, k, 1, st, 0, stream_));
                 CK(cudaEventRecord(ev_[2 + b], stream_));
             }
             ++launches_;
@@ -926,13 +926,11 @@ lbm_status Batch::apply_staged_state(int i)
     }
     Instance &in = *inst_[i];
     const long long nf = in.geo.n_fluid;
-    const size_t dir_bytes = (size_t)nf * storage_bytes(storage_);
     if (layout_ == LBM_LAYOUT_AA) aa_phase_ = 0;
     CK(cudaStreamWaitEvent(stream_, ev_staged_[b], 0));
     const int cur = cur_of(in);
-    for (int k = 0; k < Q && nf > 0; ++k) {
-        CK(ops().state_dir(d_table_, i, nf, layout_, cur, aa_phase_, k,
-                           static_cast<char *>(d_pstage_[b]) + k * dir_bytes, 0, stream_));
+    if (nf > 0) {  // all 19 directions in one launch
+        CK(ops().state_dir(d_table_, i, nf, layout_, cur, aa_phase_, 0, Q, d_pstage_[b], 0, stream_));
         ++launches_;
     }
     if (layout_ == LBM_LAYOUT_AB && in.geo.n_boundary > 0) {

@@ -243,15 +243,17 @@ __global__ void export_kernel(const InstanceDev *__restrict__ table, int inst, i
     }
 }
 
-// The stored state of direction k of the fluid cells, bit for bit, in the storage type:
-// out[j] = the stored g~_k of fluid cell j (cells in cell order, from the work list), read
-// where the layout keeps it (as export_kernel).
+// The stored state of directions k0 + blockIdx.y of the fluid cells, bit for bit, in the
+// storage type: out[blockIdx.y * nf + j] = the stored g~_k of fluid cell j (cells in cell
+// order, from the work list), read where the layout keeps it (as export_kernel).
 template <int STORE>
 __global__ void state_gather_kernel(const InstanceDev *__restrict__ table, int inst, int layout, int cur,
-                                    int aa_phase, int k, long long nf, typename Store<STORE>::T *__restrict__ out)
+                                    int aa_phase, int k0, long long nf, typename Store<STORE>::T *__restrict__ out)
 {
     using T = typename Store<STORE>::T;
     const InstanceDev &I = table[inst];
+    const int k = k0 + (int)blockIdx.y;
+    out += (long long)blockIdx.y * nf;
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < nf;
          j += (long long)gridDim.x * blockDim.x) {
         const long long cell = I.fcell[j];
@@ -264,16 +266,18 @@ __global__ void state_gather_kernel(const InstanceDev *__restrict__ table, int i
     }
 }
 
-// The inverse for a state set from outside (as import_kernel, without conversion): direction
-// k of fluid cell j from in[j] into its slot of the step-0 arrangement; in the AA layout
-// also into the link buffer of its CLI links.  Solid cells are left alone (the A-B solid
-// slots are rebuilt by wall_prepare_kernel).
+// The inverse for a state set from outside (as import_kernel, without conversion):
+// direction k = k0 + blockIdx.y of fluid cell j from in[blockIdx.y * nf + j] into its slot
+// of the step-0 arrangement; in the AA layout also into the link buffer of its CLI links.
+// Solid cells are left alone (the A-B solid slots are rebuilt by wall_prepare_kernel).
 template <int STORE>
-__global__ void state_scatter_kernel(const InstanceDev *__restrict__ table, int inst, int layout, int cur, int k,
+__global__ void state_scatter_kernel(const InstanceDev *__restrict__ table, int inst, int layout, int cur, int k0,
                                      long long nf, const typename Store<STORE>::T *__restrict__ in)
 {
     using T = typename Store<STORE>::T;
     const InstanceDev &I = table[inst];
+    const int k = k0 + (int)blockIdx.y;
+    in += (long long)blockIdx.y * nf;
     T *f = reinterpret_cast<T *>(layout == 0 ? (cur ? I.f1 : I.f0) : I.f0);
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < nf;
          j += (long long)gridDim.x * blockDim.x) {

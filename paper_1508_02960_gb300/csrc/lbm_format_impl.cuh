@@ -195,16 +195,16 @@ cudaError_t export_dir(const InstanceDev *table, int inst, long long n, int layo
 
 template <int STORE>
 cudaError_t state_dir(const InstanceDev *table, int inst, long long nf, int layout, int cur, int aa_phase, int k,
-                      void *buf, int to_host, cudaStream_t s)
+                      int nk, void *buf, int to_host, cudaStream_t s)
 {
-    if (nf <= 0) return cudaSuccess;
+    if (nf <= 0 || nk <= 0) return cudaSuccess;
     using T = typename Store<STORE>::T;
+    const dim3 grid((unsigned)flat_grid(nf, 256), (unsigned)nk);
     if (to_host)
         state_gather_kernel<STORE>
-            <<<flat_grid(nf, 256), 256, 0, s>>>(table, inst, layout, cur, aa_phase, k, nf, static_cast<T *>(buf));
+            <<<grid, 256, 0, s>>>(table, inst, layout, cur, aa_phase, k, nf, static_cast<T *>(buf));
     else
-        state_scatter_kernel<STORE>
-            <<<flat_grid(nf, 256), 256, 0, s>>>(table, inst, layout, cur, k, nf, static_cast<const T *>(buf));
+        state_scatter_kernel<STORE><<<grid, 256, 0, s>>>(table, inst, layout, cur, k, nf, static_cast<const T *>(buf));
     return cudaGetLastError();
 }
 

@@ -62,10 +62,10 @@ struct FormatOps {
                               int k, const double *fk, cudaStream_t s);
     cudaError_t (*export_dir)(const InstanceDev *table, int inst, long long ncells, int layout, int cur,
                               int aa_phase, int k, double *fk, cudaStream_t s);
-    // fluid-cell state of direction k in the storage type: to_host = 1 gathers it into buf
-    // [n_fluid], 0 scatters it from buf (the step-0 arrangement)
+    // fluid-cell state of directions k .. k + nk - 1 in the storage type: to_host = 1
+    // gathers them into buf [nk][n_fluid], 0 scatters them from buf (the step-0 arrangement)
     cudaError_t (*state_dir)(const InstanceDev *table, int inst, long long n_fluid, int layout, int cur,
-                             int aa_phase, int k, void *buf, int to_host, cudaStream_t s);
+                             int aa_phase, int k, int nk, void *buf, int to_host, cudaStream_t s);
     cudaError_t (*moments)(const Launch &L, int layout, int cur, int aa_phase, int mode, int comp,
                            double *out);
     // TMA brick step (non-reducing, single instance, A-B); one: the instance's parameters

@@ -376,7 +376,9 @@ __device__ __forceinline__ void finish_cell(const InstanceDev &I, R (&g)[Q], con
                 if constexpr (RED) C = S::load(fs + ((uint32_t)kb * KS + cell), P.isc);
             } else {
                 C = S::cvt(ld_pop<KIND>(fs + ((uint32_t)k * KS + cell)), P.isc);  // own g~_kbar(x)
-                const R B = cq != R(0) ? S::cvt(ld_pop<KIND>(linkB + l), P.isc) : R(0);
+                // CLI's own g~_k(x), loaded beside the coefficient rather than after it (a
+                // fallback link, c = 0, multiplies it by zero; the buffer holds finite values)
+                const R B = P.wall == 1 ? S::cvt(ld_pop<KIND>(linkB + l), P.isc) : R(0);
                 v = wall_own_part(P.wall, cq, C, B);
                 if (cq != R(0)) v = fma_r(cq, g[kb], v);
             }

@@ -104,6 +104,14 @@ def test_null_arguments(L):
     assert L.lbm_create(None, None, ctypes.byref(h)) == capi.ERR_ARG
     assert L.lbm_step(None, 1) == capi.ERR_ARG
     assert L.lbm_observables(None, 0.0, None) == capi.ERR_ARG
+    buf = ctypes.create_string_buffer(16)
+    assert L.lbm_get_state(None, buf, 16) == capi.ERR_ARG
+    assert L.lbm_set_state(None, buf, 16) == capi.ERR_ARG
+    assert L.lbm_stage_state(None, buf, 16) == capi.ERR_ARG
+    assert L.lbm_apply_staged_state(None) == capi.ERR_ARG
+    assert L.lbm_debug_corrupt_worklist(None) == capi.ERR_ARG
+    assert L.lbm_server_cancel(None, 0) == capi.ERR_ARG
+    assert L.lbm_build_flags() & capi.BUILD_CHECKED == 0       # the default build
     L.lbm_destroy(None)
     L.lbm_batch_destroy(None)
     L.lbm_server_destroy(None)

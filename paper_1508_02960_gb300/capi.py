@@ -10,6 +10,7 @@ Device memory is owned by the library.  A CUDA stream handle (``int`` or a
 """
 from __future__ import annotations
 
+import collections
 import ctypes
 import os
 import threading
@@ -282,6 +283,8 @@ class Context:
         h = _vp()
         check(lib().lbm_create(ctypes.byref(desc), _stream_handle(stream), ctypes.byref(h)), "lbm_create")
         self._h = h
+        self._staged = collections.deque()   # host arrays of states staged, not yet applied
+        self._applied = []                   # applied; their copies may still be queued
 
     @property
     def handle(self):
@@ -289,8 +292,10 @@ class Context:
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
-            lib().lbm_destroy(self._h)
+            lib().lbm_destroy(self._h)  # waits for the context's copies
             self._h = None
+        self._staged = collections.deque()
+        self._applied = []
 
     def __del__(self):
         try:
@@ -326,6 +331,7 @@ class Context:
     def observables(self, K_darcy: float = 0.0) -> dict:
         o = Obs()
         st = lib().lbm_observables(self._h, float(K_darcy), ctypes.byref(o))
+        self._applied = []  # the stream has synchronised: applied states' copies are done
         if st not in (OK, ERR_DIVERGED):
             check(st, "lbm_observables")
         d = o.as_dict()
@@ -394,15 +400,20 @@ class Context:
 
     def stage_state(self, s):
         """Start copying a state (get_state's layout) into a staging buffer and return
-        (lbm_stage_state); s must stay unchanged, and referenced, until the
-        apply_staged_state that consumes it has returned.  Returns s."""
+        (lbm_stage_state).  s must stay unchanged until the apply_staged_state that
+        consumes it has returned; the context keeps a reference to it until then, so a
+        temporary (e.g. a pinned buffer's view) is not freed under the copy.  Returns s."""
         assert s.dtype == self.state_dtype() and s.flags.c_contiguous
         check(lib().lbm_stage_state(self._h, s.ctypes.data, s.nbytes), "lbm_stage_state")
+        self._staged.append(s)
         return s
 
     def apply_staged_state(self):
         """Make the oldest staged state current, queued on the stream (lbm_apply_staged_state)."""
         check(lib().lbm_apply_staged_state(self._h), "lbm_apply_staged_state")
+        # the scatter is queued behind the copy, so the host array is no longer read once
+        # the stream passes this point; the reference goes when the stream next syncs
+        self._applied.append(self._staged.popleft())
 
     def get_velocity(self) -> np.ndarray:
         u = np.empty((3,) + self.shape)
@@ -426,6 +437,7 @@ class Context:
 
     def synchronize(self):
         check(lib().lbm_synchronize(self._h), "lbm_synchronize")
+        self._applied = []
 
     def save(self, path: str):
         check(lib().lbm_save(self._h, path.encode()), "lbm_save")

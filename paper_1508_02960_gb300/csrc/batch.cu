@@ -222,10 +222,8 @@ Batch::~Batch()
     }
     cudaFree(d_table_);
     cudaFree(d_tiles_);
-    cudaFree(d_tile_begin_);
     cudaFree(d_tile_count_);
     cudaFree(d_stiles_);
-    cudaFree(d_stile_begin_);
     cudaFree(d_stile_count_);
     cudaFree(d_bricks_);
     cudaFree(d_error_);
@@ -484,7 +482,7 @@ lbm_status Batch::rebuild()
     }
     std::vector<InstanceDev> table(std::max(n, 1));
     std::vector<TileDev> tiles, stiles;
-    std::vector<int> tb(std::max(n, 1)), tc(std::max(n, 1)), sb(std::max(n, 1)), sc(std::max(n, 1));
+    std::vector<int> tc(std::max(n, 1)), sc(std::max(n, 1));  // tiles of each instance
     for (int i = 0; i < n; ++i) {
         Instance &in = *inst_[i];
         fill_dev(in, table[i]);
@@ -495,10 +493,8 @@ lbm_status Batch::rebuild()
         const long long ns = std::max(1ll, (in.geo.n_fwarps + kTileSegs - 1) / kTileSegs);
         if (nt > in.partial_capacity || ns > in.partial_capacity) return fail(LBM_ERR_STATE, "partials too small");
         if (ns * kTileSegs > in.geo.n_fwarps_padded) return fail(LBM_ERR_STATE, "fluid work list too short");
-        tb[i] = (int)tiles.size();
         tc[i] = (int)nt;
         for (long long t = 0; t < nt; ++t) tiles.push_back(TileDev{i, (int)t, t * CS});
-        sb[i] = (int)stiles.size();
         sc[i] = (int)ns;
         for (long long t = 0; t < ns; ++t) stiles.push_back(TileDev{i, (int)t, t * kTileSegs});
     }
@@ -508,14 +504,12 @@ lbm_status Batch::rebuild()
     nstiles_ = (int)stiles.size();
     cudaFree(d_table_);
     cudaFree(d_tiles_);
-    cudaFree(d_tile_begin_);
     cudaFree(d_tile_count_);
     cudaFree(d_stiles_);
-    cudaFree(d_stile_begin_);
     cudaFree(d_stile_count_);
     d_table_ = nullptr;
     d_tiles_ = d_stiles_ = nullptr;
-    d_tile_begin_ = d_tile_count_ = d_stile_begin_ = d_stile_count_ = nullptr;
+    d_tile_count_ = d_stile_count_ = nullptr;
     h_table_ = table;
     CK(dev_alloc(&d_table_, sizeof(InstanceDev) * table.size()));
     CK(cudaMemcpy(d_table_, table.data(), sizeof(InstanceDev) * table.size(), cudaMemcpyHostToDevice));
@@ -523,17 +517,13 @@ lbm_status Batch::rebuild()
         CK(dev_alloc(&d_tiles_, sizeof(TileDev) * tiles.size()));
         CK(cudaMemcpy(d_tiles_, tiles.data(), sizeof(TileDev) * tiles.size(), cudaMemcpyHostToDevice));
     }
-    CK(dev_alloc(&d_tile_begin_, sizeof(int) * tb.size()));
     CK(dev_alloc(&d_tile_count_, sizeof(int) * tc.size()));
-    CK(cudaMemcpy(d_tile_begin_, tb.data(), sizeof(int) * tb.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_tile_count_, tc.data(), sizeof(int) * tc.size(), cudaMemcpyHostToDevice));
     if (nstiles_ > 0) {
         CK(dev_alloc(&d_stiles_, sizeof(TileDev) * stiles.size()));
         CK(cudaMemcpy(d_stiles_, stiles.data(), sizeof(TileDev) * stiles.size(), cudaMemcpyHostToDevice));
     }
-    CK(dev_alloc(&d_stile_begin_, sizeof(int) * sb.size()));
     CK(dev_alloc(&d_stile_count_, sizeof(int) * sc.size()));
-    CK(cudaMemcpy(d_stile_begin_, sb.data(), sizeof(int) * sb.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_stile_count_, sc.data(), sizeof(int) * sc.size(), cudaMemcpyHostToDevice));
     if (n > capacity_) {
         cudaFree(d_sums_);
@@ -601,7 +591,7 @@ struct StepQueue {
     int collision, layout;
     unsigned *status;
     int n_status;
-    const int *tile_begin, *tile_count;
+    const int *tile_count;
     double *sums;
     int n_inst;
     double *fscratch;
@@ -655,7 +645,7 @@ lbm_status Batch::step(long long n)
     for (auto &p : inst_) wx |= p->desc.wall >= LBM_LIBB;
     StepQueue q{&ops(), Launch{d_table_, d_stiles_, nstiles_, kTileSegs, grid_, kStepWarps * 32, stream_},
                 size() == 1 ? &h_table_[0] : nullptr, wx, tma_ ? &tma_launch_ : nullptr, collision_, layout_,
-                d_status_, size(), d_stile_begin_, d_stile_count_, d_sums_, size(), d_fscratch_, d_fcount_};
+                d_status_, size(), d_stile_count_, d_sums_, size(), d_fscratch_, d_fcount_};
     const long long kChunk = 1000;
     long long left = n;
     while (left > 0) {

@@ -98,9 +98,9 @@ private:
     InstanceDev *d_table_ = nullptr;
     std::vector<InstanceDev> h_table_;  // host copy (the single-instance launch passes it by value)
     TileDev *d_tiles_ = nullptr;      // tiles of the active-segment lists (state kernels)
-    int *d_tile_begin_ = nullptr, *d_tile_count_ = nullptr;
+    int *d_tile_count_ = nullptr;
     TileDev *d_stiles_ = nullptr;     // tiles of the fluid-warp lists (step kernels)
-    int *d_stile_begin_ = nullptr, *d_stile_count_ = nullptr;
+    int *d_stile_count_ = nullptr;
     int nstiles_ = 0;
     double *d_sums_ = nullptr;        // [n][kRedSlots]
     unsigned *d_status_ = nullptr;    // [n]

@@ -36,6 +36,8 @@ WORKLOADS = {
     # name: (L, r, storage, layout, collision, wall, tau, delta_rho)
     "cell128_trt_cli_f32_ab": (128, 60.0, "F32", "AB", "TRT", "CLI", 0.6, 2.0e-5),
     "cell128_trt_cli_f32_aa": (128, 60.0, "F32", "AA", "TRT", "CLI", 0.6, 2.0e-5),
+    # a dilute cell (porosity 0.98): the same kernel with few wall lanes
+    "cell128_r20_trt_cli_f32_aa": (128, 20.0, "F32", "AA", "TRT", "CLI", 0.6, 2.0e-5),
     "cell128_srt_cli_f32_ab": (128, 60.0, "F32", "AB", "SRT", "CLI", 0.6, 2.0e-5),
     "cell128_mrt_cli_f32_ab": (128, 60.0, "F32", "AB", "MRT", "CLI", 0.6, 2.0e-5),
     "cell256_trt_cli_f16_ab": (256, 120.0, "F16DEV", "AB", "TRT", "CLI", 0.6, 2.0e-5),

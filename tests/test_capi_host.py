@@ -75,7 +75,7 @@ int main(void) {
     dict(tau=0.5), dict(tau=float("nan")), dict(nx=0), dict(collision=7), dict(wall=6), dict(wall=-1),
     dict(wall=2, layout=1), dict(wall=5, layout=1), dict(wall=4, tau=2.0), dict(storage=9),
     dict(layout=3), dict(block_cells=100), dict(block_cells=64), dict(block_cells=2048), dict(block_cells=512),
-    dict(block_cells=-2), dict(perturb_u=0.5),
+    dict(block_cells=-2), dict(nx=1024, ny=1024, nz=1024), dict(perturb_u=0.5),
     dict(spheres=[[1, 1, 1, -2.0]]), dict(dev_scale_log2=99), dict(magic_lambda=-1.0),
 ])
 def test_invalid_descriptor_rejected_before_gpu(L, bad):

@@ -278,10 +278,25 @@ static int64_t cell_index(int x, int y, int z, int nx, int ny)
 
 static int wrap(int a, int n) { return ((a % n) + n) % n; }
 
+/* Sphere centres farther than MAX_CENTRE_BOXES box lengths from the origin are refused:
+ * min_image folds a displacement into the box one box length at a time. */
+#define MAX_CENTRE_BOXES 64
+
+static int centres_in_range(int nx, int ny, int nz, const double *sph, int nsph)
+{
+    for (int i = 0; i < nsph; ++i)
+        if (!(fabs(sph[4 * i + 0]) <= (double)MAX_CENTRE_BOXES * nx) ||
+            !(fabs(sph[4 * i + 1]) <= (double)MAX_CENTRE_BOXES * ny) ||
+            !(fabs(sph[4 * i + 2]) <= (double)MAX_CENTRE_BOXES * nz))
+            return 0;
+    return 1;
+}
+
 int orc_voxelize(int nx, int ny, int nz, const double *sph, int nsph, uint8_t *solid)
 {
     lattice_init();
     if (nx <= 0 || ny <= 0 || nz <= 0 || nsph < 0) return -1;
+    if (!centres_in_range(nx, ny, nz, sph, nsph)) return -1;
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
@@ -312,6 +327,7 @@ int orc_wall_distances(int nx, int ny, int nz, const uint8_t *solid, const doubl
     lattice_init();
     const int64_t n = (int64_t)nx * ny * nz;
     if (nx <= 0 || ny <= 0 || nz <= 0) return -1;
+    if (!centres_in_range(nx, ny, nz, sph, nsph)) return -1;
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)

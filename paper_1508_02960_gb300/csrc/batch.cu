@@ -76,6 +76,13 @@ lbm_status validate_desc(const lbm_desc &d)
         const lbm_sphere &s = d.spheres[i];
         if (!std::isfinite(s.cx) || !std::isfinite(s.cy) || !std::isfinite(s.cz) || !(s.r > 0) || !std::isfinite(s.r))
             return fail(LBM_ERR_ARG, "sphere " + std::to_string(i) + " has a non-finite centre or radius <= 0");
+        // the device folds a displacement into the box one box length at a time: a centre
+        // far outside it would take that many iterations per cell (or never end, once
+        // d - n rounds back to d)
+        if (std::fabs(s.cx) > kMaxCentreBoxes * d.nx || std::fabs(s.cy) > kMaxCentreBoxes * d.ny ||
+            std::fabs(s.cz) > kMaxCentreBoxes * d.nz)
+            return fail(LBM_ERR_ARG, "sphere " + std::to_string(i) + " has a centre more than " +
+                                         std::to_string(kMaxCentreBoxes) + " box lengths from the origin");
     }
     if (d.magic_lambda < 0 || !std::isfinite(d.magic_lambda)) return fail(LBM_ERR_ARG, "magic_lambda must be >= 0");
     if (d.mrt_energy_ratio < 0 || !std::isfinite(d.mrt_energy_ratio))

@@ -129,6 +129,9 @@ void set_error(const std::string &msg);
 constexpr int kMaxWarpsPerBlock = 32;
 constexpr int kMinChunkSegs = kTileSegs;  // smallest tile (work items): sizes the partial sums
 constexpr long long kDirPad = 0;       // extra elements between direction arrays
+// Sphere centres may lie at most this many box lengths from the origin along each axis
+// (the voxeliser folds displacements into the box one box length at a time).
+constexpr int kMaxCentreBoxes = 64;
 long long direction_stride(long long ncells);
 
 }  // namespace lbm

@@ -77,6 +77,8 @@ int main(void) {
     dict(layout=3), dict(block_cells=100), dict(block_cells=64), dict(block_cells=2048), dict(block_cells=512),
     dict(block_cells=-2), dict(nx=1024, ny=1024, nz=1024), dict(perturb_u=0.5),
     dict(spheres=[[1, 1, 1, -2.0]]), dict(dev_scale_log2=99), dict(magic_lambda=-1.0),
+    # centres far outside the box (the device folds them in one box length at a time)
+    dict(spheres=[[1e17, 1, 1, 2.0]]), dict(spheres=[[4, -600.0, 4, 2.0]]), dict(spheres=[[4, 4, 1e10, 2.0]]),
 ])
 def test_invalid_descriptor_rejected_before_gpu(L, bad):
     kw = dict(nx=8, ny=8, nz=8, tau=0.8)

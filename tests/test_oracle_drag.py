@@ -135,5 +135,13 @@ def test_dilute_array_stokes_drag(orc):
     assert F[0] == pytest.approx(dr / 3.0 * L * L, rel=2e-3)
     c = 4.0 / 3.0 * np.pi * r ** 3 / L ** 3
     cd_series = 1.0 / (1.0 - 1.7601 * c ** (1 / 3) + c - 1.5593 * c ** 2)
-    cd, _ = orc.drag_coefficients(F[0], U, tau, r_sum=r, area_sum=np.pi * r * r)
+    cd, cda = orc.drag_coefficients(F[0], U, tau, r_sum=r, area_sum=np.pi * r * r)
     assert cd == pytest.approx(cd_series, rel=0.02)
+    # the observables of the same steady state, tied to the drag: at steady state the drag
+    # balances the pressure force on the cell (F = dp L^2 = (dp/L) L^3), so Eq. Darcy's
+    # K = mu U / (dp/L) must equal L^3 / (6 pi r C_D) with C_D of Eq. AnalyticForce; and
+    # with d_p = 2r the two drag normalisations differ by Re_p / 12:
+    # C_D / C_D,A = rho0 pi r^2 U^2 / (6 pi mu U r) = U (2r) / (12 nu)
+    _, K, Re_p = orc.observables(U, tau, dr, L, 2.0 * r)[:3]
+    assert K == pytest.approx(L ** 3 / (6.0 * np.pi * r * cd), rel=2e-3)
+    assert Re_p == pytest.approx(12.0 * cd / cda, rel=1e-12)

@@ -185,6 +185,18 @@ def test_voxel_periodic_images(orc):
     assert (s == s[::-1, ::-1, ::-1]).all()          # mirror about the corner: i -> L-1-i
 
 
+def test_voxel_far_centres_refused(orc):
+    """Centres more than 64 box lengths out are refused (the periodic fold would loop);
+    centres a few box lengths out are folded to the same voxels as their image in the box."""
+    with pytest.raises(ValueError):
+        orc.voxelize((8, 8, 8), [[1e17, 4.0, 4.0, 2.0]])
+    with pytest.raises(ValueError):
+        orc.wall_distances(np.zeros((8, 8, 8), np.uint8), [[4.0, -600.0, 4.0, 2.0]])
+    a = orc.voxelize((8, 8, 8), [[4.25, 3.5, 4.75, 2.6]])
+    b = orc.voxelize((8, 8, 8), [[4.25 + 24.0, 3.5 - 16.0, 4.75 + 8.0, 2.6]])
+    assert a.sum() > 0 and np.array_equal(a, b)
+
+
 def test_wall_distance_against_bisection(orc):
     """q of each cut link equals the first crossing of the segment x_f1 -> x_b with the
     sphere, found here by bisection (an independent method)."""
@@ -280,6 +292,31 @@ def test_poiseuille_magic_three_sixteenths(orc):
     for kw in (dict(lam=0.25), dict(coll=0)):                           # controls
         ux, ua, _ = _channel_profile(orc, 16, 0.5, wall=0, **kw)
         assert np.abs(ux / ua - 1).max() > 1e-3
+
+
+@pytest.mark.parametrize("N,tau", [(8, 0.8), (16, 0.8), (8, 1.3)])
+def test_permeability_slit_channel_closed_form(orc, N, tau):
+    """Permeability of a plane channel from the observables (Eq. Darcy, K = mu U / (dp/L_x),
+    U the volume-averaged velocity of Sec. 1), against the closed form.  TRT with Lambda =
+    3/16 and bounce-back walls gives the exact Poiseuille profile u = G/(2 nu) eta (N - eta)
+    on the N fluid rows, eta = j - 1/2 (Sec. 2.1); summed over the rows, Sum eta (N - eta) =
+    N (2 N^2 + 1) / 12, and averaged over the box of N + 1 rows (one solid row):
+        K = N (2 N^2 + 1) / (24 (N + 1)) = N (N^2 + 1/2) / (12 (N + 1)),
+    independent of tau.  The box is 4 x (N + 1) x 3, so that an average over the wrong
+    volume, a gradient over L_y or L_z instead of L_x, dp = delta_rho instead of
+    delta_rho / 3, or a viscosity off by a factor each miss it."""
+    nx, nz = 4, 3
+    s = I.slit_channel(N, nx=nx, nz=nz)
+    ny = s.shape[1]
+    dr = 1e-5
+    nu = (tau - 0.5) / 3
+    steps = int(3.0 * N * N / nu) + 2000
+    _, sums, _ = orc.run(s, orc.init_rest(s), steps, collision=1, wall=0, tau=tau, delta_rho=dr,
+                         magic_lambda=3 / 16)
+    U_sup = sums[1] / (nx * ny * nz)
+    K = orc.observables(U_sup, tau, dr, nx, 1.0)[1]
+    K_exact = N * (N * N + 0.5) / (12.0 * (N + 1))
+    assert K == pytest.approx(K_exact, rel=1e-9, abs=0)
 
 
 def test_cli_half_equals_sbb(orc):

@@ -178,7 +178,6 @@ lbm_status Batch::make_instance(const lbm_desc &d0, cudaStream_t s, std::unique_
     auto cleanup = [&](cudaError_t ce, const char *what) {
         cudaFree(in->f0);
         cudaFree(in->f1);
-        cudaFree(in->linkB);
         cudaFree(in->partials);
         free_geometry(&in->geo);
         return cuda_fail(ce, what);
@@ -197,11 +196,6 @@ lbm_status Batch::make_instance(const lbm_desc &d0, cudaStream_t s, std::unique_
     if (d.layout == LBM_LAYOUT_AB) {
         if ((e = dev_alloc(&in->f1, pop)) != cudaSuccess) return cleanup(e, "dev_alloc(populations)");
         if ((e = clear(in->f1)) != cudaSuccess) return cleanup(e, "cudaMemset");
-    }
-    if (d.layout == LBM_LAYOUT_AA && d.wall == LBM_CLI && in->geo.n_links > 0) {
-        if ((e = dev_alloc(&in->linkB, es * in->geo.n_links)) != cudaSuccess) return cleanup(e, "dev_alloc(linkB)");
-        if ((e = cudaMemsetAsync(in->linkB, 0, es * in->geo.n_links, s)) != cudaSuccess)
-            return cleanup(e, "cudaMemset");
     }
     // partial sums: one row of kRedSlots doubles per work chunk at the smallest chunk size
     in->partial_capacity = std::max(1ll, (in->geo.n_active + kMinChunkSegs - 1) / kMinChunkSegs);
@@ -223,7 +217,6 @@ Batch::~Batch()
     for (auto &p : inst_) {
         cudaFree(p->f0);
         cudaFree(p->f1);
-        cudaFree(p->linkB);
         cudaFree(p->partials);
         free_geometry(&p->geo);
     }
@@ -285,7 +278,6 @@ lbm_status Batch::remove(int i)
     Instance &p = *inst_[i];
     cudaFree(p.f0);
     cudaFree(p.f1);
-    cudaFree(p.linkB);
     cudaFree(p.partials);
     free_geometry(&p.geo);
     inst_.erase(inst_.begin() + i);
@@ -345,7 +337,6 @@ static void fill_dev(const Instance &in, InstanceDev &D)
     D.boff = in.geo.boff;
     D.linkc = in.geo.linkc;
     D.linkw = in.geo.linkw;
-    D.linkB = in.linkB;
     D.partials = in.partials;
     D.ncells = in.geo.ncells;
     D.n32 = (uint32_t)in.geo.ncells;
@@ -576,8 +567,8 @@ lbm_status Batch::init_equilibrium(int i)
         CK(ops().init(d_table_, j, in.geo.ncells, layout_, cur_of(in), in.desc.perturb_u,
                       (unsigned long long)in.desc.seed, stream_));
         ++launches_;
-        if (layout_ == LBM_LAYOUT_AB && in.geo.n_boundary > 0) {
-            CK(ops().wall_prepare(d_table_, j, in.geo.n_boundary, in.geo.bcell, cur_of(in), stream_));
+        if (in.geo.n_boundary > 0) {
+            CK(ops().wall_prepare(d_table_, j, in.geo.n_boundary, in.geo.bcell, layout_, cur_of(in), stream_));
             ++launches_;
         }
         in.have_sums = false;
@@ -794,8 +785,8 @@ lbm_status Batch::set_f64(int i, const double *host)
         CK(ops().import_dir(d_table_, i, n, layout_, cur_of(in), k, d_stage_, stream_));
         ++launches_;
     }
-    if (layout_ == LBM_LAYOUT_AB && in.geo.n_boundary > 0) {
-        CK(ops().wall_prepare(d_table_, i, in.geo.n_boundary, in.geo.bcell, cur_of(in), stream_));
+    if (in.geo.n_boundary > 0) {
+        CK(ops().wall_prepare(d_table_, i, in.geo.n_boundary, in.geo.bcell, layout_, cur_of(in), stream_));
         ++launches_;
     }
     in.have_sums = false;
@@ -858,8 +849,8 @@ lbm_status Batch::state_io(int i, void *host, size_t bytes, bool to_host)
         if (copy_) CK(cudaStreamSynchronize(copy_));
         return LBM_OK;
     }
-    if (layout_ == LBM_LAYOUT_AB && in.geo.n_boundary > 0) {
-        CK(ops().wall_prepare(d_table_, i, in.geo.n_boundary, in.geo.bcell, cur_of(in), stream_));
+    if (in.geo.n_boundary > 0) {
+        CK(ops().wall_prepare(d_table_, i, in.geo.n_boundary, in.geo.bcell, layout_, cur_of(in), stream_));
         ++launches_;
     }
     in.have_sums = false;
@@ -930,8 +921,8 @@ lbm_status Batch::apply_staged_state(int i)
         CK(ops().state_dir(d_table_, i, nf, layout_, cur, aa_phase_, 0, Q, d_pstage_[b], 0, stream_));
         ++launches_;
     }
-    if (layout_ == LBM_LAYOUT_AB && in.geo.n_boundary > 0) {
-        CK(ops().wall_prepare(d_table_, i, in.geo.n_boundary, in.geo.bcell, cur, stream_));
+    if (in.geo.n_boundary > 0) {
+        CK(ops().wall_prepare(d_table_, i, in.geo.n_boundary, in.geo.bcell, layout_, cur, stream_));
         ++launches_;
     }
     CK(cudaEventRecord(ev_free_[b], stream_));
@@ -1050,15 +1041,10 @@ lbm_status Batch::save(int i, const char *path)
     std::vector<char> buf(pop);
     const void *src = (layout_ == LBM_LAYOUT_AB) ? (cur_of(in) ? in.f1 : in.f0) : in.f0;
     CK(cudaMemcpy(buf.data(), src, pop, cudaMemcpyDeviceToHost));
-    std::vector<char> lb;
-    if (in.linkB) {
-        lb.resize(es * in.geo.n_links);
-        CK(cudaMemcpy(lb.data(), in.linkB, lb.size(), cudaMemcpyDeviceToHost));
-    }
     CkptHeader h;
     std::memset(&h, 0, sizeof(h));
     std::memcpy(h.magic, "LBMGB300", 8);
-    h.version = 2;  // 2: A-B solid slots hold the wall terms of the next step
+    h.version = 3;  // 3: the solid slots of either layout hold the wall terms of the next step
     h.nx = in.desc.nx;
     h.ny = in.desc.ny;
     h.nz = in.desc.nz;
@@ -1069,13 +1055,12 @@ lbm_status Batch::save(int i, const char *path)
     h.aa_phase = aa_phase_;
     h.dev_scale_log2 = in.dev_scale_log2;
     h.steps = in.steps;
-    h.n_links = in.linkB ? in.geo.n_links : 0;
+    h.n_links = 0;  // no per-link buffer
     h.elem_bytes = (int64_t)es;
     h.stride = in.ks;
     FILE *f = std::fopen(path, "wb");
     if (!f) return fail(LBM_ERR_IO, std::string("cannot open ") + path);
-    bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 && std::fwrite(buf.data(), 1, buf.size(), f) == buf.size() &&
-              (lb.empty() || std::fwrite(lb.data(), 1, lb.size(), f) == lb.size());
+    bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 && std::fwrite(buf.data(), 1, buf.size(), f) == buf.size();
     ok = (std::fclose(f) == 0) && ok;
     if (!ok) return fail(LBM_ERR_IO, std::string("write failed: ") + path);
     return LBM_OK;
@@ -1092,28 +1077,27 @@ lbm_status Batch::load(int i, const char *path)
     FILE *f = std::fopen(path, "rb");
     if (!f) return fail(LBM_ERR_IO, std::string("cannot open ") + path);
     CkptHeader h;
-    if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 2) {
+    if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 3) {
         std::fclose(f);
         return fail(LBM_ERR_IO, "not a checkpoint of this library");
     }
     const size_t es = storage_bytes(storage_);
     if (h.nx != in.desc.nx || h.ny != in.desc.ny || h.nz != in.desc.nz || h.storage != storage_ ||
         h.layout != layout_ || h.collision != collision_ || h.wall != in.desc.wall || h.elem_bytes != (int64_t)es ||
-        h.dev_scale_log2 != in.dev_scale_log2 || h.n_links != (in.linkB ? in.geo.n_links : 0) ||
+        h.dev_scale_log2 != in.dev_scale_log2 || h.n_links != 0 ||
         h.stride != in.ks) {
         std::fclose(f);
         return fail(LBM_ERR_ARG, "checkpoint does not match this context's descriptor");
     }
     const size_t pop = (size_t)Q * in.ks * es;
-    std::vector<char> buf(pop), lb(h.n_links * es);
-    bool ok = std::fread(buf.data(), 1, pop, f) == pop && (lb.empty() || std::fread(lb.data(), 1, lb.size(), f) == lb.size());
+    std::vector<char> buf(pop);
+    bool ok = std::fread(buf.data(), 1, pop, f) == pop;
     std::fclose(f);
     if (!ok) return fail(LBM_ERR_IO, "checkpoint truncated");
     CK(cudaStreamSynchronize(stream_));
     if (layout_ == LBM_LAYOUT_AA) aa_phase_ = h.aa_phase;
     void *dst = (layout_ == LBM_LAYOUT_AB) ? (cur_of(in) ? in.f1 : in.f0) : in.f0;
     CK(cudaMemcpy(dst, buf.data(), pop, cudaMemcpyHostToDevice));
-    if (!lb.empty()) CK(cudaMemcpy(in.linkB, lb.data(), lb.size(), cudaMemcpyHostToDevice));
     in.steps = h.steps;
     in.have_sums = false;
     in.have_force = false;

@@ -18,7 +18,6 @@ struct Instance {
     std::vector<double> mrt_rates; // explicit MRT rates when given
     GeometryDev geo;
     void *f0 = nullptr, *f1 = nullptr;
-    void *linkB = nullptr;
     double *partials = nullptr;
     long long partial_capacity = 0;  // tiles
     int phase = 0;                   // A-B buffer holding the state when the batch flip is 0

@@ -10,8 +10,8 @@
 namespace lbm {
 
 // Where g~_k(x) of a fluid cell lives.  A-B: slot k of the current buffer.  AA after a
-// LOCAL step (or import): own slot kbar.  AA after a PULL step: slot k of x + e_k, or
-// the own slot kbar when x + e_k is solid (bounce-back redirect).
+// LOCAL step (or import): own slot kbar.  AA after a PULL step: slot k of x + e_k (a
+// solid cell's slot when x + e_k is solid: the link's own slot there).
 template <int STORE>
 __device__ __forceinline__ long long canonical_index(const InstanceDev &I, int layout, int aa_phase,
                                                      int cur, long long cell, int k, uint32_t wm,
@@ -24,8 +24,8 @@ __device__ __forceinline__ long long canonical_index(const InstanceDev &I, int l
         return (long long)k * N + cell;
     }
     buf = 0;
-    const int kb = opp(k);
-    if (aa_phase == 0 || ((wm >> kb) & 1u)) return (long long)kb * N + cell;
+    (void)wm;
+    if (aa_phase == 0) return (long long)opp(k) * N + cell;
     return (long long)k * N + X[1 + ex(k)] + Y[1 + ey(k)] + Z[1 + ez(k)];
 }
 
@@ -80,7 +80,8 @@ __device__ __forceinline__ double hash_uniform_pm1(unsigned long long seed, long
 
 // Equilibrium initial state g_k = f^eq_k(rho0, u) - w_k rho0 for fluid cells (u = 0 or a
 // seeded perturbation of amplitude amp), 0 in solid cells.  Writes the layout's
-// post-collision form (A-B buffer `cur`, or AA phase 0) and the AA side buffer.
+// post-collision form (A-B buffer `cur`, or AA phase 0); the wall terms follow from
+// wall_prepare_kernel.
 template <int STORE>
 __global__ void init_kernel(const InstanceDev *__restrict__ table, int inst, int layout, int cur,
                             double amp, unsigned long long seed)
@@ -103,38 +104,31 @@ __global__ void init_kernel(const InstanceDev *__restrict__ table, int inst, int
         if (amp != 0.0)
             for (int a = 0; a < 3; ++a) u[a] = amp * hash_uniform_pm1(seed, cell, a);
         const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        uint32_t wm = 0u, off = 0u;
-        if ((meta.y >> lane) & 1u) {
-            const uint32_t b = meta.z + __popc(meta.y & ((1u << lane) - 1u));
-            wm = I.bmask[b];
-            off = I.boff[b];
-        }
-        T *linkB = reinterpret_cast<T *>(I.linkB);
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             const double eu = ex(k) * u[0] + ey(k) * u[1] + ez(k) * u[2];
             const double g = weight(k) * I.rho0 * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
-            const T v = S::pack((typename S::R)g, I.scale);
-            f[(long long)(layout == 0 ? k : opp(k)) * I.ks + cell] = v;
-            if (layout == 1 && linkB && ((wm >> k) & 1u)) linkB[off + __popc(wm & ((1u << k) - 1u))] = v;
+            f[(long long)(layout == 0 ? k : opp(k)) * I.ks + cell] = S::pack((typename S::R)g, I.scale);
         }
     }
 }
 
-// A-B layout: the own-cell part S of every wall rule (wall_own_part), from the stored
-// post-collision state of buffer cur, into slot k of the solid cell x - e_k, which the
-// next step's pull of direction k reads (the steps themselves leave S there for the step
-// after them).  For a state set from outside: the initial state, imported populations.
-// One thread per boundary cell; every solid slot belongs to one link only.
+// The own-cell part S of every wall rule (wall_own_part), from the stored post-collision
+// state, into the solid slot the next step's pull of direction k reads (the steps
+// themselves leave S there for the step after them): A-B, from buffer cur into slot k of
+// the solid cell x - e_k; AA at phase 0 (the state after a LOCAL step, where own slot m
+// holds g~_mbar), into slot kbar of x - e_k.  For a state set from outside: the initial
+// state, imported populations.  One thread per boundary cell; every solid slot belongs to
+// one link only.
 template <int STORE>
 __global__ void wall_prepare_kernel(const InstanceDev *__restrict__ table, int inst, long long nb,
-                                    const long long *__restrict__ bcell, int cur)
+                                    const long long *__restrict__ bcell, int layout, int cur)
 {
     using S = Store<STORE>;
     using T = typename S::T;
     using R = typename S::R;
     const InstanceDev &I = table[inst];
-    T *f = reinterpret_cast<T *>(cur ? I.f1 : I.f0);
+    T *f = reinterpret_cast<T *>(layout == 0 && cur ? I.f1 : I.f0);
     const R *linkc = reinterpret_cast<const R *>(I.linkc);
     const long long ks = I.ks, nx = I.nx, ny = I.ny, nz = I.nz;
     constexpr bool sr = sizeof(T) == 2;
@@ -148,7 +142,7 @@ __global__ void wall_prepare_kernel(const InstanceDev *__restrict__ table, int i
         R drho = R(0), u[3] = {R(0), R(0), R(0)};
         if (I.wall == 4) {
             for (int m = 0; m < Q; ++m) {
-                const R gm = S::load(f + (long long)m * ks + cell, I.inv_scale);
+                const R gm = S::load(f + (long long)(layout == 0 ? m : opp(m)) * ks + cell, I.inv_scale);
                 drho += gm;
                 u[0] += R(ex(m)) * gm;
                 u[1] += R(ey(m)) * gm;
@@ -161,8 +155,9 @@ __global__ void wall_prepare_kernel(const InstanceDev *__restrict__ table, int i
         for (int k = 1; k < Q; ++k) {
             if (!((wm >> k) & 1u)) continue;
             const int kb = opp(k);
-            const R C = S::load(f + (long long)kb * ks + cell, I.inv_scale);
-            const R B = S::load(f + (long long)k * ks + cell, I.inv_scale);
+            // C = g~_kbar(x), B = g~_k(x): slots kbar and k in A-B, k and kbar in AA
+            const R C = S::load(f + (long long)(layout == 0 ? kb : k) * ks + cell, I.inv_scale);
+            const R B = S::load(f + (long long)(layout == 0 ? k : kb) * ks + cell, I.inv_scale);
             const uint32_t l = off + __popc(wm & ((1u << k) - 1u));
             R sv;
             if (I.wall >= 2) {  // as wall_own_part_w in the step kernel
@@ -180,7 +175,8 @@ __global__ void wall_prepare_kernel(const InstanceDev *__restrict__ table, int i
                 sv = wall_own_part(I.wall, cq, C, B);
             }
             const long long src = (x - ex(k) + nx) % nx + nx * ((y - ey(k) + ny) % ny + ny * ((z - ez(k) + nz) % nz));
-            f[(long long)k * ks + src] = sr ? S::pack_sr(sv, I.scale, round_bits(h, k, float(sv))) : S::pack(sv, I.scale);
+            f[(long long)(layout == 0 ? k : kb) * ks + src] =
+                sr ? S::pack_sr(sv, I.scale, round_bits(h, k, float(sv))) : S::pack(sv, I.scale);
         }
     }
 }
@@ -205,14 +201,7 @@ __global__ void import_kernel(const InstanceDev *__restrict__ table, int inst, i
             f[slot] = S::pack(0.0f, I.scale);
             continue;
         }
-        const T v = S::pack((typename S::R)(fk[cell] - wr), I.scale);
-        f[slot] = v;
-        if (layout == 1 && ((meta.y >> lane) & 1u) && I.linkB) {
-            const uint32_t b = meta.z + __popc(meta.y & ((1u << lane) - 1u));
-            const uint32_t wm = I.bmask[b];
-            if ((wm >> k) & 1u)
-                reinterpret_cast<T *>(I.linkB)[I.boff[b] + __popc(wm & ((1u << k) - 1u))] = v;
-        }
+        f[slot] = S::pack((typename S::R)(fk[cell] - wr), I.scale);
     }
 }
 
@@ -268,8 +257,8 @@ __global__ void state_gather_kernel(const InstanceDev *__restrict__ table, int i
 
 // The inverse for a state set from outside (as import_kernel, without conversion):
 // direction k = k0 + blockIdx.y of fluid cell j from in[blockIdx.y * nf + j] into its slot
-// of the step-0 arrangement; in the AA layout also into the link buffer of its CLI links.
-// Solid cells are left alone (the A-B solid slots are rebuilt by wall_prepare_kernel).
+// of the step-0 arrangement.  Solid cells are left alone (their wall terms are rebuilt by
+// wall_prepare_kernel).
 template <int STORE>
 __global__ void state_scatter_kernel(const InstanceDev *__restrict__ table, int inst, int layout, int cur, int k0,
                                      long long nf, const typename Store<STORE>::T *__restrict__ in)
@@ -282,17 +271,7 @@ __global__ void state_scatter_kernel(const InstanceDev *__restrict__ table, int 
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < nf;
          j += (long long)gridDim.x * blockDim.x) {
         const long long cell = I.fcell[j];
-        const T v = in[j];
-        f[(long long)(layout == 0 ? k : opp(k)) * I.ks + cell] = v;
-        if (layout == 1 && I.linkB) {
-            const uint4 meta = I.seg[cell >> 5];
-            const int lane = (int)(cell & 31);
-            if ((meta.y >> lane) & 1u) {
-                const uint32_t b = meta.z + __popc(meta.y & ((1u << lane) - 1u));
-                const uint32_t wm = I.bmask[b];
-                if ((wm >> k) & 1u) reinterpret_cast<T *>(I.linkB)[I.boff[b] + __popc(wm & ((1u << k) - 1u))] = v;
-            }
-        }
+        f[(long long)(layout == 0 ? k : opp(k)) * I.ks + cell] = in[j];
     }
 }
 

@@ -226,8 +226,7 @@ enum { STATUS_DIVERGED = 1u, STATUS_TIMEOUT = 2u, STATUS_BOUNDS = 4u };
 // warp's first boundary cell.
 // Boundary cell b: bmask[b] bit k set when x - e_k is solid (the pull of direction k hits
 // the wall), boff[b] the index of its first link; its links are ordered by k.  Link l:
-// linkc[l] = CLI coefficient (1-2q)/(1+2q) (0 where CLI falls back to SBB), linkB[l] =
-// the cell's own post-collision population of the link (AA layout only).
+// linkc[l] = CLI coefficient (1-2q)/(1+2q) (0 where CLI falls back to SBB).
 // ------------------------------------------------------------------------------------
 struct InstanceDev {
     void *f0, *f1;           // populations [19][ks] (direction k at k * ks); AA uses f0 only
@@ -239,7 +238,6 @@ struct InstanceDev {
     const uint32_t *boff;    // [n_boundary]
     const void *linkc;       // [n_links], type R
     const void *linkw;       // [n_links][kLinkW], type R (walls >= LBM_LIBB), else NULL
-    void *linkB;             // [n_links], type T (AA layout)
     double *partials;        // [n_tiles of this instance][kRedSlots]
     long long ncells;
     uint32_t n32;            // ncells

@@ -217,11 +217,11 @@ cudaError_t moments(const Launch &L, int layout, int cur, int aa_phase, int mode
 }
 
 template <int STORE>
-cudaError_t wall_prepare(const InstanceDev *table, int inst, long long nb, const long long *bcell, int cur,
-                         cudaStream_t s)
+cudaError_t wall_prepare(const InstanceDev *table, int inst, long long nb, const long long *bcell, int layout,
+                         int cur, cudaStream_t s)
 {
     if (nb <= 0) return cudaSuccess;
-    wall_prepare_kernel<STORE><<<flat_grid(nb, 128), 128, 0, s>>>(table, inst, nb, bcell, cur);
+    wall_prepare_kernel<STORE><<<flat_grid(nb, 128), 128, 0, s>>>(table, inst, nb, bcell, layout, cur);
     return cudaGetLastError();
 }
 

@@ -73,9 +73,10 @@ struct FormatOps {
     // once per kernel, before any launch or capture: opt in to its shared memory; returns
     // the blocks per multiprocessor it can hold (0 on error)
     int (*tma_prepare)(int coll, int wx);
-    // A-B layout: wall terms of the stored state into the solid slots (wall_prepare_kernel)
+    // wall terms of the stored state into the solid slots (wall_prepare_kernel; layout 0 =
+    // A-B from buffer cur, 1 = AA at phase 0)
     cudaError_t (*wall_prepare)(const InstanceDev *table, int inst, long long n_boundary, const long long *bcell,
-                                int cur, cudaStream_t s);
+                                int layout, int cur, cudaStream_t s);
     const void *(*step_kernel_ptr)(int coll, int kind);  // for occupancy queries
 };
 

@@ -22,10 +22,16 @@
 //
 // AA layout (in-place, one buffer).  PULL steps read g~_k(x - e_k) from slot kbar of
 // x - e_k and push g~_k(x) into slot k of x + e_k; LOCAL steps read slot k and write
-// slot kbar of x itself.  Every slot is then read and written by one thread only.  A
-// push into a solid cell goes to the own slot kbar instead, which is exactly where the
-// next step's bounce-back reads it.  CLI's own value g~_k(x) would be overwritten by the
-// neighbour x + e_k in either step, so each CLI link keeps it in a side buffer (linkB).
+// slot kbar of x itself.  Every slot is then read and written by one thread only.
+// Walls.  No fluid cell owns a slot of a solid cell, and slot kbar of the solid cell
+// s = x - e_k belongs to the link (x, k) alone: a PULL step of x pulls direction k from
+// it and pushes g~_kbar(x) into it (x + e_kbar = s).  Each step leaves the own-cell part S
+// of the link's wall rule (wall_own_part, from the post-collision values in registers)
+// where the next step's ordinary pull of direction k finds it: a LOCAL step stores S into
+// slot kbar of s; a PULL step stores it into the own slot k, which no other cell reads or
+// writes in a PULL step, besides its ordinary push of g~_kbar(x) into slot kbar of s.
+// So the wall rule needs no load beyond the 19 pulls, as in the A-B layout, and the two
+// layouts agree bit for bit.
 #pragma once
 
 #include "lbm_device.cuh"
@@ -346,16 +352,14 @@ __device__ __forceinline__ R wall_own_part_w(const Par<R> &P, const R *lw, int k
 // registers), so SBB needs no wall code at all and CLI adds c g_kbar^in, g_kbar^in being
 // the cell's ordinary pull from x_f2 = x + e_k.  A state set from outside (initial state,
 // imported populations) gets these slots from wall_prepare_kernel.
-// Walls in the AA layout: C is in the own slot k, B (CLI) in the link buffer linkB, and
-// the same arithmetic runs at the start of the step.
+// Walls in the AA layout: the same, with S where the AA layout's pull reads (see above).
 template <int COLL, int STORE, int KIND, bool RED, bool WX, typename R>
 __device__ __forceinline__ void finish_cell(const InstanceDev &I, R (&g)[Q], const Par<R> &P, const R *rates,
                                             uint32_t cell, uint32_t x,
                                             bool inner, const uint32_t *pull_off, const uint32_t *push_off,
                                             uint32_t wm, uint32_t off, const typename Store<STORE>::T *fs,
                                             typename Store<STORE>::T *fd, const R *linkc, const R *linkw,
-                                            typename Store<STORE>::T *linkB, unsigned *status, R &rd, R &rx, R &ry,
-                                            R &rz, R (&fm)[3])
+                                            unsigned *status, R &rd, R &rx, R &ry, R &rz, R (&fm)[3])
 {
     using S = Store<STORE>;
     using T = typename S::T;
@@ -368,19 +372,21 @@ __device__ __forceinline__ void finish_cell(const InstanceDev &I, R (&g)[Q], con
             const uint32_t l = off + __popc(wm & ((1u << k) - 1u));
             const R cq = P.wall == 1 ? ld_keep(linkc + l, l2_keep_policy()) : R(0);
             R v, C;
-            if constexpr (KIND == KIND_AB) {
-                v = g[k];  // S, left by the previous step in the solid slot
-                if (WX && P.wall >= 2)
-                    v = wall_neighbour_terms<STORE>(P, P.wall, linkw + (size_t)l * kLinkW, k, cell, g, fs, v);
-                else if (cq != R(0)) v = fma_r(cq, g[kb], v);
-                if constexpr (RED) C = S::load(fs + ((uint32_t)kb * KS + cell), P.isc);
-            } else {
-                C = S::cvt(ld_pop<KIND>(fs + ((uint32_t)k * KS + cell)), P.isc);  // own g~_kbar(x)
-                // CLI's own g~_k(x), loaded beside the coefficient rather than after it (a
-                // fallback link, c = 0, multiplies it by zero; the buffer holds finite values)
-                const R B = P.wall == 1 ? S::cvt(ld_pop<KIND>(linkB + l), P.isc) : R(0);
-                v = wall_own_part(P.wall, cq, C, B);
-                if (cq != R(0)) v = fma_r(cq, g[kb], v);
+            v = g[k];  // S, left by the previous step where this pull reads
+            if (WX && KIND == KIND_AB && P.wall >= 2)
+                v = wall_neighbour_terms<STORE>(P, P.wall, linkw + (size_t)l * kLinkW, k, cell, g, fs, v);
+            else if (cq != R(0)) v = fma_r(cq, g[kb], v);
+            if constexpr (RED) {
+                // the own post-collision g~_kbar(x) of the previous step (momentum exchange):
+                // A-B: own slot kbar; AA after a LOCAL step: own slot k; AA after a PULL
+                // step: where it was pushed, slot kbar of x - e_k
+                uint32_t ci;
+                if constexpr (KIND == KIND_AB) ci = (uint32_t)kb * KS + cell;
+                else if constexpr (KIND == KIND_AA_PULL) ci = (uint32_t)k * KS + cell;
+                else ci = (uint32_t)kb * KS + coord_of(P, cell).pull(k);
+                C = checked(I, ci - (KIND == KIND_AA_PULL ? (uint32_t)k : (uint32_t)kb) * KS, I.n32)
+                        ? S::cvt(ld_pop<KIND>(fs + ci), P.isc)
+                        : R(0);
             }
             g[k] = v;
             if constexpr (RED) {  // e_kbar = -e_k
@@ -420,18 +426,12 @@ __device__ __forceinline__ void finish_cell(const InstanceDev &I, R (&g)[Q], con
                 uint32_t idx = cell + push_off[k];
                 if (ex(k) == 1) idx -= cxp;
                 if (ex(k) == -1) idx += cxm;
-                // push to x + e_k, or bounce into the own slot kbar when x + e_k is solid
-                const bool bounce = (wm >> opp(k)) & 1u;
-                if (bounce) idx = (uint32_t)opp(k) * KS + cell;
-                if (checked(I, idx - (uint32_t)(bounce ? opp(k) : k) * KS, I.n32)) fd[idx] = packed[k];
+                if (checked(I, idx - (uint32_t)k * KS, I.n32)) fd[idx] = packed[k];
             }
         } else {
             const Coord co = coord_of(P, cell);
 #pragma unroll
-            for (int k = 0; k < Q; ++k) {
-                if ((wm >> opp(k)) & 1u) fd[(uint32_t)opp(k) * KS + cell] = packed[k];
-                else fd[(uint32_t)k * KS + co.push(k)] = packed[k];
-            }
+            for (int k = 0; k < Q; ++k) fd[(uint32_t)k * KS + co.push(k)] = packed[k];
         }
     } else {
 #pragma unroll
@@ -440,8 +440,25 @@ __device__ __forceinline__ void finish_cell(const InstanceDev &I, R (&g)[Q], con
             else fd[(uint32_t)opp(k) * KS + cell] = packed[k];
         }
     }
-    if constexpr (KIND == KIND_AB) {
-        if (wm) {  // the own-cell part of every wall rule, into the solid slot the next pull reads
+    if constexpr (KIND == KIND_AA_PULL) {
+        // the own-cell part of every wall rule into the own slot k, which the next (LOCAL)
+        // step's pull of direction k reads
+        if (wm) {
+#pragma unroll
+            for (int k = 1; k < Q; ++k) {
+                if (!((wm >> k) & 1u)) continue;
+                const uint32_t l = off + __popc(wm & ((1u << k) - 1u));
+                const R cq = P.wall == 1 ? ld_keep(linkc + l, l2_keep_policy()) : R(0);
+                const R sv = wall_own_part(P.wall, cq, g[opp(k)], g[k]);
+                fd[(uint32_t)k * KS + cell] = sr ? S::pack_sr(sv, P.sc, round_bits(h, k, float(sv))) : S::pack(sv, P.sc);
+            }
+        }
+    }
+    if constexpr (KIND != KIND_AA_PULL) {
+        // A-B, and AA LOCAL steps: the own-cell part of every wall rule into the solid slot
+        // the next step's pull of direction k reads (A-B: slot k of x - e_k in the other
+        // buffer; AA: slot kbar of x - e_k)
+        if (wm) {
             const uint32_t cxm = x == 0 ? P.nx : 0u, cxp = x == P.nx - 1 ? P.nx : 0u;
             Coord co;
             if (!inner) co = coord_of(P, cell);
@@ -456,25 +473,19 @@ __device__ __forceinline__ void finish_cell(const InstanceDev &I, R (&g)[Q], con
                     const R cq = P.wall == 1 ? ld_keep(linkc + l, l2_keep_policy()) : R(0);
                     sv = wall_own_part(P.wall, cq, g[opp(k)], g[k]);
                 }
+                // the slot direction: k in A-B, kbar in AA (pull_off of an AA instance
+                // addresses slot kbar of x - e_k)
+                const uint32_t d = KIND == KIND_AB ? (uint32_t)k : (uint32_t)opp(k);
                 uint32_t idx;
                 if (inner) {
                     idx = cell + pull_off[k];
                     if (ex(k) == 1) idx += cxm;
                     if (ex(k) == -1) idx -= cxp;
                 } else {
-                    idx = (uint32_t)k * KS + co.pull(k);
+                    idx = d * KS + co.pull(k);
                 }
-                if (checked(I, idx - (uint32_t)k * KS, I.n32))
+                if (checked(I, idx - d * KS, I.n32))
                     fd[idx] = sr ? S::pack_sr(sv, P.sc, round_bits(h, k, float(sv))) : S::pack(sv, P.sc);
-            }
-        }
-    }
-    if constexpr (KIND != KIND_AB) {
-        if (wm && P.wall == 1) {
-#pragma unroll
-            for (int k = 1; k < Q; ++k) {
-                if (!((wm >> k) & 1u)) continue;
-                linkB[off + __popc(wm & ((1u << k) - 1u))] = packed[k];
             }
         }
     }
@@ -591,8 +602,7 @@ __device__ __forceinline__ void finish_item(const InstanceDev &I, const Par<R> &
     finish_cell<COLL, STORE, KIND, RED, WX, R>(I, g, P, rates, it.cell, it.x, it.inner, I.pull_off,
                                                it.inner ? I.push_off : nullptr, wm, it.off, fs, fd,
                                                reinterpret_cast<const R *>(I.linkc),
-                                               reinterpret_cast<const R *>(I.linkw), reinterpret_cast<T *>(I.linkB),
-                                               status, rd, rx, ry, rz, fm);
+                                               reinterpret_cast<const R *>(I.linkw), status, rd, rx, ry, rz, fm);
     if constexpr (RED) {
         acc.v[RED_DRHO] = rd;
         acc.v[RED_U + 0] = rx;

@@ -322,6 +322,7 @@ static void fill_dev(const Instance &in, InstanceDev &D)
     D.aseg = in.geo.aseg;
     D.n_active = (uint32_t)in.geo.n_active;
     D.fcell = in.geo.fcell;
+    D.flane = in.geo.flane;
     D.fwarp = in.geo.fwarp;
     D.n_fwarps = (uint32_t)in.geo.n_fwarps;
     D.n_fwarps_padded = (uint32_t)in.geo.n_fwarps_padded;

@@ -119,9 +119,10 @@ lbm_status lbm_debug_corrupt_worklist(lbm_ctx *ctx)
     if (!ctx || ctx->b.size() != 1) return fail(LBM_ERR_ARG, "ctx is NULL");
     if (!kChecked) return fail(LBM_ERR_STATE, "only the checked build (LBM_CHECKED) tests its indices");
     const Instance &in = ctx->b.at(0);
-    if (!in.geo.fcell || in.geo.n_fwarps < 1) return fail(LBM_ERR_STATE, "no fluid cells");
+    if (!in.geo.flane || in.geo.n_fwarps < 1) return fail(LBM_ERR_STATE, "no fluid cells");
     const uint32_t bad = (uint32_t)in.geo.ncells;  // one past the last cell
-    cudaError_t e = cudaMemcpyAsync(in.geo.fcell, &bad, sizeof(bad), cudaMemcpyHostToDevice, ctx->b.stream());
+    // the cell of the step kernels' first work-list entry (flane[0].x)
+    cudaError_t e = cudaMemcpyAsync(in.geo.flane, &bad, sizeof(bad), cudaMemcpyHostToDevice, ctx->b.stream());
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->b.stream());
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "cudaMemcpyAsync");
 }

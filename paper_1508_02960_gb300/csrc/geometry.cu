@@ -173,6 +173,32 @@ __global__ void fwarp_kernel(long long nw, const uint32_t *__restrict__ fcell, c
     }
 }
 
+// The step kernels' per-lane work-list entries, so that a step finds a cell's wall mask
+// and links without a dependent load: flane[32w + l] = {cell, wall mask | (first link -
+// the warp's first link) << 19}, and fwarp[w].y becomes the warp's first link (0 when it
+// has no boundary cell).  A warp's links are consecutive (boundary cells in cell order, each
+// with at most 18 links), so the offset fits in the 13 bits above the mask.
+__global__ void flane_kernel(long long nw, const uint32_t *__restrict__ fcell, const uint32_t *__restrict__ bmask,
+                             const uint32_t *__restrict__ boff, uint2 *__restrict__ fwarp, uint2 *__restrict__ flane)
+{
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nw; w += warps) {
+        const uint2 wd = fwarp[w];
+        const uint32_t c = fcell[w * 32 + lane];
+        uint32_t wm = 0u, off = 0u;
+        if ((wd.x >> lane) & 1u) {
+            const uint32_t b = wd.y + __popc(wd.x & ((1u << lane) - 1u));
+            wm = bmask[b];
+            off = boff[b];
+        }
+        const uint32_t base = wd.x ? __shfl_sync(0xffffffffu, off, __ffs(wd.x) - 1) : 0u;
+        flane[w * 32 + lane] = make_uint2(c, wm | ((wm ? off - base : 0u) << 19));
+        __syncwarp();
+        if (lane == 0) fwarp[w].y = base;
+    }
+}
+
 __global__ void seg_base_kernel(long long nseg, uint4 *__restrict__ seg, const unsigned long long *__restrict__ base)
 {
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < nseg;
@@ -451,6 +477,7 @@ void free_geometry(GeometryDev *g)
     cudaFree(g->seg);
     cudaFree(g->aseg);
     cudaFree(g->fcell);
+    cudaFree(g->flane);
     cudaFree(g->fwarp);
     cudaFree(g->bmask);
     cudaFree(g->boff);
@@ -600,12 +627,17 @@ cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_
             GEO_CHECK(cudaGetLastError());
         }
     }
+    // per-lane entries of the step kernels' work list (needs the boundary table's links)
+    GEO_CHECK(dev_alloc(&g->flane, sizeof(uint2) * 32 * g->n_fwarps_padded));
+    flane_kernel<<<grid_for(g->n_fwarps_padded * 32, 256), 256, 0, s>>>(g->n_fwarps_padded, g->fcell, g->bmask,
+                                                                          g->boff, g->fwarp, g->flane);
+    GEO_CHECK(cudaGetLastError());
     GEO_CHECK(cudaMemcpyAsync(h_ctr, d_ctr, sizeof(h_ctr), cudaMemcpyDeviceToHost, s));
     GEO_CHECK(cudaStreamSynchronize(s));
     g->n_fluid = (long long)h_ctr[0];
     g->n_links_cli = (long long)h_ctr[1];
     g->bytes = n + sizeof(uint4) * (g->nseg_padded + g->n_active_padded) +
-               (sizeof(uint32_t) * 32 + sizeof(uint2)) * g->n_fwarps_padded +
+               ((sizeof(uint32_t) + sizeof(uint2)) * 32 + sizeof(uint2)) * g->n_fwarps_padded +
                (sizeof(uint32_t) * 2 + sizeof(long long)) * g->n_boundary +
                (sizeof(double) + (c_double ? 8 : 4) * (wall >= 2 ? 1 + kLinkW : 1)) * g->n_links;
 

@@ -222,8 +222,10 @@ enum { STATUS_DIVERGED = 1u, STATUS_TIMEOUT = 2u, STATUS_BOUNDS = 4u };
 //   seg[s].z  index of the first such boundary cell of the segment in the boundary table
 // The step kernels take the fluid cells themselves, in cell order, 32 per warp: fcell[32w +
 // l] is the cell of lane l of fluid warp w (0xFFFFFFFF past the last fluid cell), fwarp[w].x
-// bit l set when that cell is a boundary cell, fwarp[w].y the boundary-table index of the
-// warp's first boundary cell.
+// bit l set when that cell is a boundary cell, fwarp[w].y the index of the warp's first
+// link; flane[32w + l] = {fcell[32w + l], wall mask | (first link - fwarp[w].y) << 19} (the
+// mask as bmask below, 0 for other cells), so that a step needs no dependent load to find
+// a cell's walls.
 // Boundary cell b: bmask[b] bit k set when x - e_k is solid (the pull of direction k hits
 // the wall), boff[b] the index of its first link; its links are ordered by k.  Link l:
 // linkc[l] = CLI coefficient (1-2q)/(1+2q) (0 where CLI falls back to SBB).
@@ -233,6 +235,7 @@ struct InstanceDev {
     const uint4 *seg;        // [nseg]
     const uint4 *aseg;       // [n_active_padded]: seg entries of segments holding fluid, .w = segment
     const uint32_t *fcell;   // [32 n_fwarps_padded]
+    const uint2 *flane;      // [32 n_fwarps_padded]
     const uint2 *fwarp;      // [n_fwarps_padded]
     const uint32_t *bmask;   // [n_boundary]
     const uint32_t *boff;    // [n_boundary]

@@ -501,15 +501,16 @@ struct WarpItem {
 };
 
 // Locate one work item: this lane's cell and coordinates, its wall mask and links, and
-// whether every lane is away from the y and z faces.  Reads only the work list and the
-// boundary table, which no step writes.
+// whether every lane is away from the y and z faces.  Reads only the work list (one entry
+// per warp and one per lane, no dependent load), which no step writes.
 template <typename R>
 __device__ __forceinline__ void locate_item(const InstanceDev &I, const Par<R> &P, uint32_t w, int lane, WarpItem &it)
 {
     const uint64_t keep = l2_keep_policy();
     const bool w_ok = checked(I, w, I.n_fwarps_padded);
     it.wd = w_ok ? ld_keep(I.fwarp + w, keep) : make_uint2(0u, 0u);
-    it.cell = w_ok ? ld_keep(I.fcell + (w * 32u + (uint32_t)lane), keep) : 0xFFFFFFFFu;
+    const uint2 e = w_ok ? ld_keep(I.flane + (w * 32u + (uint32_t)lane), keep) : make_uint2(0xFFFFFFFFu, 0u);
+    it.cell = e.x;
     if (it.cell != 0xFFFFFFFFu && !checked(I, it.cell, I.n32)) it.cell = 0xFFFFFFFFu;
     const bool live = it.cell != 0xFFFFFFFFu;
     const uint32_t yz = fast_div(it.cell, P.dnx);
@@ -518,17 +519,10 @@ __device__ __forceinline__ void locate_item(const InstanceDev &I, const Par<R> &
     const uint32_t y = yz - z * P.ny;
     const bool in_yz = !live || (y - 1u < P.ny - 2u && z - 1u < P.nz - 2u);
     it.inner = __all_sync(0xffffffffu, in_yz);
-    it.wm = 0u;
-    it.off = 0u;
-    if ((it.wd.x >> lane) & 1u) {
-        const uint32_t b = it.wd.y + __popc(it.wd.x & ((1u << lane) - 1u));
-        if (checked(I, b, I.n_boundary)) {
-            it.wm = ld_keep(I.bmask + b, keep);
-            it.off = ld_keep(I.boff + b, keep);
-            // every link of the cell within the link tables
-            if (!checked(I, it.off + __popc(it.wm), I.n_links + 1u)) it.wm = 0u;
-        }
-    }
+    it.wm = e.y & 0x7FFFFu;
+    it.off = it.wd.y + (e.y >> 19);
+    // every link of the cell within the link tables
+    if (it.wm && !checked(I, it.off + __popc(it.wm), I.n_links + 1u)) it.wm = 0u;
 }
 
 // Issue the 19 pulls of a located work item into raw[] (storage type, converted in
@@ -710,7 +704,11 @@ __global__ void __launch_bounds__(kStepWarps * 32, step_min_blocks<STORE, COLL, 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int t = blockIdx.x;
     if (t >= ntiles) return;
-    const TileDev tile = tiles[t];
+    // a single instance's tiles are consecutive: tile t holds work items kTileSegs t ...
+    // (its table entry holds the same, so that no load precedes the work list's)
+    TileDev tile;
+    if constexpr (BATCH) tile = tiles[t];
+    else tile = TileDev{0, t, (long long)t * kTileSegs};
     const InstanceDev &I = instance_of<BATCH>(table, one, tile.inst);
     const Par<R> P = load_par<R>(I);
     R rates[Q];

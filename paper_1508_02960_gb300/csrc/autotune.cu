@@ -52,7 +52,7 @@ void read_file(const std::string &path)
         Tuned t;
         if (!std::getline(ls, key, '\t')) continue;
         if (!(ls >> t.block >> t.ms[0] >> t.ms[1])) continue;
-        if (t.block != 32 * kTileSegs && t.block != kBrickCells) continue;
+        if (t.block != kTileApiCells && t.block != kBrickCells) continue;
         g_cache[key] = t;
     }
 }
@@ -121,7 +121,7 @@ double time_candidate(const lbm_desc &d0, cudaStream_t s, int block_cells, long 
 
 lbm_status autotune_block(Batch &b, const lbm_desc &d, cudaStream_t s)
 {
-    if (b.size() != 1) return b.set_block(32 * kTileSegs);
+    if (b.size() != 1) return b.set_block(kTileApiCells);
     const long long n_fluid = b.at(0).geo.n_fluid;
     const std::string key = make_key(d, n_fluid);
     const std::string file = cache_file();
@@ -140,9 +140,9 @@ lbm_status autotune_block(Batch &b, const lbm_desc &d, cudaStream_t s)
         }
     }
     if (!found) {
-        t.ms[0] = time_candidate(d, s, 32 * kTileSegs, n_fluid);
+        t.ms[0] = time_candidate(d, s, kTileApiCells, n_fluid);
         t.ms[1] = bricks_allowed(d) ? time_candidate(d, s, kBrickCells, n_fluid) : -1.0;
-        t.block = (t.ms[1] > 0 && (t.ms[0] <= 0 || t.ms[1] < t.ms[0])) ? kBrickCells : 32 * kTileSegs;
+        t.block = (t.ms[1] > 0 && (t.ms[0] <= 0 || t.ms[1] < t.ms[0])) ? kBrickCells : kTileApiCells;
         for (double &m : t.ms) m = std::max(m, 0.0);
         set_error("");  // a dropped candidate is not an error of the context
         std::lock_guard<std::mutex> lk(g_mu);

@@ -87,7 +87,7 @@ lbm_status validate_desc(const lbm_desc &d)
     if (d.magic_lambda < 0 || !std::isfinite(d.magic_lambda)) return fail(LBM_ERR_ARG, "magic_lambda must be >= 0");
     if (d.mrt_energy_ratio < 0 || !std::isfinite(d.mrt_energy_ratio))
         return fail(LBM_ERR_ARG, "mrt_energy_ratio must be >= 0");
-    if (d.block_cells != 0 && d.block_cells != LBM_BLOCK_AUTO && d.block_cells != 32 * kTileSegs &&
+    if (d.block_cells != 0 && d.block_cells != LBM_BLOCK_AUTO && d.block_cells != kTileApiCells &&
         d.block_cells != kBrickCells)
         return fail(LBM_ERR_ARG, "block_cells: 0 or 128 (tiles of fluid cells), 256 (TMA bricks) or -1 (autotune)");
     if (d.block_cells == kBrickCells &&
@@ -289,7 +289,7 @@ lbm_status Batch::set_block(int block_cells)
 {
     int mode;
     if (block_cells == 0) mode = 0;
-    else if (block_cells == 32 * kTileSegs) mode = 1;
+    else if (block_cells == kTileApiCells) mode = 1;
     else if (block_cells == kBrickCells) mode = 2;
     else return fail(LBM_ERR_ARG, "block_cells: 0 or 128 (tiles of fluid cells) or 256 (TMA bricks)");
     if (mode != step_mode_) {
@@ -369,6 +369,16 @@ static void fill_dev(const Instance &in, InstanceDev &D)
     }
     D.delta_rho = d.delta_rho;
     D.rho0 = d.rho0;
+    D.omega_f = (float)D.omega;
+    D.omega_m_f = (float)D.omega_m;
+    D.rho0_f = (float)D.rho0;
+    D.irho0_f = 1.0f / D.rho0_f;
+    D.delta_rho_f = (float)D.delta_rho;
+    D.irho0 = 1.0 / D.rho0;
+    for (int i = 0; i < Q; ++i) {
+        D.rate_f[i] = (float)D.s[i] / (float)mrt_norm2(i);
+        D.rate_d[i] = D.s[i] / (double)mrt_norm2(i);
+    }
 }
 
 // cuTensorMapEncodeTiled, looked up once through the runtime (no link to the driver library)

@@ -68,7 +68,7 @@ public:
     lbm_status sync();
     void fill_info(int i, lbm_info *out) const;
     long long launches() const { return launches_; }
-    int block_cells() const { return tma_ ? kBrickCells : 32 * kTileSegs; }
+    int block_cells() const { return tma_ ? kBrickCells : kTileApiCells; }
     int aa_phase() const { return aa_phase_; }
     cudaStream_t stream() const { return stream_; }
     long long fluid_cells() const;
@@ -107,7 +107,7 @@ private:
     unsigned *h_status_ = nullptr;    // pinned [n]
     int capacity_ = 0;
     int ntiles_ = 0;
-    int block_ = 32 * kTileSegs;      // cells per chunk of the state kernels
+    int block_ = 32 * kStepWarps;      // cells per chunk of the state kernels
     int step_mode_ = 0;               // 0 (default) and 1: tiles of fluid cells; 2: TMA bricks
     // TMA brick kernel (single instance, A-B layout, box a multiple of the brick)
     bool tma_ = false;

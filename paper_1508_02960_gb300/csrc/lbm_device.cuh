@@ -260,6 +260,14 @@ struct InstanceDev {
     double omega_m;          // TRT omega-
     double s[Q];             // MRT relaxation rates
     double delta_rho, rho0;
+    // the same parameters as the step kernels use them, computed on the host so that no
+    // thread converts or divides them: single precision for the formats that collide in FP32
+    // (each the correctly rounded single of the double above, 1/rho0 the correctly rounded
+    // quotient), and the MRT rates divided by |M_i|^2 in both precisions
+    float omega_f, omega_m_f, rho0_f, irho0_f, delta_rho_f;
+    double irho0;
+    float rate_f[Q];
+    double rate_d[Q];
     // sizes the checked build tests indices against, and the batch's sticky error word
     // (STATUS_BOUNDS, STATUS_TIMEOUT), which the host reads with the reductions
     uint32_t n_fwarps_padded, n_boundary, n_links;
@@ -315,10 +323,12 @@ constexpr int kBrickX = 32, kBrickY = 2, kBrickZ = 4;
 constexpr int kBrickCells = kBrickX * kBrickY * kBrickZ;
 constexpr int kBrickStages = 2;
 
-// Step-kernel tiling: a tile is kStepWarps consecutive work items (32 fluid cells each),
-// one per warp of a kStepWarps-warp block.
+// Step-kernel tiling: a tile is kTileSegs consecutive work items (32 fluid cells each), one
+// per warp of a kStepWarps-warp block.  kTileApiCells is the block_cells value of the C ABI
+// that selects this kernel.
 constexpr int kStepWarps = 4;
 constexpr int kTileSegs = kStepWarps;
+constexpr int kTileApiCells = 32 * kTileSegs;
 enum { COLL_SRT = 0, COLL_TRT = 1, COLL_MRT = 2 };
 
 // FP64 reduction slots per tile and per instance: sum of (rho - rho0), of u_x, u_y, u_z

@@ -130,7 +130,7 @@ cudaError_t launch_final_reduce(const InstanceDev *table, const int *tile_count,
 void set_error(const std::string &msg);
 
 constexpr int kMaxWarpsPerBlock = 32;
-constexpr int kMinChunkSegs = kTileSegs;  // smallest tile (work items): sizes the partial sums
+constexpr int kMinChunkSegs = kStepWarps;  // smallest tile (work items) of any kernel: sizes the partial sums
 constexpr long long kDirPad = 0;       // extra elements between direction arrays
 // Sphere centres may lie at most this many box lengths from the origin along each axis
 // (the voxeliser folds displacements into the box one box length at a time).

@@ -76,11 +76,19 @@ template <typename R> __device__ __forceinline__ Par<R> load_par(const InstanceD
     p.nz = I.nz;
     p.dnx = I.div_nx;
     p.dny = I.div_ny;
-    p.omega = R(I.omega);
-    p.omega_m = R(I.omega_m);
-    p.rho0 = R(I.rho0);
-    p.irho0 = R(1) / R(I.rho0);
-    p.dshift = R(I.delta_rho);
+    if constexpr (sizeof(R) == sizeof(float)) {
+        p.omega = I.omega_f;
+        p.omega_m = I.omega_m_f;
+        p.rho0 = I.rho0_f;
+        p.irho0 = I.irho0_f;
+        p.dshift = I.delta_rho_f;
+    } else {
+        p.omega = I.omega;
+        p.omega_m = I.omega_m;
+        p.rho0 = I.rho0;
+        p.irho0 = I.irho0;
+        p.dshift = I.delta_rho;
+    }
     p.sc = I.scale;
     p.isc = I.inv_scale;
     p.wall = I.wall;
@@ -598,12 +606,12 @@ __device__ __forceinline__ void finish_item(const InstanceDev &I, const Par<R> &
                                                reinterpret_cast<const R *>(I.linkc),
                                                reinterpret_cast<const R *>(I.linkw), status, rd, rx, ry, rz, fm);
     if constexpr (RED) {
-        acc.v[RED_DRHO] = rd;
-        acc.v[RED_U + 0] = rx;
-        acc.v[RED_U + 1] = ry;
-        acc.v[RED_U + 2] = rz;
+        acc.v[RED_DRHO] += rd;
+        acc.v[RED_U + 0] += rx;
+        acc.v[RED_U + 1] += ry;
+        acc.v[RED_U + 2] += rz;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) acc.v[RED_F + d] = fm[d];
+        for (int d = 0; d < 3; ++d) acc.v[RED_F + d] += fm[d];
     }
 }
 
@@ -666,7 +674,10 @@ template <int COLL, typename R> __device__ __forceinline__ void load_rates(const
 {
     if constexpr (COLL == COLL_MRT) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) rates[i] = R(I.s[i]) / R(mrt_norm2(i));
+        for (int i = 0; i < Q; ++i) {
+            if constexpr (sizeof(R) == sizeof(float)) rates[i] = I.rate_f[i];
+            else rates[i] = I.rate_d[i];
+        }
     }
 }
 

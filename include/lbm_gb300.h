@@ -339,8 +339,10 @@ LBM_API lbm_status lbm_synchronize(lbm_ctx *ctx);
  * the library, held by every GPU that loads it.  n_cells is limited to 268,435,456
  * (8192 blocks of 32768 cells); larger fields return LBM_ERR_ARG.  The first call on
  * each device looks up the scratch address (cudaGetSymbolAddress) and should come before
- * any stream capture.  Calls share the scratch: calls that overlap on the GPU race.
- * Returns without waiting for the kernels. */
+ * any stream capture.  The address is kept, per device ordinal, for the life of the
+ * process: after cudaDeviceReset on a device it is stale, so a process that resets a
+ * device must not call this entry point on it again.  Calls share the scratch: calls that
+ * overlap on the GPU race.  Returns without waiting for the kernels. */
 LBM_API lbm_status lbm_moment_sums_f64_noalloc(const double *f_dev, const uint8_t *solid_dev, int64_t n_cells,
                                                double rho0, double *sums_dev, void *cuda_stream);
 

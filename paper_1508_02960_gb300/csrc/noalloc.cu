@@ -11,10 +11,12 @@
 // each, 256 KiB in total).  Every GPU that loads the library holds it until the process
 // exits.  Host code cannot use the array's name as a device address; the address is
 // looked up once per device (cudaGetSymbolAddress, with that device current) by the first
-// call on that device, which should therefore happen before any stream capture.  All
-// calls share the array: a call only reads slots that it wrote itself earlier in the same
-// call, so nothing has to start at zero, but two calls that overlap on the GPU (on
-// different streams without ordering) race on it.
+// call on that device, which should therefore happen before any stream capture.  The
+// address is kept per device ordinal until the process exits; a cudaDeviceReset unloads the
+// module, so after one the kept address is stale and this entry point must not be called
+// on that device again.  All calls share the array: a call only reads slots that it wrote
+// itself earlier in the same call, so nothing has to start at zero, but two calls that
+// overlap on the GPU (on different streams without ordering) race on it.
 #include <mutex>
 
 #include "batch.h"

@@ -10,6 +10,8 @@ import pytest
 
 from paper_1508_02960_gb300 import inputs as I
 
+import half_bounds as HB
+
 pytestmark = pytest.mark.gpu
 
 
@@ -54,6 +56,36 @@ def test_bench_cell_128_fp32_against_oracle(capi, orc, layout):
     assert _rel(f, ref, solid) <= 1e-5
     F = np.array([o["F_x"], o["F_y"], o["F_z"]])
     assert np.abs(F - Fref).max() <= 2e-4 * np.abs(Fref).max(), (F, Fref)
+
+
+@pytest.mark.parametrize("fmt", ["F16DEV", "BF16DEV"])
+@pytest.mark.parametrize("layout", ["AB", "AA"])
+def test_bench_cell_128_half_storage_against_oracle(capi, orc, fmt, layout):
+    """The 16-bit deviation formats on the benchmark cell (the kernels of the 512^3 BF16 AA
+    configuration at a size the oracle can run): two steps, each against one oracle step
+    from the GPU's exported state before it, so that both in-place step kinds run at full
+    size."""
+    g = I.centred_sphere(128, 60.0)
+    solid = orc.voxelize(g.shape, g.spheres)
+    q = orc.wall_distances(solid, g.spheres)
+    _, w, _ = orc.lattice()
+    s = 20
+    dev, ulp = HB.storable(fmt, I.noise((19,) + solid.shape, 29) * 2e-4, s)
+    f0 = w[:, None, None, None] + dev
+    f0[:, solid == 1] = 0.0
+    del dev
+    kw = dict(tau=0.6, delta_rho=2e-5, magic_lambda=3 / 16, collision=capi.TRT, wall=capi.CLI)
+    with capi.Context(spheres=g.spheres, shape=g.shape, storage=getattr(capi, fmt),
+                      layout=getattr(capi, "LAYOUT_" + layout), dev_scale_log2=s if fmt == "F16DEV" else 0,
+                      **kw) as ctx:
+        ctx.set_populations(f0)
+        prev = f0
+        for i in range(2):
+            ctx.step(1)
+            f = ctx.get_populations()
+            fref, _, _ = orc.run(solid, prev, 1, q=q, **kw)
+            HB.check_step(orc, solid, w, f, fref, prev, ulp, walls=True)
+            prev = f
 
 
 @pytest.mark.parametrize("which", ["sphere", "pack40"])

@@ -15,6 +15,8 @@ import pytest
 
 from paper_1508_02960_gb300 import inputs as I
 
+import half_bounds as HB
+
 pytestmark = pytest.mark.gpu
 
 
@@ -148,7 +150,7 @@ def test_step_parity_matrix(capi, orc, geom, layout, storage, coll, wall):
 
 
 @pytest.mark.parametrize("geom", ["ragged", "staged"])
-@pytest.mark.parametrize("storage", ["F64", "F32"])
+@pytest.mark.parametrize("storage", ["F64", "F32", "F16DEV", "BF16DEV"])
 @pytest.mark.parametrize("wall", ["SBB", "CLI"])
 def test_aa_matches_ab_bitwise(capi, orc, geom, storage, wall):
     g = GEOMS[geom]
@@ -172,74 +174,64 @@ def test_aa_matches_ab_bitwise(capi, orc, geom, storage, wall):
 
 
 # ---------------------------------------------------------------------------------------
-# Reduced-precision storage: one step, within one unit in the last place of the format
+# Reduced-precision storage: within one unit in the last place of the format per step
 # ---------------------------------------------------------------------------------------
-def _round_bf16(x):
-    """Round-to-nearest-even of float64 values to bfloat16 (through float32)."""
-    f = np.asarray(x, dtype=np.float32)
-    b = f.view(np.uint32).astype(np.uint64)
-    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
-    return b.astype(np.uint32).view(np.float32).astype(np.float64)
-
-
-def _ulp_bf16(x):
-    e = np.floor(np.log2(np.maximum(np.abs(x), 1e-38)))
-    return 2.0 ** (e - 7)
-
-
-def _ulp_f16(x):
-    e = np.floor(np.log2(np.maximum(np.abs(x), 2.0 ** -14)))
-    return 2.0 ** (e - 10)
-
-
 @pytest.mark.parametrize("geom", ["ragged", "staged"])
 @pytest.mark.parametrize("fmt", ["F16DEV", "BF16DEV"])
+@pytest.mark.parametrize("layout", ["AB", "AA"])
 @pytest.mark.parametrize("coll", ["TRT", "MRT"])
 @pytest.mark.parametrize("wall", ["SBB", "CLI"])
-def test_half_storage_one_step(capi, orc, geom, fmt, coll, wall):
+def test_half_storage_one_step(capi, orc, geom, fmt, layout, coll, wall):
     g = GEOMS[geom]
     solid = orc.voxelize(g.shape, g.spheres)
     q = orc.wall_distances(solid, g.spheres)
     _, w, _ = orc.lattice()
     s = 20
-    scale = 2.0 ** s if fmt == "F16DEV" else 1.0
-    xi = I.noise((19,) + solid.shape, 3) * 2e-4
-    if fmt == "F16DEV":
-        dev = np.float16(xi * scale).astype(np.float64) / scale        # exactly storable
-        ulp = lambda v: _ulp_f16(v * scale) / scale
-    else:
-        dev = _round_bf16(xi)
-        ulp = _ulp_bf16
+    dev, ulp = HB.storable(fmt, I.noise((19,) + solid.shape, 3) * 2e-4, s)
     f0 = w[:, None, None, None] + dev
     f0[:, solid == 1] = 0.0
     kw = dict(tau=0.66, delta_rho=2e-4, collision=getattr(capi, coll), wall=getattr(capi, wall))
     with capi.Context(spheres=g.spheres, shape=g.shape, storage=getattr(capi, fmt),
-                      dev_scale_log2=s if fmt == "F16DEV" else 0, **kw) as ctx:
+                      layout=getattr(capi, "LAYOUT_" + layout), dev_scale_log2=s if fmt == "F16DEV" else 0,
+                      **kw) as ctx:
         ctx.set_populations(f0)
         assert np.abs(ctx.get_populations() - f0).max() < 1e-17       # import is exact
         ctx.step(1)
         f = ctx.get_populations()
     fref, _, _ = orc.run(solid, f0, 1, q=q, **kw)
-    m = solid == 0
-    g_gpu = (f - w[:, None, None, None])[:, m]
-    g_ref = (fref - w[:, None, None, None])[:, m]
-    err = np.abs(g_gpu - g_ref)
-    # FP32 collision error: a few dozen roundings of operands up to max|g| (floor for
-    # results so small that their storage ulp is below it)
-    floor = 64 * 2.0 ** -24 * np.abs(g_ref).max()
-    bound = ulp(g_ref) * 1.0001 + floor
-    if wall == "CLI":
-        # A-B layout: the own-cell part C - c B of a cut link's rule waits one step in the
-        # solid slot, stored in the format (one more rounding of a value up to 2 max|g| of
-        # the cell), and the collision spreads that error over the cell's outputs
-        e, _, _ = orc.lattice()
-        wallcell = np.zeros(solid.shape, bool)
-        for k in range(1, 19):
-            wallcell |= np.roll(solid, shift=(e[k, 2], e[k, 1], e[k, 0]), axis=(0, 1, 2)) == 1
-        wallcell &= solid == 0
-        amax = np.abs(dev).max(axis=0)
-        bound = bound + np.where(wallcell, 4 * ulp(2 * amax), 0.0)[m][None, :]
-    assert np.all(err <= bound)
+    # from an imported state only CLI's own-cell part is rounded once more (SBB's is exact)
+    HB.check_step(orc, solid, w, f, fref, f0, ulp, walls=(wall == "CLI"))
+
+
+@pytest.mark.parametrize("geom", ["ragged", "staged"])
+@pytest.mark.parametrize("fmt", ["F16DEV", "BF16DEV"])
+@pytest.mark.parametrize("layout", ["AB", "AA"])
+@pytest.mark.parametrize("coll", ["TRT", "MRT"])
+@pytest.mark.parametrize("wall", ["SBB", "CLI"])
+def test_half_storage_step_by_step(capi, orc, geom, fmt, layout, coll, wall):
+    """Six consecutive steps (each AA step kind three times), each compared with one oracle
+    step from the GPU's own exported state before it: the per-step bound holds at every step
+    and in both in-place phases, without the growth a multi-step comparison would need."""
+    g = GEOMS[geom]
+    solid = orc.voxelize(g.shape, g.spheres)
+    q = orc.wall_distances(solid, g.spheres)
+    _, w, _ = orc.lattice()
+    s = 20
+    dev, ulp = HB.storable(fmt, I.noise((19,) + solid.shape, 8) * 2e-4, s)
+    f0 = w[:, None, None, None] + dev
+    f0[:, solid == 1] = 0.0
+    kw = dict(tau=0.66, delta_rho=2e-4, collision=getattr(capi, coll), wall=getattr(capi, wall))
+    with capi.Context(spheres=g.spheres, shape=g.shape, storage=getattr(capi, fmt),
+                      layout=getattr(capi, "LAYOUT_" + layout), dev_scale_log2=s if fmt == "F16DEV" else 0,
+                      **kw) as ctx:
+        ctx.set_populations(f0)
+        prev = f0
+        for i in range(6):
+            ctx.step(1)
+            f = ctx.get_populations()
+            fref, _, _ = orc.run(solid, prev, 1, q=q, **kw)
+            HB.check_step(orc, solid, w, f, fref, prev, ulp, walls=(i > 0 or wall == "CLI"))
+            prev = f
 
 
 # ---------------------------------------------------------------------------------------

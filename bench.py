@@ -1,16 +1,19 @@
 """Benchmark of the fused D3Q19 sphere-pack step on GB300.
 
-One benchmark step = one pass of the whole hot path over the workload: CHECK_INTERVAL
-fused stream-collide time steps (pull streaming, periodic pressure shift, CLI walls,
-TRT collision), the FP64 volume-averaged velocity reduction of the last of them, and
-the host convergence/observable evaluation.  The metric is fluid-cell million lattice
-updates per second (MLUPS) and the fraction of the HBM roofline the step kernel
-reaches (19 reads + 19 writes of the stored format per fluid-cell update).
+One benchmark step = one pass of the whole hot path over the workload: TIME_STEPS fused
+stream-collide time steps (pull streaming, periodic pressure shift, CLI walls, TRT
+collision, store), the FP64 volume-averaged velocity reduction of the last of them, and the
+host convergence/observable evaluation.  The metric is fluid-cell million lattice updates per
+second (MLUPS) and the fraction of the HBM roofline the step kernel reaches (19 reads + 19
+writes of the stored format per fluid-cell update).
 
-Workload (default): 128^3 periodic simple-cubic cell, sphere radius 60 (porosity
-0.569), TRT with Lambda = 3/16, CLI walls with analytic q, FP32 storage, A-B layout,
-tau = 0.6, pressure drop for Re_p ~ 1.  Synthetic, seeded; inputs (318 MB of
-populations) exceed the 126 MB L2, so no flush is needed between steps.
+Workload (default): 128^3 periodic simple-cubic cell, sphere radius 60 (porosity 0.569),
+TRT with Lambda = 3/16, CLI walls with analytic q, FP32 storage, in-place AA layout
+(159 MB of populations; the A-B layout on the same cell is timed beside it), tau = 0.6,
+pressure drop for Re_p ~ 1.  Synthetic, seeded.  The touched state (fluid populations,
+91 MB, plus wall slots) is below the 126 MB L2, so every benchmark step is preceded by a
+write of 256 MB that flushes L2; within a benchmark step the state stays resident as it
+does in any run.
 
 Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 For N > 1 it runs under torchrun, one independent replica per GPU (the single-cell
@@ -30,7 +33,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-CHECK_INTERVAL = 100
+TIME_STEPS = 1000          # fused time steps per benchmark step (one FP64 reduction each)
+L2_FLUSH_BYTES = 256 << 20
 
 WORKLOADS = {
     # name: (L, r, storage, layout, collision, wall, tau, delta_rho)
@@ -78,7 +82,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
             return
@@ -474,9 +478,10 @@ def aggregate_over_ranks(units: float, seconds: float, world: int, device: str =
     return float(t.item()), float(m.item())
 
 
-def cpu_baseline(workload: str, target_s: float = 12.0) -> dict:
+def cpu_baseline(workload: str, target_s: float = 10.0, one_core_s: float = 5.0) -> dict:
     """The FP64 oracle (as it stands) timed on this host's cores on a bounded sample of the
-    same workload: the same geometry and operators for as many steps as fit ~target_s."""
+    same workload: the same geometry and operators for as many steps as fit ~target_s with
+    every core, then again on one core for ~one_core_s."""
     import numpy as np
 
     import oracle
@@ -495,10 +500,23 @@ def cpu_baseline(workload: str, target_s: float = 12.0) -> dict:
     t0 = time.perf_counter()
     f, _, _ = oracle.run(solid, f, steps, **kw)
     dt = time.perf_counter() - t0
+    cores = oracle.max_threads()
+    # the same oracle on one core
+    oracle.set_threads(1)
+    t0 = time.perf_counter()
+    f, _, _ = oracle.run(solid, f, 1, **kw)
+    t1c = time.perf_counter() - t0
+    steps1 = max(1, min(50, int(one_core_s / max(t1c, 1e-3))))
+    t0 = time.perf_counter()
+    f, _, _ = oracle.run(solid, f, steps1, **kw)
+    dt1 = time.perf_counter() - t0
+    oracle.set_threads(cores)
     del f
-    return {"value": nf * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.max_threads(), "kind": "oracle",
+    return {"value": nf * steps / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
             "sample": f"{L}^3 r={r:g} {coll}/{wall} FP64 oracle, {steps} time steps from rest "
-                      f"({nf} fluid cells), OpenMP over z", "seconds": round(dt, 3)}
+                      f"({nf} fluid cells), OpenMP over z", "seconds": round(dt, 3),
+            "one_core": {"value": nf * steps1 / dt1 / 1e6, "unit": "MLUPS", "cores": 1,
+                         "sample": f"{steps1} further time steps of the same run", "seconds": round(dt1, 3)}}
 
 
 def run_reference(args, rank, world):
@@ -522,7 +540,7 @@ def run_reference(args, rank, world):
     f, _, _ = oracle.run(solid, f, 1, **kw)
     t1 = time.perf_counter() - t0
     # size each sample so that the whole run stays within about two minutes
-    per = max(1, min(CHECK_INTERVAL, int(100.0 / max(args.steps + args.warmup, 1) / max(t1, 1e-3))))
+    per = max(1, min(TIME_STEPS, int(100.0 / max(args.steps + args.warmup, 1) / max(t1, 1e-3))))
     for _ in range(args.warmup):
         f, _, _ = oracle.run(solid, f, per, **kw)
     t0 = time.perf_counter()
@@ -553,8 +571,8 @@ def other_layout(workload: str):
 
 def time_device(workload, args, stream):
     """Device-resident timing of a workload (warm-up, then args.steps graph launches of
-    CHECK_INTERVAL steps with CUDA events on the launching stream); the same
-    procedure as the headline's timed region."""
+    TIME_STEPS steps, each after an L2 flush, with CUDA events on the launching stream); the
+    same procedure as the headline's timed region."""
     import torch
 
     from paper_1508_02960_gb300 import capi
@@ -568,21 +586,23 @@ def time_device(workload, args, stream):
         nf = ctx.info()["n_fluid"]
         ctx.init_equilibrium()
         for _ in range(args.warmup + 2):
-            ctx.step(CHECK_INTERVAL)
+            ctx.step(TIME_STEPS)
             ctx.observables()
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
-        for _ in range(args.steps):
-            ctx.step(CHECK_INTERVAL)
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ctx.step(TIME_STEPS)
             ctx.observables()
         t1.record(stream)
         torch.cuda.synchronize()
         ms = t0.elapsed_time(t1)
-    value = nf * CHECK_INTERVAL * args.steps / (ms * 1e-3) / 1e6
+    value = nf * TIME_STEPS * args.steps / (ms * 1e-3) / 1e6
     peak, _ = load_peaks()
-    achieved = 38.0 * BYTES[storage] * nf * CHECK_INTERVAL * args.steps / (ms * 1e-3) / 1e9
+    achieved = 38.0 * BYTES[storage] * nf * TIME_STEPS * args.steps / (ms * 1e-3) / 1e9
     return {"workload": workload, "layout": layout, "value": value, "unit": "MLUPS",
             "ms_per_step": ms / args.steps, "roofline_frac": achieved / peak}
 
@@ -606,15 +626,16 @@ def run_gpu(args, rank, world, local):
     info = ctx.info()
     nf = info["n_fluid"]
     ctx.init_equilibrium()
-    ctx.step(2 * CHECK_INTERVAL)
+    ctx.step(2 * TIME_STEPS)
     ctx.observables()
 
     # ---- device-resident timing -------------------------------------------------------
     for _ in range(args.warmup):
-        ctx.step(CHECK_INTERVAL)
+        ctx.step(TIME_STEPS)
         ctx.observables()
     launches0 = ctx.info()["kernel_launches"]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     clocks = ClockSampler(local)
     barrier(world)
     torch.cuda.synchronize()
@@ -623,8 +644,9 @@ def run_gpu(args, rank, world, local):
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
     for i in range(args.steps):
+        flush.fill_(float(i))                 # 256 MB write: nothing of the state left in L2
         ev[i][0].record(stream)
-        ctx.step(CHECK_INTERVAL)              # graph: CHECK_INTERVAL fused steps + reduction
+        ctx.step(TIME_STEPS)                  # graph: TIME_STEPS fused steps + reduction
         ev[i][1].record(stream)
         obs = ctx.observables()               # FP64 sums to host, convergence quantities
     t_end.record(stream)
@@ -634,13 +656,13 @@ def run_gpu(args, rank, world, local):
     launches = ctx.info()["kernel_launches"] - launches0
     total_ms = t_start.elapsed_time(t_end)
     graph_ms = [a.elapsed_time(b) for a, b in ev]
-    updates = float(nf) * CHECK_INTERVAL * args.steps
+    updates = float(nf) * TIME_STEPS * args.steps
     all_updates, total_s = aggregate_over_ranks(updates, total_ms * 1e-3, world)
     total_ms = total_s * 1e3
     value = all_updates / total_s / 1e6
 
     # per-launch duration of the step kernel inside the timed region
-    kernel_ms = statistics.mean(graph_ms) / CHECK_INTERVAL
+    kernel_ms = statistics.mean(graph_ms) / TIME_STEPS
     alg_bytes = 38.0 * es * nf
     peak, peak_kind = load_peaks()
     achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
@@ -660,7 +682,7 @@ def run_gpu(args, rank, world, local):
             ctx.apply_staged_state()          # this step's input becomes the state
             if i + 1 < n:
                 ctx.stage_state(s_host)       # H2D of the next step's input, during this step
-            ctx.step(CHECK_INTERVAL)
+            ctx.step(TIME_STEPS)
             ctx.observables()                 # D2H of the step's result
 
     e2e_steps(2)
@@ -688,8 +710,10 @@ def run_gpu(args, rank, world, local):
             "data": "synthetic",
             "config": {"workload": args.workload, "cells": L ** 3, "fluid_cells": nf, "sphere_radius": r,
                        "storage": storage, "layout": layout, "collision": coll, "wall": wall, "tau": tau,
-                       "delta_rho": dr, "time_steps_per_step": CHECK_INTERVAL, "block_cells": info["block_cells"],
-                       "l2": "inputs larger than L2 (populations %.0f MB)" % (info["bytes_populations"] / 1e6),
+                       "delta_rho": dr, "time_steps_per_step": TIME_STEPS, "block_cells": info["block_cells"],
+                       "l2": "L2 flushed before every benchmark step (256 MB write); populations %.0f MB, "
+                             "%.0f MB of them touched per time step" % (info["bytes_populations"] / 1e6,
+                                                                          38.0 * es * nf / 2e6),
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
@@ -717,7 +741,7 @@ def run_gpu(args, rank, world, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))

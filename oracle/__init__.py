@@ -254,3 +254,97 @@ def fit_barree_conway(re, kstar, init=None):
     p = np.array([m_of(sol.x[0]), np.exp(sol.x[1]), np.exp(sol.x[2]), np.exp(sol.x[3])])
     return p, float(np.sqrt(np.mean(sol.fun ** 2)))
 
+
+
+def time_average(solid, f, n_samples: int, interval: int, *, q=None, **kw):
+    """Time average of the volume-averaged velocity and of the drag (Sec. 4: the flow is
+    averaged over a period of the developed flow; the drag of the resolution study is
+    time-averaged): advance n_samples * interval steps, take U_sup = sum u_x / (nx ny nz) and
+    the drag F_D of the last step of every interval, average both in FP64.
+    Returns (f, U_mean, F_mean[3])."""
+    solid = np.ascontiguousarray(solid, dtype=np.uint8)
+    ncell = solid.size
+    U_sum, F_sum = 0.0, np.zeros(3)
+    for _ in range(int(n_samples)):
+        F = np.zeros(3)
+        f, sums, _ = run(solid, f, int(interval), q=q, force=F, **kw)
+        U_sum += sums[1] / ncell
+        F_sum += F
+    return f, U_sum / n_samples, F_sum / n_samples
+
+
+def developed_average(solid, f, *, min_spinup_ft, max_spinup_ft, drag_tol, average_ft, samples_per_ft,
+                      max_steps, q=None, **kw):
+    """Developed-flow average (Sec. 4: averaging starts once the drag on the spheres has
+    converged, then covers a number of flow-through times), in the reading that a
+    flow-through time is T = nx / U_sup of the latest sample:
+      1. one sample of nx steps gives the first T;
+      2. spin-up in windows of one T, each sampled samples_per_ft times (sub-intervals of
+         round(T / samples_per_ft) steps); the window's mean drag F_x is compared with the
+         previous window's; T is renewed after every window; the flow is developed when at
+         least min_spinup_ft flow-through times have passed and the relative change is below
+         drag_tol; the spin-up ends undeveloped after max_spinup_ft flow-through times;
+      3. the average: round(average_ft * samples_per_ft) samples, round(T / samples_per_ft)
+         steps apart, of U_sup and the drag, averaged in FP64.
+    Returns a dict with the averaged U_sup and F, the spin-up and averaging step counts and
+    whether the drag converged; max_steps caps the whole run (status 'capped')."""
+    solid = np.ascontiguousarray(solid, dtype=np.uint8)
+    nz, ny, nx = solid.shape
+    ncell = solid.size
+    state = {"f": f, "total": 0, "U": 0.0, "F": np.zeros(3)}
+
+    def sample(n):
+        F = np.zeros(3)
+        state["f"], sums, _ = run(solid, state["f"], int(n), q=q, force=F, **kw)
+        state["total"] += int(n)
+        state["U"] = sums[1] / ncell
+        state["F"] = F
+
+    def rnd(x):  # nearest integer, halves away from zero (x > 0 here)
+        return int(np.floor(x + 0.5))
+
+    def flow_through():
+        if not (abs(state["U"]) > 0):
+            raise ValueError("no flow: U_sup is 0")
+        return max(1.0, nx / abs(state["U"]))
+
+    sample(max(1, nx))
+    T = flow_through()
+    spin_ft = state["total"] / T
+    spin_steps = state["total"]
+    prev, change, developed = None, 1.0, False
+    while True:
+        sub = max(1, rnd(T / samples_per_ft))
+        if state["total"] + sub * samples_per_ft > max_steps:
+            return dict(status="capped", spinup_steps=spin_steps, spinup_ft=spin_ft, drag_change=change,
+                        f=state["f"])
+        wsum = 0.0
+        for _ in range(samples_per_ft):
+            sample(sub)
+            wsum += state["F"][0]
+        spin_steps += sub * samples_per_ft
+        spin_ft += sub * samples_per_ft / T
+        W = wsum / samples_per_ft
+        change = 1.0 if prev is None else abs(W - prev) / max(abs(W), 1e-300)
+        prev = W
+        T = flow_through()
+        if spin_ft >= min_spinup_ft and change < drag_tol:
+            developed = True
+            break
+        if spin_ft >= max_spinup_ft:
+            break
+    sub = max(1, rnd(T / samples_per_ft))
+    n_samples = max(1, rnd(average_ft * samples_per_ft))
+    U_sum, F_sum, done = 0.0, np.zeros(3), 0
+    status = "ok"
+    for _ in range(n_samples):
+        if state["total"] + sub > max_steps:
+            status = "capped"
+            break
+        sample(sub)
+        U_sum += state["U"]
+        F_sum += state["F"]
+        done += 1
+    return dict(status=status, developed=developed, spinup_steps=spin_steps, spinup_ft=spin_ft,
+                drag_change=change, average_steps=done * sub, U_sup=U_sum / max(done, 1),
+                F=F_sum / max(done, 1), f=state["f"])

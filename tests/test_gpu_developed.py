@@ -98,3 +98,48 @@ def test_bad_options_and_flow_at_rest(capi):
         c.init_equilibrium()
         with pytest.raises(capi.LBMError):
             c.run_developed()
+
+
+def test_time_average_against_oracle(capi, orc):
+    """lbm_average against the oracle's windowed average of U_sup and the drag (the same
+    sampling schedule), FP64, from a seeded perturbed state."""
+    g = I.Geometry(24, 20, 18, np.array([[11.3, 9.6, 8.7, 6.2]]))
+    solid = orc.voxelize(g.shape, g.spheres)
+    q = orc.wall_distances(solid, g.spheres)
+    _, w, _ = orc.lattice()
+    f0 = w[:, None, None, None] * (1.0 + 1e-3 * I.noise((19,) + solid.shape, 13))
+    f0[:, solid == 1] = 0.0
+    kw = dict(tau=0.7, delta_rho=2e-4, magic_lambda=3 / 16, collision=capi.TRT, wall=capi.CLI)
+    with capi.Context(spheres=g.spheres, shape=g.shape, storage=capi.F64, **kw) as ctx:
+        ctx.set_populations(f0)
+        ctx.step(30)
+        avg = ctx.average(6, 25)
+    f, _, _ = orc.run(solid, f0, 30, q=q, **kw)
+    _, U, F = orc.time_average(solid, f, 6, 25, q=q, **kw)
+    assert avg["status"] == capi.OK and avg["steps"] == 30 + 150
+    assert avg["U_sup"] == pytest.approx(U, rel=1e-9, abs=0)
+    Fg = np.array([avg["F_x"], avg["F_y"], avg["F_z"]])
+    assert np.abs(Fg - F).max() <= 1e-9 * np.abs(F).max() + 1e-15
+
+
+def test_developed_average_against_oracle(capi, orc):
+    """lbm_run_developed against the oracle's developed-flow average (the spin-up windows of
+    one flow-through time, the drag test, the averaging schedule), FP64: the same spin-up and
+    averaging step counts, U_sup and drag to 1e-9."""
+    g = I.centred_sphere(16, 5.0)
+    solid = orc.voxelize(g.shape, g.spheres)
+    q = orc.wall_distances(solid, g.spheres)
+    kw = dict(tau=0.7, delta_rho=4e-3, magic_lambda=3 / 16, collision=capi.TRT, wall=capi.CLI)
+    opts = dict(min_spinup_ft=2.0, max_spinup_ft=12.0, drag_tol=1e-4, average_ft=3.0, samples_per_ft=4,
+                max_steps=200000)
+    with capi.Context(spheres=g.spheres, shape=g.shape, storage=capi.F64, **kw) as ctx:
+        ctx.init_equilibrium()
+        r = ctx.run_developed(**opts)
+    o = orc.developed_average(solid, orc.init_rest(solid), q=q, **opts, **kw)
+    assert r["status"] == capi.OK and o["status"] == "ok"
+    assert r["developed"] == int(o["developed"])
+    assert r["spinup_steps"] == o["spinup_steps"] and r["average_steps"] == o["average_steps"]
+    assert r["spinup_ft"] == pytest.approx(o["spinup_ft"], rel=1e-9)
+    assert r["avg"]["U_sup"] == pytest.approx(o["U_sup"], rel=1e-9, abs=0)
+    Fg = np.array([r["avg"]["F_x"], r["avg"]["F_y"], r["avg"]["F_z"]])
+    assert np.abs(Fg - o["F"]).max() <= 1e-9 * np.abs(o["F"]).max() + 1e-15

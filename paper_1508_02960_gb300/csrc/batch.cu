@@ -175,11 +175,7 @@ lbm_status Batch::make_instance(const lbm_desc &d0, cudaStream_t s, std::unique_
     // 16 bytes of slack: 16-bit formats copy the aligned 32-bit word holding a population
     in->ks = direction_stride(n);
     const size_t pop = (size_t)Q * in->ks * es + 16;
-    auto cleanup = [&](cudaError_t ce, const char *what) {
-        cudaFree(in->f0);
-        cudaFree(in->f1);
-        cudaFree(in->partials);
-        free_geometry(&in->geo);
+    auto cleanup = [&](cudaError_t ce, const char *what) {  // in's destructor frees the memory
         return cuda_fail(ce, what);
     };
     // Canaries: the padding after each direction's ncells values (and the slack) holds
@@ -210,16 +206,19 @@ lbm_status Batch::make_instance(const lbm_desc &d0, cudaStream_t s, std::unique_
 // ------------------------------------------------------------------------------------
 // Batch
 // ------------------------------------------------------------------------------------
+Instance::~Instance()
+{
+    cudaFree(f0);
+    cudaFree(f1);
+    cudaFree(partials);
+    free_geometry(&geo);
+}
+
 Batch::~Batch()
 {
     if (stream_ || cap_) cudaStreamSynchronize(stream_);
     for (auto &kv : graphs_) cudaGraphExecDestroy(kv.second);
-    for (auto &p : inst_) {
-        cudaFree(p->f0);
-        cudaFree(p->f1);
-        cudaFree(p->partials);
-        free_geometry(&p->geo);
-    }
+    inst_.clear();
     cudaFree(d_table_);
     cudaFree(d_tiles_);
     cudaFree(d_tile_count_);
@@ -264,7 +263,10 @@ lbm_status Batch::add(std::unique_ptr<Instance> in)
     const lbm_desc &d = in->desc;
     if (d.storage != storage_ || d.collision != collision_ || d.layout != layout_)
         return fail(LBM_ERR_ARG, "instances of a batch must share storage, collision and layout");
-    if (layout_ == LBM_LAYOUT_AA && !inst_.empty()) return fail(LBM_ERR_ARG, "AA layout supports one instance");
+    // the instances of an AA batch share one in-place arrangement: a new one joins when the
+    // batch is back in the arrangement of step 0 (after an even number of steps)
+    if (layout_ == LBM_LAYOUT_AA && !inst_.empty() && aa_phase_ != 0)
+        return fail(LBM_ERR_STATE, "an AA batch takes new instances after an even number of steps only");
     in->phase = 0;
     inst_.push_back(std::move(in));
     dirty_ = true;
@@ -275,12 +277,7 @@ lbm_status Batch::remove(int i)
 {
     if (i < 0 || i >= size()) return fail(LBM_ERR_ARG, "instance index out of range");
     CK(cudaStreamSynchronize(stream_));
-    Instance &p = *inst_[i];
-    cudaFree(p.f0);
-    cudaFree(p.f1);
-    cudaFree(p.partials);
-    free_geometry(&p.geo);
-    inst_.erase(inst_.begin() + i);
+    inst_.erase(inst_.begin() + i);  // the instance frees its device memory
     dirty_ = true;
     return LBM_OK;
 }
@@ -566,8 +563,23 @@ lbm_status Batch::rebuild()
     return LBM_OK;
 }
 
+// A state set from outside is written in the AA arrangement of step 0.  In a batch of
+// several AA instances that is possible only while the others are in it too.
+lbm_status Batch::aa_restart(int i)
+{
+    if (layout_ != LBM_LAYOUT_AA || aa_phase_ == 0) return LBM_OK;
+    if (i >= 0 && size() > 1)
+        return fail(LBM_ERR_STATE, "an AA batch sets one instance's state after an even number of steps only");
+    aa_phase_ = 0;
+    return LBM_OK;
+}
+
 lbm_status Batch::init_equilibrium(int i)
 {
+    {
+        lbm_status st = aa_restart(i);
+        if (st != LBM_OK) return st;
+    }
     if (dirty_) {
         lbm_status st = rebuild();
         if (st != LBM_OK) return st;
@@ -587,7 +599,6 @@ lbm_status Batch::init_equilibrium(int i)
         in.sums_pending = false;
         in.steps = 0;
     }
-    if (layout_ == LBM_LAYOUT_AA) aa_phase_ = 0;
     return LBM_OK;
 }
 
@@ -787,7 +798,10 @@ lbm_status Batch::set_f64(int i, const double *host)
         lbm_status st = rebuild();
         if (st != LBM_OK) return st;
     }
-    if (layout_ == LBM_LAYOUT_AA) aa_phase_ = 0;
+    {
+        lbm_status st = aa_restart(i);
+        if (st != LBM_OK) return st;
+    }
     Instance &in = *inst_[i];
     const long long n = in.geo.ncells;
     CK(ensure_stage(&d_stage_, &stage_cells_, n));
@@ -818,7 +832,10 @@ lbm_status Batch::state_io(int i, void *host, size_t bytes, bool to_host)
     const long long nf = in.geo.n_fluid;
     const size_t dir_bytes = (size_t)nf * storage_bytes(storage_);
     if (bytes != (size_t)Q * dir_bytes) return fail(LBM_ERR_ARG, "state buffer must hold 19 * n_fluid elements");
-    if (!to_host && layout_ == LBM_LAYOUT_AA) aa_phase_ = 0;
+    if (!to_host) {
+        lbm_status st = aa_restart(i);
+        if (st != LBM_OK) return st;
+    }
     if (nf > 0) {
         lbm_status cs = ensure_copy_stream();
         if (cs != LBM_OK) return cs;
@@ -925,7 +942,10 @@ lbm_status Batch::apply_staged_state(int i)
     }
     Instance &in = *inst_[i];
     const long long nf = in.geo.n_fluid;
-    if (layout_ == LBM_LAYOUT_AA) aa_phase_ = 0;
+    {
+        lbm_status st = aa_restart(i);
+        if (st != LBM_OK) return st;
+    }
     CK(cudaStreamWaitEvent(stream_, ev_staged_[b], 0));
     const int cur = cur_of(in);
     if (nf > 0) {  // all 19 directions in one launch
@@ -1106,6 +1126,8 @@ lbm_status Batch::load(int i, const char *path)
     std::fclose(f);
     if (!ok) return fail(LBM_ERR_IO, "checkpoint truncated");
     CK(cudaStreamSynchronize(stream_));
+    if (layout_ == LBM_LAYOUT_AA && size() > 1 && h.aa_phase != aa_phase_)
+        return fail(LBM_ERR_STATE, "the checkpoint's AA arrangement differs from the batch's");
     if (layout_ == LBM_LAYOUT_AA) aa_phase_ = h.aa_phase;
     void *dst = (layout_ == LBM_LAYOUT_AB) ? (cur_of(in) ? in.f1 : in.f0) : in.f0;
     CK(cudaMemcpy(dst, buf.data(), pop, cudaMemcpyHostToDevice));

@@ -33,6 +33,11 @@ struct Instance {
     bool sums_pending = false;       // the last queued step reduced the moments
     size_t bytes_pop = 0;
     long long ks = 0;                // elements between direction arrays
+
+    Instance() = default;
+    Instance(const Instance &) = delete;
+    Instance &operator=(const Instance &) = delete;
+    ~Instance();                     // frees the instance's device memory
 };
 
 class Batch {
@@ -44,7 +49,8 @@ public:
     static size_t footprint(const lbm_desc &d);
 
     lbm_status init(cudaStream_t user_stream, int storage, int collision, int layout);
-    lbm_status add(std::unique_ptr<Instance> inst);    // A-B batches only when stepping has begun
+    // AA batches: after an even number of steps only (the instances share one arrangement)
+    lbm_status add(std::unique_ptr<Instance> inst);
     lbm_status remove(int i);                          // releases device memory of instance i
     int size() const { return (int)inst_.size(); }
     Instance &at(int i) { return *inst_[i]; }
@@ -85,6 +91,7 @@ public:
 
 private:
     lbm_status rebuild();          // upload table and tiles, drop graphs
+    lbm_status aa_restart(int i);  // instance i (i < 0: all) set from outside: AA arrangement of step 0
     int cur_of(const Instance &in) const { return in.phase ^ flip_; }
     const FormatOps &ops() const { return format_ops(storage_); }
 

@@ -439,8 +439,6 @@ lbm_status lbm_batch_create(const lbm_desc *descs, int32_t n, void *cuda_stream,
     if (!out) return fail(LBM_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!descs || n < 1) return fail(LBM_ERR_ARG, "need at least one descriptor");
-    for (int i = 0; i < n; ++i)
-        if (descs[i].layout != LBM_LAYOUT_AB) return fail(LBM_ERR_ARG, "batches use the A-B layout");
     lbm_batch *b = new (std::nothrow) lbm_batch();
     if (!b) return fail(LBM_ERR_NO_MEMORY, "host allocation failed");
     lbm_status st = create_batch(b->b, descs, n, (cudaStream_t)cuda_stream);

@@ -39,12 +39,10 @@ cudaError_t step_red(const Launch &L, int flip, unsigned *status, const Instance
     if (one) {  // a single instance: parameters travel in the constant bank
         e = launch_step(step_kernel<COLL, STORE, KIND, false, RED, WX>, L, L.table, *one, L.tiles, L.ntiles, flip,
                         status);
-    } else if constexpr (KIND == KIND_AB) {
+    } else {  // a batch: parameters from the device table
         static const InstanceDev unused{};
         e = launch_step(step_kernel<COLL, STORE, KIND, true, RED, WX>, L, L.table, unused, L.tiles, L.ntiles, flip,
                         status);
-    } else {
-        return cudaErrorInvalidValue;  // the AA layout runs single instances only
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

@@ -3,15 +3,20 @@
 // boundary), per-point convergence test on the volume-averaged velocity, retirement,
 // and submit-to-finish latency.
 //
-// One worker thread owns a private CUDA stream and one Batch per (storage, collision)
-// group.  Every chunk: admit what fits, advance each group by check_interval steps
-// (a captured graph ending in the FP64 reduction), read the per-point sums, retire.
+// Two threads, each with a private CUDA stream.  The admission thread takes queued points
+// that fit the memory budget and builds them (geometry and memory, on its own stream) while
+// the GPU steps the resident ones.  The worker owns one Batch per (storage, collision,
+// layout) group.  Every chunk: take the points the admission thread has built, advance each
+// group by check_interval steps (a captured graph ending in the FP64 reduction), read the
+// per-point sums, retire.  check_interval is even, so that in-place (AA) groups are back in
+// the arrangement of step 0 at every chunk boundary, where new points join them.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
 #include <map>
 #include <mutex>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "batch.h"
@@ -42,24 +47,32 @@ struct Request {
 
 }  // namespace
 
+using GroupKey = std::tuple<int, int, int>;  // storage, collision, layout
+
 struct lbm_server {
     lbm_server_opts opts{};
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
+    std::condition_variable cv_work, cv_done, cv_admit;
     std::deque<int64_t> queue;
     std::map<int64_t, Request> reqs;
     int64_t next_id = 1;
     bool stop = false;
     size_t used = 0;
     int device = 0;
-    cudaStream_t stream = nullptr;
-    std::map<std::pair<int, int>, std::unique_ptr<Batch>> groups;
-    std::map<std::pair<int, int>, std::vector<int64_t>> members;  // request id per batch slot
+    cudaStream_t stream = nullptr;   // stepping (worker)
+    cudaStream_t astream = nullptr;  // instance builds (admission thread)
+    int building = 0;                // points being built by the admission thread
+    // points built and waiting to join their group at the next chunk boundary
+    std::vector<std::pair<int64_t, std::unique_ptr<Instance>>> ready;
+    std::map<GroupKey, std::unique_ptr<Batch>> groups;
+    std::map<GroupKey, std::vector<int64_t>> members;  // request id per batch slot
     lbm_server_stats stats{};
-    std::thread worker;
+    std::thread worker, admitter;
 
     void run();
-    void admit();
+    void admit_loop();
+    void join_ready();
+    int resident_count();
     void finish(Request &r, lbm_status st, const Instance *in);
 };
 
@@ -75,44 +88,85 @@ void lbm_server::finish(Request &r, lbm_status st, const Instance *in)
     else ++stats.failed;
 }
 
-void lbm_server::admit()
+int lbm_server::resident_count()
 {
-    // called with the lock held; builds instances without it
-    while (!queue.empty()) {
-        int resident = 0;
-        for (auto &g : groups) resident += g.second->size();
-        if (resident >= opts.max_resident) return;
+    int resident = (int)ready.size() + building;
+    for (auto &g : groups) resident += g.second->size();
+    return resident;
+}
+
+// Admission thread: builds the queued points that fit the memory budget and the resident
+// cap, on its own stream, while the worker keeps the GPU stepping.
+void lbm_server::admit_loop()
+{
+    cudaSetDevice(device);
+    std::unique_lock<std::mutex> lk(mu);
+    while (true) {
+        cv_admit.wait(lk, [this] {
+            if (stop) return true;
+            if (queue.empty() || resident_count() >= opts.max_resident) return false;
+            return used + reqs[queue.front()].bytes <= opts.hbm_budget_bytes;
+        });
+        if (stop) break;
         Request &r = reqs[queue.front()];
-        if (used + r.bytes > opts.hbm_budget_bytes) return;
         queue.pop_front();
         used += r.bytes;
         r.state = Request::RUNNING;
+        ++building;
         lbm_desc d = r.desc;
         d.spheres = r.spheres.empty() ? nullptr : r.spheres.data();
         d.flags = r.flags.empty() ? nullptr : r.flags.data();
         d.q = r.q.empty() ? nullptr : r.q.data();
         d.mrt_rates = r.mrt.empty() ? nullptr : r.mrt.data();
-        d.layout = LBM_LAYOUT_AB;
-        mu.unlock();
+        const int64_t id = r.id;
+        lk.unlock();
         std::unique_ptr<Instance> in;
-        lbm_status st = Batch::make_instance(d, stream, &in);
-        std::pair<int, int> key(d.storage, d.collision);
-        mu.lock();
+        lbm_status st = Batch::make_instance(d, astream, &in);
+        lk.lock();
+        --building;
+        Request &rr = reqs[id];
         if (st != LBM_OK) {
-            finish(r, st, nullptr);
+            finish(rr, st, nullptr);
             cv_done.notify_all();
+            cv_admit.notify_all();
             continue;
+        }
+        ready.emplace_back(id, std::move(in));
+        cv_work.notify_all();
+    }
+}
+
+// Worker, at a chunk boundary (lock held): the built points join their groups.  Every
+// group is in the arrangement of step 0 here (check_interval is even).
+void lbm_server::join_ready()
+{
+    for (auto &p : ready) {
+        Request &r = reqs[p.first];
+        const lbm_desc &d = p.second->desc;
+        const GroupKey key(d.storage, d.collision, d.layout);
+        if (r.cancel) {  // cancelled while it was being built
+            finish(r, LBM_ERR_CANCELLED, nullptr);
+            continue;    // the instance frees its memory with ready below
         }
         auto &g = groups[key];
         if (!g) {
             g.reset(new Batch());
-            g->init(stream, d.storage, d.collision, LBM_LAYOUT_AB);
-            if (d.block_cells) g->set_block(d.block_cells);
+            g->init(stream, d.storage, d.collision, d.layout);
+            if (d.block_cells > 0) g->set_block(d.block_cells);
         }
-        g->add(std::move(in));
+        lbm_status st = g->add(std::move(p.second));  // on failure the instance is freed
+        if (st == LBM_OK) {
+            st = g->init_equilibrium(g->size() - 1);
+            if (st != LBM_OK) g->remove(g->size() - 1);
+        }
+        if (st != LBM_OK) {
+            finish(r, st, nullptr);
+            continue;
+        }
         members[key].push_back(r.id);
-        g->init_equilibrium(g->size() - 1);
     }
+    ready.clear();
+    cv_done.notify_all();
 }
 
 void lbm_server::run()
@@ -120,11 +174,11 @@ void lbm_server::run()
     cudaSetDevice(device);
     std::unique_lock<std::mutex> lk(mu);
     while (true) {
-        admit();
+        join_ready();
         int resident = 0;
         for (auto &g : groups) resident += g.second->size();
         if (resident == 0) {
-            if (stop) break;
+            if (stop && building == 0) break;
             cv_work.wait_for(lk, std::chrono::milliseconds(50));
             continue;
         }
@@ -170,6 +224,7 @@ void lbm_server::run()
         stats.kernel_launches = 0;
         for (auto &kv : groups) stats.kernel_launches += kv.second->launches();
         cv_done.notify_all();
+        cv_admit.notify_all();  // memory may have been freed
     }
 }
 
@@ -184,14 +239,18 @@ lbm_status lbm_server_create(const lbm_server_opts *opts, lbm_server **out)
     if (!s) return fail(LBM_ERR_NO_MEMORY, "host allocation failed");
     s->opts = *opts;
     if (s->opts.check_interval <= 0) s->opts.check_interval = 200;
+    s->opts.check_interval += s->opts.check_interval & 1;  // even: AA groups back in step 0's arrangement
     if (s->opts.max_resident <= 0) s->opts.max_resident = 256;
     cudaGetDevice(&s->device);
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->astream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
+        if (s->stream) cudaStreamDestroy(s->stream);
         delete s;
         return cuda_fail(e, "cudaStreamCreate");
     }
     s->worker = std::thread([s] { s->run(); });
+    s->admitter = std::thread([s] { s->admit_loop(); });
     *out = s;
     return LBM_OK;
 }
@@ -200,7 +259,8 @@ lbm_status lbm_server_submit(lbm_server *s, const lbm_desc *desc, double tol, in
 {
     if (!s || !desc || !req_id) return fail(LBM_ERR_ARG, "NULL argument");
     if (!(tol > 0) || max_steps < 1) return fail(LBM_ERR_ARG, "tol must be > 0 and max_steps >= 1");
-    if (desc->nx < 1 || desc->ny < 1 || desc->nz < 1) return fail(LBM_ERR_ARG, "nx, ny, nz must be >= 1");
+    lbm_status v = validate_desc(*desc);
+    if (v != LBM_OK) return v;
     Request r;
     r.desc = *desc;
     const size_t n = (size_t)desc->nx * desc->ny * desc->nz;
@@ -212,7 +272,6 @@ lbm_status lbm_server_submit(lbm_server *s, const lbm_desc *desc, double tol, in
     r.desc.flags = nullptr;
     r.desc.q = nullptr;
     r.desc.mrt_rates = nullptr;
-    r.desc.layout = LBM_LAYOUT_AB;
     r.tol = tol;
     r.max_steps = max_steps;
     r.bytes = Batch::footprint(r.desc);
@@ -224,7 +283,7 @@ lbm_status lbm_server_submit(lbm_server *s, const lbm_desc *desc, double tol, in
     s->queue.push_back(r.id);
     s->reqs[r.id] = std::move(r);
     ++s->stats.submitted;
-    s->cv_work.notify_all();
+    s->cv_admit.notify_all();
     return LBM_OK;
 }
 
@@ -282,7 +341,7 @@ lbm_status lbm_server_cancel(lbm_server *s, int64_t req_id)
         s->cv_done.notify_all();
         return LBM_OK;
     }
-    r.cancel = true;  // resident: the worker retires it after the current chunk
+    r.cancel = true;  // being built or resident: retired at the next chunk boundary
     return LBM_OK;
 }
 
@@ -309,18 +368,18 @@ void lbm_server_destroy(lbm_server *s)
         s->queue.clear();
         for (auto &kv : s->reqs)
             if (kv.second.state == Request::QUEUED) kv.second.state = Request::DONE;
+        // resident points are retired by the worker only on convergence: end them at the
+        // next chunk boundary
+        for (auto &kv : s->reqs) kv.second.max_steps = 0;
         s->cv_work.notify_all();
+        s->cv_admit.notify_all();
     }
-    // resident points are retired by the worker only on convergence; drop them here
-    if (s->worker.joinable()) {
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            for (auto &kv : s->reqs) kv.second.max_steps = 0;
-        }
-        s->worker.join();
-    }
+    if (s->admitter.joinable()) s->admitter.join();
+    if (s->worker.joinable()) s->worker.join();
+    s->ready.clear();
     s->groups.clear();
     if (s->stream) cudaStreamDestroy(s->stream);
+    if (s->astream) cudaStreamDestroy(s->astream);
     delete s;
 }
 

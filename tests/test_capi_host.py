@@ -97,8 +97,9 @@ def test_batch_rejects_mixed_formats(L):
     arr = (capi.Desc * 2)(d1, d2)
     h = ctypes.c_void_p()
     assert L.lbm_batch_create(arr, 2, None, ctypes.byref(h)) == capi.ERR_ARG
-    d3, k3 = capi.make_desc(nx=8, ny=8, nz=8, layout=capi.LAYOUT_AA)
-    assert L.lbm_batch_create(ctypes.byref(d3), 1, None, ctypes.byref(h)) == capi.ERR_ARG
+    d3, k3 = capi.make_desc(nx=8, ny=8, nz=8, storage=capi.F32, layout=capi.LAYOUT_AA)
+    arr = (capi.Desc * 2)(d1, d3)                  # one layout per batch
+    assert L.lbm_batch_create(arr, 2, None, ctypes.byref(h)) == capi.ERR_ARG
 
 
 def test_null_arguments(L):

@@ -297,10 +297,12 @@ def test_divergence_is_reported(capi):
         assert done < 5000
 
 
-def test_batch_alone_vs_mix_bitwise(capi):
+@pytest.mark.parametrize("layout", ["AB", "AA"])
+def test_batch_alone_vs_mix_bitwise(capi, layout):
     geoms = [I.centred_sphere(24, 8.0), RAGGED, I.centred_sphere(40, 15.0), STAGED, I.centred_sphere(64, 20.0)]
     descs_keep = [capi.make_desc(spheres=gg.spheres, shape=gg.shape, tau=0.6 + 0.05 * i, delta_rho=1e-4 * (i + 1),
-                                 collision=capi.TRT, wall=capi.CLI, storage=capi.F16DEV)
+                                 collision=capi.TRT, wall=capi.CLI, storage=capi.F16DEV,
+                                 layout=getattr(capi, "LAYOUT_" + layout))
                   for i, gg in enumerate(geoms)]
     descs = [d for d, _ in descs_keep]
     b = capi.Batch(descs)
@@ -314,3 +316,30 @@ def test_batch_alone_vs_mix_bitwise(capi):
             ctx.step(60)
             assert np.array_equal(ctx.get_populations(), mix[i][0])
             assert ctx.observables()["U_sup"] == mix[i][1]["U_sup"]
+
+
+def test_aa_batch_sets_one_instance_only_in_step0_arrangement(capi, orc):
+    """The instances of an in-place batch share one arrangement: one instance's state can be
+    set after an even number of steps (and steps on alike), not after an odd one."""
+    geoms = [I.centred_sphere(24, 8.0), RAGGED]
+    keep = [capi.make_desc(spheres=gg.spheres, shape=gg.shape, tau=0.7, delta_rho=1e-4, collision=capi.TRT,
+                           wall=capi.CLI, storage=capi.F32, layout=capi.LAYOUT_AA) for gg in geoms]
+    b = capi.Batch([d for d, _ in keep])
+    try:
+        b.init_equilibrium()
+        b.step(3)
+        f1 = b.get_populations(1)
+        with pytest.raises(capi.LBMError) as e:
+            b.set_populations(1, f1)
+        assert e.value.status == capi.ERR_STATE
+        b.step(1)
+        f1 = b.get_populations(1)
+        b.set_populations(1, f1)                  # even: allowed, and a no-op on the state
+        assert np.array_equal(b.get_populations(1), f1)
+        b.step(6)
+        with capi.Context(desc=keep[1][0]) as ctx:
+            ctx.init_equilibrium()
+            ctx.step(10)
+            assert np.array_equal(ctx.get_populations(), b.get_populations(1))
+    finally:
+        b.close()

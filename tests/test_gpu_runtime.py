@@ -51,17 +51,21 @@ def test_run_to_convergence_matches_oracle_steady_state(capi, orc, wall):
     assert obs["Re_p"] == pytest.approx(U * 12.0 / ((0.8 - 0.5) / 3), rel=1e-12)
 
 
-def _point(capi, L, r, tau, dr):
+def _point(capi, L, r, tau, dr, layout="AB"):
     g = I.centred_sphere(L, r)
     return capi.make_desc(spheres=g.spheres, shape=g.shape, tau=tau, delta_rho=dr, collision=capi.TRT,
-                          wall=capi.CLI, storage=capi.F32)
+                          wall=capi.CLI, storage=capi.F32, layout=getattr(capi, "LAYOUT_" + layout))
 
 
-def test_server_results_equal_alone_and_continuous_batching(capi):
+@pytest.mark.parametrize("layout", ["AB", "AA"])
+def test_server_results_equal_alone_and_continuous_batching(capi, layout):
+    """Points are built by the admission thread while others step; in-place (AA) points join
+    their group at chunk boundaries (even step counts).  Each result equals the same point
+    run alone through a context, bit for bit."""
     import time
     pts = [(24, 8.0, 0.7, 1e-4), (32, 11.0, 0.6, 5e-5), (40, 13.0, 0.8, 2e-4), (24, 9.5, 0.9, 1e-4),
            (32, 10.0, 0.75, 1e-4), (40, 16.0, 0.65, 3e-5)]
-    keep = [_point(capi, *p) for p in pts]
+    keep = [_point(capi, *p, layout=layout) for p in pts]
     # budget for about three points at a time: the rest queue and are admitted as others retire
     foot = 2 * 19 * 4 * 40 ** 3 + 2 * 2 ** 20
     srv = capi.Server(hbm_budget_bytes=3 * foot, check_interval=100, max_resident=8)

@@ -653,7 +653,8 @@ def run_gpu(args, rank, world, local):
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
-    launches = ctx.info()["kernel_launches"] - launches0
+    info_t = ctx.info()
+    launches = info_t["kernel_launches"] - launches0
     total_ms = t_start.elapsed_time(t_end)
     graph_ms = [a.elapsed_time(b) for a, b in ev]
     updates = float(nf) * TIME_STEPS * args.steps
@@ -711,6 +712,8 @@ def run_gpu(args, rank, world, local):
             "config": {"workload": args.workload, "cells": L ** 3, "fluid_cells": nf, "sphere_radius": r,
                        "storage": storage, "layout": layout, "collision": coll, "wall": wall, "tau": tau,
                        "delta_rho": dr, "time_steps_per_step": TIME_STEPS, "block_cells": info["block_cells"],
+                       "step_shape": {"warps": info_t["step_warps"], "source": info_t["shape_source"],
+                                      "ms_candidates": [round(x, 5) for x in info_t["shape_ms"]]},
                        "l2": "L2 flushed before every benchmark step (256 MB write); populations %.0f MB, "
                              "%.0f MB of them touched per time step" % (info["bytes_populations"] / 1e6,
                                                                           38.0 * es * nf / 2e6),

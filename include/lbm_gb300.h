@@ -157,6 +157,13 @@ typedef struct {
     int32_t pad_;
     double tune_ms_tiles;      /* autotuner: ms per step of the tile kernel (0 = not timed) */
     double tune_ms_bricks;     /* autotuner: ms per step of the brick kernel (0 = not timed) */
+    /* block shape of the non-reducing SBB/CLI step of the tile kernel, tuned online by the
+     * first lbm_step / lbm_batch_step call of more than 48 steps (all shapes give the same
+     * state bit for bit): warps per block (4, 2 or 8; 0 = brick kernel), how it was chosen
+     * (0 default, 1 timed, 2 cached for the same storage, collision, layout, instance count,
+     * fluid cells and device), and ms per step of the candidates 4, 2, 8 (0 = not timed) */
+    int32_t step_warps, shape_source;
+    double shape_ms[3];
 } lbm_info;
 
 typedef struct lbm_ctx lbm_ctx;

@@ -100,10 +100,14 @@ class Info(ctypes.Structure):
                [(n, ctypes.c_int32) for n in
                 ("block_cells", "storage", "layout", "collision", "wall", "dev_scale_log2")] + \
                [("steps", ctypes.c_int64), ("autotune", ctypes.c_int32), ("pad_", ctypes.c_int32),
-                ("tune_ms_tiles", ctypes.c_double), ("tune_ms_bricks", ctypes.c_double)]
+                ("tune_ms_tiles", ctypes.c_double), ("tune_ms_bricks", ctypes.c_double),
+                ("step_warps", ctypes.c_int32), ("shape_source", ctypes.c_int32),
+                ("shape_ms", ctypes.c_double * 3)]
 
     def as_dict(self):
-        return {n: getattr(self, n) for n, _ in self._fields_ if n != "pad_"}
+        d = {n: getattr(self, n) for n, _ in self._fields_ if n != "pad_"}
+        d["shape_ms"] = list(d["shape_ms"])
+        return d
 
 
 class ServerOpts(ctypes.Structure):

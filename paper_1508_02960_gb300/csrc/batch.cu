@@ -217,8 +217,9 @@ Instance::~Instance()
 Batch::~Batch()
 {
     if (stream_ || cap_) cudaStreamSynchronize(stream_);
-    for (auto &kv : graphs_) cudaGraphExecDestroy(kv.second);
+    for (auto &kv : graphs_) cudaGraphExecDestroy(kv.second.exec);
     inst_.clear();
+    for (int w = 0; w < kShapeWarpsN; ++w) cudaFree(d_wtiles_[w]);
     cudaFree(d_table_);
     cudaFree(d_tiles_);
     cudaFree(d_tile_count_);
@@ -475,8 +476,6 @@ lbm_status Batch::setup_tma()
 lbm_status Batch::rebuild()
 {
     CK(cudaStreamSynchronize(stream_));
-    for (auto &kv : graphs_) cudaGraphExecDestroy(kv.second);
-    graphs_.clear();
     const int n = size();
     const int CS = block_ / 32;  // segments per work chunk
     int dev = 0, sms = 0;
@@ -487,7 +486,7 @@ lbm_status Batch::rebuild()
         CK(cudaMemset(d_error_, 0, sizeof(unsigned)));
     }
     std::vector<InstanceDev> table(std::max(n, 1));
-    std::vector<TileDev> tiles, stiles;
+    std::vector<TileDev> tiles, stiles, wtiles[kShapeWarpsN];
     std::vector<int> tc(std::max(n, 1)), sc(std::max(n, 1));  // tiles of each instance
     for (int i = 0; i < n; ++i) {
         Instance &in = *inst_[i];
@@ -503,6 +502,13 @@ lbm_status Batch::rebuild()
         for (long long t = 0; t < nt; ++t) tiles.push_back(TileDev{i, (int)t, t * CS});
         sc[i] = (int)ns;
         for (long long t = 0; t < ns; ++t) stiles.push_back(TileDev{i, (int)t, t * kTileSegs});
+        // tiles of the other block shapes of the non-reducing step (no partial sums)
+        for (int w = 0; w < kShapeWarpsN; ++w) {
+            const int W = kShapeWarps[w];
+            const long long nw = (in.geo.n_fwarps + W - 1) / W;
+            if (nw * W > in.geo.n_fwarps_padded) return fail(LBM_ERR_STATE, "fluid work list too short");
+            for (long long t = 0; t < nw; ++t) wtiles[w].push_back(TileDev{i, (int)t, t * W});
+        }
     }
     if (tiles.size() > (size_t)INT32_MAX || stiles.size() > (size_t)INT32_MAX)
         return fail(LBM_ERR_ARG, "too many tiles");
@@ -528,6 +534,16 @@ lbm_status Batch::rebuild()
     if (nstiles_ > 0) {
         CK(dev_alloc(&d_stiles_, sizeof(TileDev) * stiles.size()));
         CK(cudaMemcpy(d_stiles_, stiles.data(), sizeof(TileDev) * stiles.size(), cudaMemcpyHostToDevice));
+    }
+    for (int w = 0; w < kShapeWarpsN; ++w) {
+        cudaFree(d_wtiles_[w]);
+        d_wtiles_[w] = nullptr;
+        nwtiles_[w] = (int)wtiles[w].size();
+        if (nwtiles_[w] > 0) {
+            CK(dev_alloc(&d_wtiles_[w], sizeof(TileDev) * wtiles[w].size()));
+            CK(cudaMemcpy(d_wtiles_[w], wtiles[w].data(), sizeof(TileDev) * wtiles[w].size(),
+                          cudaMemcpyHostToDevice));
+        }
     }
     CK(dev_alloc(&d_stile_count_, sizeof(int) * sc.size()));
     CK(cudaMemcpy(d_stile_count_, sc.data(), sizeof(int) * sc.size(), cudaMemcpyHostToDevice));
@@ -556,9 +572,15 @@ lbm_status Batch::rebuild()
     }
     // one step block per tile; the hardware block scheduler balances the tiles
     grid_ = std::max(1, nstiles_);
+    sms_ = sms;
+    for (auto &kv : graphs_) cudaGraphExecDestroy(kv.second.exec);
+    graphs_.clear();
+    shape_ = StepShape{};
+    shape_src_ = 0;
     aux_grid_ = std::max(1, std::min(sms * 8, (ntiles_ + 7) / 8));
     lbm_status st = setup_tma();
     if (st != LBM_OK) return st;
+    lookup_shape();
     dirty_ = false;
     return LBM_OK;
 }
@@ -604,7 +626,9 @@ lbm_status Batch::init_equilibrium(int i)
 
 struct StepQueue {
     const FormatOps *ops;
-    Launch L;
+    Launch L;                // the reducing step (kStepWarps-warp tiles, one block each)
+    Launch Ln[2];            // the non-reducing steps (the tuned shape), by AA kind (A-B: [0])
+    int warps;               // warps per block of Ln
     const InstanceDev *one;  // single instance: its parameters by value; else NULL
     int wx;                  // some instance uses an interpolated wall rule
     const TmaLaunch *tma;    // non-reducing steps on the TMA brick kernel; else NULL
@@ -636,8 +660,12 @@ static cudaError_t queue_steps(const StepQueue &q, cudaStream_t s, long long n, 
             TmaLaunch T = *q.tma;
             T.stream = s;
             e = q.ops->step_tma(q.collision, q.wx, T, *q.one, flip);
+        } else if (red || q.wx) {  // the reducing and interpolated-wall steps: kStepWarps tiles
+            e = q.ops->step(q.collision, kind, L, flip, red ? 1 : 0, q.status, q.one, q.wx, kStepWarps);
         } else {
-            e = q.ops->step(q.collision, kind, L, flip, red ? 1 : 0, q.status, q.one, q.wx);
+            Launch Ls = q.Ln[kind == KIND_AA_LOCAL ? 1 : 0];
+            Ls.stream = s;
+            e = q.ops->step(q.collision, kind, Ls, flip, 0, q.status, q.one, 0, q.warps);
         }
         if (e != cudaSuccess) return e;
         ++launches;
@@ -652,6 +680,149 @@ static cudaError_t queue_steps(const StepQueue &q, cudaStream_t s, long long n, 
     return cudaSuccess;
 }
 
+// Launch of the non-reducing step of AA kind (or A-B) `kind` in block shape sh.
+Launch Batch::shaped_launch(const StepShape &sh, int kind) const
+{
+    int w = 0;
+    while (w < kShapeWarpsN && kShapeWarps[w] != sh.warps) ++w;
+    (void)kind;
+    const int nt = nwtiles_[w];
+    return Launch{d_table_, d_wtiles_[w], nt, sh.warps, std::max(1, nt), sh.warps * 32, stream_};
+}
+
+// The graph of m steps (+ the reduction when red) from (flip_, aa_phase_) in shape sh,
+// instantiated on first use and kept in a small least-recently-used cache.
+lbm_status Batch::graph_for(long long m, bool red, const StepShape &sh, int wx, cudaGraphExec_t *out)
+{
+    const GraphKey key{m * 2 + (red ? 1 : 0), flip_, aa_phase_, sh.warps};
+    auto it = graphs_.find(key);
+    if (it != graphs_.end()) {
+        it->second.used = ++graph_clock_;
+        *out = it->second.exec;
+        return LBM_OK;
+    }
+    if (graphs_.size() >= kGraphCache) {  // evict the least recently used graph
+        auto lru = graphs_.begin();
+        for (auto g = graphs_.begin(); g != graphs_.end(); ++g)
+            if (g->second.used < lru->second.used) lru = g;
+        cudaGraphExecDestroy(lru->second.exec);
+        graphs_.erase(lru);
+    }
+    StepQueue q{&ops(),
+                Launch{d_table_, d_stiles_, nstiles_, kTileSegs, grid_, kStepWarps * 32, stream_},
+                {shaped_launch(sh, layout_ == LBM_LAYOUT_AB ? KIND_AB : KIND_AA_PULL),
+                 shaped_launch(sh, KIND_AA_LOCAL)},
+                sh.warps,
+                size() == 1 ? &h_table_[0] : nullptr,
+                wx,
+                tma_ ? &tma_launch_ : nullptr,
+                collision_,
+                layout_,
+                d_status_,
+                size(),
+                d_stile_count_,
+                d_sums_,
+                size(),
+                d_fscratch_,
+                d_fcount_};
+    int f = flip_, a = aa_phase_;
+    long long dummy = 0;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = queue_steps(q, cap_, m, red, f, a, dummy);
+    cudaError_t e2 = cudaStreamEndCapture(cap_, &graph);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(e, "capture of step kernels");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    graphs_[key] = CachedGraph{exec, ++graph_clock_};
+    *out = exec;
+    return LBM_OK;
+}
+
+// Block shapes of the non-reducing step, tuned online: every shape gives the same state bit
+// for bit (the cells' arithmetic does not depend on how the tiles are grouped), so the first
+// steps of a batch time each candidate on the live state.  The choice is cached per
+// (storage, collision, layout, instance count, total fluid cells, multiprocessor count) for
+// the process.
+namespace {
+struct ShapeKey {
+    int storage, collision, layout, n_inst, sms;
+    long long n_fluid;
+    bool operator<(const ShapeKey &o) const
+    {
+        return std::tie(storage, collision, layout, n_inst, sms, n_fluid) <
+               std::tie(o.storage, o.collision, o.layout, o.n_inst, o.sms, o.n_fluid);
+    }
+};
+std::mutex g_shape_mu;
+std::map<ShapeKey, StepShape> g_shapes;
+const StepShape kShapeCandidates[] = {{kShapeWarps[0]}, {kShapeWarps[1]}, {kShapeWarps[2]}};
+constexpr int kTuneSteps = 16;  // steps timed per candidate (even: flip and AA phase return)
+}  // namespace
+
+void Batch::lookup_shape()
+{
+    tune_shape_ = false;
+    if (tma_ || size() == 0) return;
+    for (auto &p : inst_)
+        if (p->desc.wall >= LBM_LIBB) return;  // the interpolated-wall step has one shape
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    auto it = g_shapes.find(ShapeKey{storage_, collision_, layout_, size(), sms_, fluid_cells()});
+    if (it != g_shapes.end()) {
+        shape_ = it->second;
+        shape_src_ = 2;
+    } else {
+        tune_shape_ = true;
+    }
+}
+
+lbm_status Batch::tune_shape(int wx)
+{
+    const int nc = (int)(sizeof(kShapeCandidates) / sizeof(kShapeCandidates[0]));
+    cudaEvent_t ev[2];
+    CK(cudaEventCreate(&ev[0]));
+    CK(cudaEventCreate(&ev[1]));
+    double best = 0.0;
+    StepShape pick = shape_;
+    lbm_status st = LBM_OK;
+    for (int c = 0; c < nc && st == LBM_OK; ++c) {
+        const StepShape &sh = kShapeCandidates[c];
+        cudaGraphExec_t exec = nullptr;
+        if ((st = graph_for(kTuneSteps, false, sh, wx, &exec)) != LBM_OK) break;
+        cudaError_t e = cudaEventRecord(ev[0], stream_);
+        if (e == cudaSuccess) e = cudaGraphLaunch(exec, stream_);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], stream_);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "timing of a step shape");
+            break;
+        }
+        launches_ += kTuneSteps;
+        shape_ms_[c] = ms / kTuneSteps;
+        if (c == 0 || ms < best) {
+            best = ms;
+            pick = sh;
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (st != LBM_OK) return st;
+    shape_ = pick;
+    shape_src_ = 1;
+    tune_shape_ = false;
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    g_shapes[ShapeKey{storage_, collision_, layout_, size(), sms_, fluid_cells()}] = pick;
+    return LBM_OK;
+}
+
 lbm_status Batch::step(long long n)
 {
     TraceRange trace("lbm.step");
@@ -663,36 +834,20 @@ lbm_status Batch::step(long long n)
     }
     int wx = 0;
     for (auto &p : inst_) wx |= p->desc.wall >= LBM_LIBB;
-    StepQueue q{&ops(), Launch{d_table_, d_stiles_, nstiles_, kTileSegs, grid_, kStepWarps * 32, stream_},
-                size() == 1 ? &h_table_[0] : nullptr, wx, tma_ ? &tma_launch_ : nullptr, collision_, layout_,
-                d_status_, size(), d_stile_count_, d_sums_, size(), d_fscratch_, d_fcount_};
-    const long long kChunk = 1000;
+    const int nc = (int)(sizeof(kShapeCandidates) / sizeof(kShapeCandidates[0]));
     long long left = n;
+    if (tune_shape_ && n > (long long)nc * kTuneSteps) {  // the first steps time the shapes
+        lbm_status st = tune_shape(wx);
+        if (st != LBM_OK) return st;
+        left -= (long long)nc * kTuneSteps;
+    }
+    const long long kChunk = 1000;
     while (left > 0) {
         const long long m = left > 2 * kChunk ? kChunk : left;
         const bool red = (m == left);
-        const auto key = std::make_tuple(m * 2 + (red ? 1 : 0), flip_, aa_phase_);
-        auto it = graphs_.find(key);
         cudaGraphExec_t exec = nullptr;
-        if (it == graphs_.end()) {
-            int f = flip_, a = aa_phase_;
-            long long dummy = 0;
-            cudaGraph_t graph = nullptr;
-            CK(cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = queue_steps(q, cap_, m, red, f, a, dummy);
-            cudaError_t e2 = cudaStreamEndCapture(cap_, &graph);
-            if (e != cudaSuccess) {
-                if (graph) cudaGraphDestroy(graph);
-                return cuda_fail(e, "capture of step kernels");
-            }
-            if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
-            e = cudaGraphInstantiate(&exec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-            graphs_[key] = exec;
-        } else {
-            exec = it->second;
-        }
+        lbm_status st = graph_for(m, red, shape_, wx, &exec);
+        if (st != LBM_OK) return st;
         CK(cudaGraphLaunch(exec, stream_));
         launches_ += m + (red ? 1 : 0);
         if (layout_ == LBM_LAYOUT_AB) flip_ ^= (int)(m & 1);
@@ -1051,6 +1206,9 @@ void Batch::fill_info(int i, lbm_info *out) const
     out->autotune = tune_src_;
     out->tune_ms_tiles = tune_ms_[0];
     out->tune_ms_bricks = tune_ms_[1];
+    out->step_warps = tma_ ? 0 : shape_.warps;
+    out->shape_source = shape_src_;
+    for (int c = 0; c < kShapeWarpsN; ++c) out->shape_ms[c] = shape_ms_[c];
 }
 
 // ------------------------------------------------------------------------------------

@@ -1,6 +1,6 @@
 // batch.h -- host runtime object behind contexts, batches and the server: a set of
 // independent periodic cells that share storage format, collision operator and layout
-// and advance together, one persistent kernel launch per time step.
+// and advance together, one kernel launch per time step over the tiles of all of them.
 #pragma once
 
 #include <map>
@@ -39,6 +39,14 @@ struct Instance {
     Instance &operator=(const Instance &) = delete;
     ~Instance();                     // frees the instance's device memory
 };
+
+// Block shape of the non-reducing SBB/CLI step: warps per block, one tile of that many work
+// items per block.
+struct StepShape {
+    int warps = kStepWarps;
+};
+constexpr int kShapeWarps[] = {4, 2, 8};  // the candidates, in the order they are timed
+constexpr int kShapeWarpsN = 3;
 
 class Batch {
 public:
@@ -90,6 +98,23 @@ public:
     lbm_status prepare();              // upload tables and choose the step kernel now if pending
 
 private:
+    struct GraphKey {
+        long long steps_red;
+        int flip, aa, shape;
+        bool operator<(const GraphKey &o) const
+        {
+            return std::tie(steps_red, flip, aa, shape) < std::tie(o.steps_red, o.flip, o.aa, o.shape);
+        }
+    };
+    struct CachedGraph {
+        cudaGraphExec_t exec;
+        long long used;
+    };
+    static constexpr size_t kGraphCache = 16;  // instantiated step graphs kept per batch
+    Launch shaped_launch(const StepShape &sh, int kind) const;
+    lbm_status graph_for(long long m, bool red, const StepShape &sh, int wx, cudaGraphExec_t *out);
+    void lookup_shape();                // the cached shape of this batch, or tuning pending
+    lbm_status tune_shape(int wx);      // time every candidate shape on the live state
     lbm_status rebuild();          // upload table and tiles, drop graphs
     lbm_status aa_restart(int i);  // instance i (i < 0: all) set from outside: AA arrangement of step 0
     int cur_of(const Instance &in) const { return in.phase ^ flip_; }
@@ -128,7 +153,16 @@ private:
     int aa_phase_ = 0;
     bool dirty_ = true;
     long long launches_ = 0;
-    std::map<std::tuple<long long, int, int>, cudaGraphExec_t> graphs_;
+    std::map<GraphKey, CachedGraph> graphs_;
+    long long graph_clock_ = 0;
+    // tiles of every block shape of the non-reducing step
+    TileDev *d_wtiles_[kShapeWarpsN] = {nullptr, nullptr, nullptr};
+    int nwtiles_[kShapeWarpsN] = {0, 0, 0};
+    StepShape shape_;
+    int shape_src_ = 0;                // 0 default, 1 measured by this batch, 2 from the cache
+    double shape_ms_[kShapeWarpsN] = {0, 0, 0};
+    bool tune_shape_ = false;
+    int sms_ = 0;
     double *d_stage_ = nullptr;       // FP64 staging for import/export (one direction)
     long long stage_cells_ = 0;
     // state transfers: two staging buffers of one direction each, a copy stream, and

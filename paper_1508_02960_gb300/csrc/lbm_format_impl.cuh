@@ -32,51 +32,64 @@ cudaError_t launch_step(void (*kernel)(P...), const Launch &L, A &&...args)
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
 }
 
-template <int STORE, int COLL, int KIND, bool RED, bool WX>
+template <int STORE, int COLL, int KIND, bool RED, bool WX, int WARPS>
 cudaError_t step_red(const Launch &L, int flip, unsigned *status, const InstanceDev *one)
 {
     cudaError_t e;
     if (one) {  // a single instance: parameters travel in the constant bank
-        e = launch_step(step_kernel<COLL, STORE, KIND, false, RED, WX>, L, L.table, *one, L.tiles, L.ntiles, flip,
-                        status);
+        e = launch_step(step_kernel<COLL, STORE, KIND, false, RED, WX, WARPS>, L, L.table, *one, L.tiles, L.ntiles,
+                        flip, status);
     } else {  // a batch: parameters from the device table
         static const InstanceDev unused{};
-        e = launch_step(step_kernel<COLL, STORE, KIND, true, RED, WX>, L, L.table, unused, L.tiles, L.ntiles, flip,
-                        status);
+        e = launch_step(step_kernel<COLL, STORE, KIND, true, RED, WX, WARPS>, L, L.table, unused, L.tiles, L.ntiles,
+                        flip, status);
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
-// wx: some instance uses an interpolated wall rule (LIBB, QIBB, IEBB, MR; A-B only)
+// wx: some instance uses an interpolated wall rule (LIBB, QIBB, IEBB, MR; A-B only).
+// warps: warps per block of a non-reducing SBB/CLI step (2, 4 or 8); the reducing and the
+// interpolated-wall steps run kStepWarps.
 template <int STORE, int COLL, int KIND>
-cudaError_t step_one(const Launch &L, int flip, int reduce, unsigned *status, const InstanceDev *one, int wx)
+cudaError_t step_one(const Launch &L, int flip, int reduce, unsigned *status, const InstanceDev *one, int wx,
+                     int warps)
 {
     if constexpr (KIND == KIND_AB) {
         if (wx)
-            return reduce ? step_red<STORE, COLL, KIND, true, true>(L, flip, status, one)
-                          : step_red<STORE, COLL, KIND, false, true>(L, flip, status, one);
+            return reduce ? step_red<STORE, COLL, KIND, true, true, kStepWarps>(L, flip, status, one)
+                          : step_red<STORE, COLL, KIND, false, true, kStepWarps>(L, flip, status, one);
     } else {
         if (wx) return cudaErrorInvalidValue;
     }
-    return reduce ? step_red<STORE, COLL, KIND, true, false>(L, flip, status, one)
-                  : step_red<STORE, COLL, KIND, false, false>(L, flip, status, one);
+    if (reduce) return step_red<STORE, COLL, KIND, true, false, kStepWarps>(L, flip, status, one);
+    switch (warps) {
+    case 2: return step_red<STORE, COLL, KIND, false, false, 2>(L, flip, status, one);
+    case 8: return step_red<STORE, COLL, KIND, false, false, 8>(L, flip, status, one);
+    default: return step_red<STORE, COLL, KIND, false, false, kStepWarps>(L, flip, status, one);
+    }
 }
 
 template <int STORE>
 cudaError_t step(int coll, int kind, const Launch &L, int flip, int reduce, unsigned *status, const InstanceDev *one,
-                 int wx)
+                 int wx, int warps)
 {
     switch (coll * 3 + kind) {
-    case COLL_SRT * 3 + KIND_AB: return step_one<STORE, COLL_SRT, KIND_AB>(L, flip, reduce, status, one, wx);
-    case COLL_SRT * 3 + KIND_AA_PULL: return step_one<STORE, COLL_SRT, KIND_AA_PULL>(L, flip, reduce, status, one, wx);
-    case COLL_SRT * 3 + KIND_AA_LOCAL: return step_one<STORE, COLL_SRT, KIND_AA_LOCAL>(L, flip, reduce, status, one, wx);
-    case COLL_TRT * 3 + KIND_AB: return step_one<STORE, COLL_TRT, KIND_AB>(L, flip, reduce, status, one, wx);
-    case COLL_TRT * 3 + KIND_AA_PULL: return step_one<STORE, COLL_TRT, KIND_AA_PULL>(L, flip, reduce, status, one, wx);
-    case COLL_TRT * 3 + KIND_AA_LOCAL: return step_one<STORE, COLL_TRT, KIND_AA_LOCAL>(L, flip, reduce, status, one, wx);
-    case COLL_MRT * 3 + KIND_AB: return step_one<STORE, COLL_MRT, KIND_AB>(L, flip, reduce, status, one, wx);
-    case COLL_MRT * 3 + KIND_AA_PULL: return step_one<STORE, COLL_MRT, KIND_AA_PULL>(L, flip, reduce, status, one, wx);
-    case COLL_MRT * 3 + KIND_AA_LOCAL: return step_one<STORE, COLL_MRT, KIND_AA_LOCAL>(L, flip, reduce, status, one, wx);
+    case COLL_SRT * 3 + KIND_AB: return step_one<STORE, COLL_SRT, KIND_AB>(L, flip, reduce, status, one, wx, warps);
+    case COLL_SRT * 3 + KIND_AA_PULL:
+        return step_one<STORE, COLL_SRT, KIND_AA_PULL>(L, flip, reduce, status, one, wx, warps);
+    case COLL_SRT * 3 + KIND_AA_LOCAL:
+        return step_one<STORE, COLL_SRT, KIND_AA_LOCAL>(L, flip, reduce, status, one, wx, warps);
+    case COLL_TRT * 3 + KIND_AB: return step_one<STORE, COLL_TRT, KIND_AB>(L, flip, reduce, status, one, wx, warps);
+    case COLL_TRT * 3 + KIND_AA_PULL:
+        return step_one<STORE, COLL_TRT, KIND_AA_PULL>(L, flip, reduce, status, one, wx, warps);
+    case COLL_TRT * 3 + KIND_AA_LOCAL:
+        return step_one<STORE, COLL_TRT, KIND_AA_LOCAL>(L, flip, reduce, status, one, wx, warps);
+    case COLL_MRT * 3 + KIND_AB: return step_one<STORE, COLL_MRT, KIND_AB>(L, flip, reduce, status, one, wx, warps);
+    case COLL_MRT * 3 + KIND_AA_PULL:
+        return step_one<STORE, COLL_MRT, KIND_AA_PULL>(L, flip, reduce, status, one, wx, warps);
+    case COLL_MRT * 3 + KIND_AA_LOCAL:
+        return step_one<STORE, COLL_MRT, KIND_AA_LOCAL>(L, flip, reduce, status, one, wx, warps);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -139,24 +152,6 @@ template <int STORE> int tma_prepare(int coll, int wx)
     case COLL_MRT * 2: return tma_prepare_one<STORE, COLL_MRT, false>();
     case COLL_MRT * 2 + 1: return tma_prepare_one<STORE, COLL_MRT, true>();
     default: return 0;
-    }
-}
-
-// The single-instance, non-reducing kernel of (coll, kind): the one a time step runs.
-template <int STORE>
-const void *step_ptr(int coll, int kind)
-{
-    switch (coll * 3 + kind) {
-    case COLL_SRT * 3 + KIND_AB: return (const void *)step_kernel<COLL_SRT, STORE, KIND_AB, false, false, false>;
-    case COLL_SRT * 3 + KIND_AA_PULL: return (const void *)step_kernel<COLL_SRT, STORE, KIND_AA_PULL, false, false, false>;
-    case COLL_SRT * 3 + KIND_AA_LOCAL: return (const void *)step_kernel<COLL_SRT, STORE, KIND_AA_LOCAL, false, false, false>;
-    case COLL_TRT * 3 + KIND_AB: return (const void *)step_kernel<COLL_TRT, STORE, KIND_AB, false, false, false>;
-    case COLL_TRT * 3 + KIND_AA_PULL: return (const void *)step_kernel<COLL_TRT, STORE, KIND_AA_PULL, false, false, false>;
-    case COLL_TRT * 3 + KIND_AA_LOCAL: return (const void *)step_kernel<COLL_TRT, STORE, KIND_AA_LOCAL, false, false, false>;
-    case COLL_MRT * 3 + KIND_AB: return (const void *)step_kernel<COLL_MRT, STORE, KIND_AB, false, false, false>;
-    case COLL_MRT * 3 + KIND_AA_PULL: return (const void *)step_kernel<COLL_MRT, STORE, KIND_AA_PULL, false, false, false>;
-    case COLL_MRT * 3 + KIND_AA_LOCAL: return (const void *)step_kernel<COLL_MRT, STORE, KIND_AA_LOCAL, false, false, false>;
-    default: return nullptr;
     }
 }
 
@@ -236,7 +231,6 @@ FormatOps make_ops()
     o.wall_prepare = &wall_prepare<STORE>;
     o.step_tma = &step_tma<STORE>;
     o.tma_prepare = &tma_prepare<STORE>;
-    o.step_kernel_ptr = &step_ptr<STORE>;
     return o;
 }
 

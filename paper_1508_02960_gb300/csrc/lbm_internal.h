@@ -54,8 +54,10 @@ struct TmaLaunch {
 struct FormatOps {
     // one: host copy of the only instance's parameters (passed by value), or NULL for a batch;
     // wx: some instance uses LIBB, QIBB, IEBB or MR (A-B layout)
+    // warps: warps per block of a non-reducing SBB/CLI step (2, 4 or 8; the reducing and the
+    // interpolated-wall steps run kStepWarps); L.block must be warps * 32
     cudaError_t (*step)(int coll, int kind, const Launch &L, int flip, int reduce, unsigned *status,
-                        const InstanceDev *one, int wx);
+                        const InstanceDev *one, int wx, int warps);
     cudaError_t (*init)(const InstanceDev *table, int inst, long long ncells, int layout, int cur,
                         double amp, unsigned long long seed, cudaStream_t s);
     cudaError_t (*import_dir)(const InstanceDev *table, int inst, long long ncells, int layout, int cur,
@@ -77,7 +79,6 @@ struct FormatOps {
     // A-B from buffer cur, 1 = AA at phase 0)
     cudaError_t (*wall_prepare)(const InstanceDev *table, int inst, long long n_boundary, const long long *bcell,
                                 int layout, int cur, cudaStream_t s);
-    const void *(*step_kernel_ptr)(int coll, int kind);  // for occupancy queries
 };
 
 const FormatOps &format_ops(int storage);

@@ -165,9 +165,9 @@ __device__ __forceinline__ uint2 ld_keep(const uint2 *a, uint64_t pol)
 #ifndef LBM_STEP_WARPS_PER_SM
 #define LBM_STEP_WARPS_PER_SM 36
 #endif
-template <int STORE, int COLL, bool RED, bool WX> constexpr int step_min_blocks()
+template <int STORE, int COLL, bool RED, bool WX, int WARPS = kStepWarps> constexpr int step_min_blocks()
 {
-    return (STORE == ST_F64 ? 8 : (RED || WX || COLL == COLL_MRT) ? 32 : LBM_STEP_WARPS_PER_SM) / kStepWarps;
+    return (STORE == ST_F64 ? 8 : (RED || WX || COLL == COLL_MRT) ? 32 : LBM_STEP_WARPS_PER_SM) / WARPS;
 }
 
 // Moments of the incoming populations (Eq. Macro), in deviation form.
@@ -646,7 +646,7 @@ __device__ __forceinline__ void warp_sum_ff(float &hi, float &lo)
 template <typename R>
 __device__ __forceinline__ void reduce_tile(const RedAcc<R> &acc, double *partials, long long tile)
 {
-    __shared__ double red[kStepWarps][RED_F + 3];
+    __shared__ double red[kStepWarps][RED_F + 3];  // the reducing step runs kStepWarps-warp blocks
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double v[RED_F + 3];
 #pragma unroll
@@ -695,19 +695,21 @@ __device__ __forceinline__ const InstanceDev &instance_of(const InstanceDev *tab
     else return one;
 }
 
-// The fused step.  One block per tile of kStepWarps work items (32 fluid cells each), one
-// item per warp.  A single instance's parameters travel by value (constant bank); a
-// batch's come from the device table (A-B layout only).  flip selects the A-B buffer pair
-// (src = f[phase ^ flip]).  The RED variant (the step that ends a chunk) also makes every
-// tile write its FP64 partial sums (the kRedSlots slots: drho, u_x, u_y, u_z and the
-// momentum exchanged with the solid) and flags diverged cells in status[instance]; the
-// other steps carry none of that code.  The WX variant (A-B only) also runs the
-// interpolated wall rules LIBB, QIBB, IEBB and MR.
-template <int COLL, int STORE, int KIND, bool BATCH, bool RED, bool WX>
-__global__ void __launch_bounds__(kStepWarps * 32, step_min_blocks<STORE, COLL, RED, WX>())
+// The fused step.  One block of WARPS warps per tile of WARPS work items (32 fluid cells
+// each), one item per warp.  Each cell's arithmetic does not depend on WARPS, so every block
+// shape gives the same state bit for bit; the reducing step always runs kStepWarps-warp
+// tiles.  A single instance's parameters travel by value (constant bank); a batch's come
+// from the device table.  flip selects the A-B buffer pair (src = f[phase ^ flip]).  The RED
+// variant (the step that ends a chunk) also makes every tile write its FP64 partial sums
+// (the kRedSlots slots: drho, u_x, u_y, u_z and the momentum exchanged with the solid) and
+// flags diverged cells in status[instance]; the other steps carry none of that code.  The WX
+// variant (A-B only) also runs the interpolated wall rules LIBB, QIBB, IEBB and MR.
+template <int COLL, int STORE, int KIND, bool BATCH, bool RED, bool WX, int WARPS = kStepWarps>
+__global__ void __launch_bounds__(WARPS * 32, step_min_blocks<STORE, COLL, RED, WX, WARPS>())
     step_kernel(const InstanceDev *__restrict__ table, const __grid_constant__ InstanceDev one,
                 const TileDev *__restrict__ tiles, int ntiles, int flip, unsigned *__restrict__ status)
 {
+    static_assert(!RED || WARPS == kStepWarps, "the reducing step runs kStepWarps-warp tiles");
     using S = Store<STORE>;
     using T = typename S::T;
     using R = typename S::R;
@@ -715,11 +717,11 @@ __global__ void __launch_bounds__(kStepWarps * 32, step_min_blocks<STORE, COLL, 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int t = blockIdx.x;
     if (t >= ntiles) return;
-    // a single instance's tiles are consecutive: tile t holds work items kTileSegs t ...
-    // (its table entry holds the same, so that no load precedes the work list's)
+    // a single instance's tiles are consecutive: tile t holds work items WARPS t ... (its
+    // table entry holds the same, so that no load precedes the work list's)
     TileDev tile;
     if constexpr (BATCH) tile = tiles[t];
-    else tile = TileDev{0, t, (long long)t * kTileSegs};
+    else tile = TileDev{0, t, (long long)t * WARPS};
     const InstanceDev &I = instance_of<BATCH>(table, one, tile.inst);
     const Par<R> P = load_par<R>(I);
     R rates[Q];

@@ -50,9 +50,10 @@ int main(void) {
          sizeof(lbm_server_opts), sizeof(lbm_server_stats), sizeof(lbm_sphere));
   printf("%zu %zu %zu %zu %zu\\n", offsetof(lbm_desc, tau), offsetof(lbm_desc, collision),
          offsetof(lbm_desc, d_p), offsetof(lbm_desc, seed), offsetof(lbm_info, block_cells));
-  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(lbm_develop_opts), sizeof(lbm_develop_result),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(lbm_develop_opts), sizeof(lbm_develop_result),
          offsetof(lbm_develop_result, developed), offsetof(lbm_obs, K_star), offsetof(lbm_develop_opts, max_steps),
-         offsetof(lbm_info, autotune), offsetof(lbm_info, tune_ms_bricks));
+         offsetof(lbm_info, autotune), offsetof(lbm_info, tune_ms_bricks), offsetof(lbm_info, step_warps),
+         offsetof(lbm_info, shape_ms));
   return 0;
 }
 """)
@@ -68,7 +69,8 @@ int main(void) {
     assert [int(v) for v in c.split()] == [ctypes.sizeof(capi.DevelopOpts), ctypes.sizeof(capi.DevelopResult),
                                            capi.DevelopResult.developed.offset, capi.Obs.K_star.offset,
                                            capi.DevelopOpts.max_steps.offset, capi.Info.autotune.offset,
-                                           capi.Info.tune_ms_bricks.offset]
+                                           capi.Info.tune_ms_bricks.offset, capi.Info.step_warps.offset,
+                                           capi.Info.shape_ms.offset]
 
 
 @pytest.mark.parametrize("bad", [

@@ -307,13 +307,15 @@ def test_batch_alone_vs_mix_bitwise(capi, layout):
     descs = [d for d, _ in descs_keep]
     b = capi.Batch(descs)
     b.init_equilibrium()
-    b.step(60)
+    b.step(160)                                   # the first 48 steps time the block shapes
+    info = b.info()
+    assert info["step_warps"] in (2, 4, 8) and info["shape_source"] in (1, 2)
     mix = [(b.get_populations(i), b.observables(i)) for i in range(len(geoms))]
     b.close()
     for i, d in enumerate(descs):
         with capi.Context(desc=d) as ctx:
             ctx.init_equilibrium()
-            ctx.step(60)
+            ctx.step(160)
             assert np.array_equal(ctx.get_populations(), mix[i][0])
             assert ctx.observables()["U_sup"] == mix[i][1]["U_sup"]
 
@@ -343,3 +345,23 @@ def test_aa_batch_sets_one_instance_only_in_step0_arrangement(capi, orc):
             assert np.array_equal(ctx.get_populations(), b.get_populations(1))
     finally:
         b.close()
+
+
+@pytest.mark.parametrize("layout", ["AB", "AA"])
+def test_block_shapes_give_the_same_state(capi, layout):
+    """The online shape tuner times three block shapes on the live state (4, 2 and 8 warps per
+    block): a run whose first 48 steps went through all of them equals, bit for bit, a run in
+    short calls that never tunes."""
+    g = STAGED
+    kw = dict(spheres=g.spheres, shape=g.shape, tau=0.64, delta_rho=2e-4, collision=capi.TRT, wall=capi.CLI,
+              storage=capi.F32, layout=getattr(capi, "LAYOUT_" + layout))
+    with capi.Context(**kw) as a, capi.Context(**kw) as b:
+        a.init_equilibrium()
+        b.init_equilibrium()
+        a.step(200)
+        ia = a.info()
+        assert ia["shape_source"] in (1, 2) and ia["step_warps"] in (2, 4, 8)
+        for _ in range(5):
+            b.step(40)                             # calls of at most 48 steps: no tuning here
+        assert np.array_equal(a.get_populations(), b.get_populations())
+        assert a.observables()["U_sup"] == b.observables()["U_sup"]

@@ -258,9 +258,11 @@ def study_sweep(args):
         g = p.geometry
         dr = capi.delta_rho_for_re_p(p.re_p, p.tau, g.d_p, p.L, K, 0.0078)
         d, k = capi.make_desc(spheres=g.spheres, shape=g.shape, tau=p.tau, delta_rho=dr, collision=capi.TRT,
-                              wall=capi.CLI, storage=capi.F16DEV, magic_lambda=p.magic_lambda)
+                              wall=capi.CLI, storage=capi.F16DEV, magic_lambda=p.magic_lambda,
+                              layout=getattr(capi, "LAYOUT_" + args.sweep_layout))
         sub.append((d, k, p))
-    total_bytes = sum(2 * 19 * 2 * p.L ** 3 for p in pts)
+    buffers = 2 if args.sweep_layout == "AB" else 1
+    total_bytes = sum(buffers * 19 * 2 * p.L ** 3 for p in pts)
     srv = capi.Server(hbm_budget_bytes=int(args.sweep_budget_gb * 2 ** 30), check_interval=200, max_resident=256)
     t0 = time.perf_counter()
     ids = [srv.submit(d, 1e-6, args.study_max_steps) for d, _, _ in sub]
@@ -283,7 +285,8 @@ def study_sweep(args):
         checks.append({"point": j, "L": p.L, "steps_alone": steps, "steps_mix": res[j][1]["steps"],
                        "U_alone": o["U_sup"], "U_mix": res[j][1]["U_sup"],
                        "identical": o["U_sup"] == res[j][1]["U_sup"] and steps == res[j][1]["steps"]})
-    print(json.dumps({"study": "sweep", "points": len(pts), "cells_total": int(sum(p.L ** 3 for p in pts)),
+    print(json.dumps({"study": "sweep", "layout": args.sweep_layout, "storage": "F16DEV",
+                      "points": len(pts), "cells_total": int(sum(p.L ** 3 for p in pts)),
                       "population_bytes_total": total_bytes, "budget_gb": args.sweep_budget_gb,
                       "wall_s": wall, "aggregate_mlups": stats["mlups"], "busy_s": stats["busy_seconds"],
                       "fluid_updates": stats["fluid_updates"], "converged": conv, "capped": len(pts) - conv,
@@ -734,6 +737,7 @@ def main():
     ap.add_argument("--study-max-steps", type=int, default=60000)
     ap.add_argument("--sweep-points", type=int, default=64)
     ap.add_argument("--sweep-budget-gb", type=float, default=6.0)
+    ap.add_argument("--sweep-layout", choices=["AB", "AA"], default="AB")
     args = ap.parse_args()
     if args.profile_steps > 0:
         run_profile(args)

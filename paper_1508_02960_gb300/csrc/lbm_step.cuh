@@ -159,15 +159,19 @@ __device__ __forceinline__ uint2 ld_keep(const uint2 *a, uint64_t pol)
 
 // Blocks per multiprocessor the register allocation is sized for.  The plain SRT and TRT
 // step of the 32- and 16-bit formats: 36 warps (56 registers a thread; measured 1-6 %
-// faster than 32 warps at 64 registers, and 40 warps spill).  MRT and the reducing and
-// interpolated-wall variants keep 32 warps (64 registers), where 56 would spill (MRT at 56
-// spills 136 bytes and ran 3 % slower).  FP64: 8 warps.
+// faster than 32 warps at 64 registers, and 40 warps spill).  MRT, the reducing and
+// interpolated-wall variants and the in-place 16-bit steps keep 32 warps (64 registers),
+// where 56 would spill (MRT at 56 spills 136 bytes and ran 3 % slower).  FP64: 8 warps.
 #ifndef LBM_STEP_WARPS_PER_SM
 #define LBM_STEP_WARPS_PER_SM 36
 #endif
-template <int STORE, int COLL, bool RED, bool WX, int WARPS = kStepWarps> constexpr int step_min_blocks()
+template <int STORE, int COLL, bool RED, bool WX, int WARPS = kStepWarps, int KIND = KIND_AB>
+constexpr int step_min_blocks()
 {
-    return (STORE == ST_F64 ? 8 : (RED || WX || COLL == COLL_MRT) ? 32 : LBM_STEP_WARPS_PER_SM) / WARPS;
+    // the in-place steps of the 16-bit formats (stochastic rounding, scaling) spill at 56
+    // registers: 32 warps, measured 0.3-3 % faster than 36
+    constexpr bool wide = RED || WX || COLL == COLL_MRT || ((STORE == ST_F16 || STORE == ST_BF16) && KIND != KIND_AB);
+    return (STORE == ST_F64 ? 8 : wide ? 32 : LBM_STEP_WARPS_PER_SM) / WARPS;
 }
 
 // Moments of the incoming populations (Eq. Macro), in deviation form.
@@ -705,7 +709,7 @@ __device__ __forceinline__ const InstanceDev &instance_of(const InstanceDev *tab
 // flags diverged cells in status[instance]; the other steps carry none of that code.  The WX
 // variant (A-B only) also runs the interpolated wall rules LIBB, QIBB, IEBB and MR.
 template <int COLL, int STORE, int KIND, bool BATCH, bool RED, bool WX, int WARPS = kStepWarps>
-__global__ void __launch_bounds__(WARPS * 32, step_min_blocks<STORE, COLL, RED, WX, WARPS>())
+__global__ void __launch_bounds__(WARPS * 32, step_min_blocks<STORE, COLL, RED, WX, WARPS, KIND>())
     step_kernel(const InstanceDev *__restrict__ table, const __grid_constant__ InstanceDev one,
                 const TileDev *__restrict__ tiles, int ntiles, int flip, unsigned *__restrict__ status)
 {

@@ -424,3 +424,33 @@ def test_sbb_cli_agree_under_refinement(orc):
     assert abs(cli[1] / cli[0] - 1) < 1e-2
     assert abs(cli[1] / cli[0] - 1) < abs(sbb[1] / sbb[0] - 1)
     assert (np.abs(sbb / cli - 1) < 0.06).all()
+
+
+def test_time_averages_of_a_steady_flow(orc):
+    """The oracle's time averages (Sec. 4: averages of the developed flow) pinned by a steady
+    Stokes flow: once the flow no longer changes, the windowed average of U_sup and of the
+    drag equals the steady value, and the developed-flow procedure finds the drag converged
+    and averages round(average_ft * samples_per_ft) samples of round(T / samples_per_ft)
+    steps, T = nx / U_sup."""
+    g = I.centred_sphere(12, 3.5)
+    s = orc.voxelize(g.shape, g.spheres)
+    q = orc.wall_distances(s, g.spheres)
+    kw = dict(q=q, tau=0.8, delta_rho=2e-3, magic_lambda=3 / 16, collision=1, wall=1)
+    f, U_old = orc.init_rest(s), None
+    for _ in range(200):
+        F = np.zeros(3)
+        f, sums, _ = orc.run(s, f, 100, force=F, **kw)
+        U = sums[1] / g.n_cells
+        if U_old is not None and abs(U - U_old) < 1e-13 * abs(U):
+            break
+        U_old = U
+    _, U_avg, F_avg = orc.time_average(s, f, 5, 40, **kw)
+    assert U_avg == pytest.approx(U, rel=1e-12, abs=0)
+    assert np.allclose(F_avg, F, rtol=1e-10, atol=1e-12 * abs(F[0]))     # F_y, F_z: rounding only
+    o = orc.developed_average(s, f, min_spinup_ft=1.0, max_spinup_ft=50.0, drag_tol=1e-9, average_ft=2.0,
+                              samples_per_ft=3, max_steps=10 ** 6, **kw)
+    assert o["status"] == "ok" and o["developed"]
+    T = 12 / abs(U)
+    assert o["average_steps"] == 6 * int(np.floor(T / 3 + 0.5))
+    assert o["U_sup"] == pytest.approx(U, rel=1e-12, abs=0)
+    assert np.allclose(o["F"], F, rtol=1e-10, atol=1e-12 * abs(F[0]))

@@ -173,13 +173,19 @@ __global__ void fwarp_kernel(long long nw, const uint32_t *__restrict__ fcell, c
     }
 }
 
-// The step kernels' per-lane work-list entries, so that a step finds a cell's wall mask
-// and links without a dependent load: flane[32w + l] = {cell, wall mask | (first link -
-// the warp's first link) << 19}, and fwarp[w].y becomes the warp's first link (0 when it
-// has no boundary cell).  A warp's links are consecutive (boundary cells in cell order, each
-// with at most 18 links), so the offset fits in the 13 bits above the mask.
-__global__ void flane_kernel(long long nw, const uint32_t *__restrict__ fcell, const uint32_t *__restrict__ bmask,
-                             const uint32_t *__restrict__ boff, uint2 *__restrict__ fwarp, uint2 *__restrict__ flane)
+// The step kernels' per-lane work-list entries, so that a step finds what it needs of a
+// cell without a dependent load or a division: flane[32w + l] = {cell, bits}, bits holding
+//   0-18   the wall mask (bit k: x - e_k solid),
+//   19-28  the cell's first link minus the warp's first link,
+//   29, 30 x = 0, x = nx - 1 (the pulls and pushes that cross the x faces),
+//   31     every cell of the warp is away from the y and z faces (the same in all 32 lanes),
+// and fwarp[w].y becomes the warp's first link (0 when it has no boundary cell).  A warp's
+// links are consecutive (boundary cells in cell order, each with at most 18 of them), so
+// the offset is below 31 * 18 < 2^10.  Padding lanes hold cell 0xFFFFFFFF and no flags.
+static_assert(31 * 18 < (1 << 10), "link offset field of the work-list entries");
+__global__ void flane_kernel(long long nw, int nx, int ny, int nz, const uint32_t *__restrict__ fcell,
+                             const uint32_t *__restrict__ bmask, const uint32_t *__restrict__ boff,
+                             uint2 *__restrict__ fwarp, uint2 *__restrict__ flane)
 {
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
@@ -193,7 +199,16 @@ __global__ void flane_kernel(long long nw, const uint32_t *__restrict__ fcell, c
             off = boff[b];
         }
         const uint32_t base = wd.x ? __shfl_sync(0xffffffffu, off, __ffs(wd.x) - 1) : 0u;
-        flane[w * 32 + lane] = make_uint2(c, wm | ((wm ? off - base : 0u) << 19));
+        uint32_t flags = 0u;
+        bool in_yz = true;
+        if (c != 0xFFFFFFFFu) {
+            const uint32_t x = c % (uint32_t)nx, yz = c / (uint32_t)nx;
+            const uint32_t y = yz % (uint32_t)ny, z = yz / (uint32_t)ny;
+            flags = (x == 0 ? 1u << 29 : 0u) | (x == (uint32_t)nx - 1u ? 1u << 30 : 0u);
+            in_yz = y >= 1 && y + 2 <= (uint32_t)ny && z >= 1 && z + 2 <= (uint32_t)nz;
+        }
+        if (__all_sync(0xffffffffu, in_yz)) flags |= 1u << 31;
+        flane[w * 32 + lane] = make_uint2(c, wm | ((wm ? off - base : 0u) << 19) | flags);
         __syncwarp();
         if (lane == 0) fwarp[w].y = base;
     }
@@ -629,8 +644,8 @@ cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_
     }
     // per-lane entries of the step kernels' work list (needs the boundary table's links)
     GEO_CHECK(dev_alloc(&g->flane, sizeof(uint2) * 32 * g->n_fwarps_padded));
-    flane_kernel<<<grid_for(g->n_fwarps_padded * 32, 256), 256, 0, s>>>(g->n_fwarps_padded, g->fcell, g->bmask,
-                                                                          g->boff, g->fwarp, g->flane);
+    flane_kernel<<<grid_for(g->n_fwarps_padded * 32, 256), 256, 0, s>>>(g->n_fwarps_padded, nx, ny, nz, g->fcell,
+                                                                          g->bmask, g->boff, g->fwarp, g->flane);
     GEO_CHECK(cudaGetLastError());
     GEO_CHECK(cudaMemcpyAsync(h_ctr, d_ctr, sizeof(h_ctr), cudaMemcpyDeviceToHost, s));
     GEO_CHECK(cudaStreamSynchronize(s));

@@ -223,9 +223,10 @@ enum { STATUS_DIVERGED = 1u, STATUS_TIMEOUT = 2u, STATUS_BOUNDS = 4u };
 // The step kernels take the fluid cells themselves, in cell order, 32 per warp: fcell[32w +
 // l] is the cell of lane l of fluid warp w (0xFFFFFFFF past the last fluid cell), fwarp[w].x
 // bit l set when that cell is a boundary cell, fwarp[w].y the index of the warp's first
-// link; flane[32w + l] = {fcell[32w + l], wall mask | (first link - fwarp[w].y) << 19} (the
-// mask as bmask below, 0 for other cells), so that a step needs no dependent load to find
-// a cell's walls.
+// link; flane[32w + l] = {fcell[32w + l], bits}: bits 0-18 the wall mask (as bmask below, 0
+// for other cells), 19-28 the first link - fwarp[w].y, 29 and 30 x = 0 and x = nx - 1, 31
+// all 32 cells of the warp away from the y and z faces, so that a step needs no dependent
+// load and no division to find a cell's walls and its periodic fix-ups.
 // Boundary cell b: bmask[b] bit k set when x - e_k is solid (the pull of direction k hits
 // the wall), boff[b] the index of its first link; its links are ordered by k.  Link l:
 // linkc[l] = CLI coefficient (1-2q)/(1+2q) (0 where CLI falls back to SBB).

@@ -94,8 +94,8 @@ struct GeometryDev {
     uint4 *aseg = nullptr;         // [n_active_padded] segments holding fluid: {x, y, z, segment}
     long long n_active = 0, n_active_padded = 0;
     uint32_t *fcell = nullptr;     // [32 n_fwarps_padded] fluid cells in cell order (pad 0xFFFFFFFF)
-    uint2 *flane = nullptr;        // [32 n_fwarps_padded] the same cells with their wall masks:
-                                   // {cell, wall mask | (first link - warp's first link) << 19}
+    uint2 *flane = nullptr;        // [32 n_fwarps_padded] the same cells with their wall masks,
+                                   // link offsets and face flags (lbm_device.cuh)
     uint2 *fwarp = nullptr;        // [n_fwarps_padded] per 32 fluid cells: boundary bits, first link
     long long n_fwarps = 0, n_fwarps_padded = 0;
     uint32_t *bmask = nullptr;     // [n_boundary]

@@ -367,7 +367,7 @@ __device__ __forceinline__ R wall_own_part_w(const Par<R> &P, const R *lw, int k
 // Walls in the AA layout: the same, with S where the AA layout's pull reads (see above).
 template <int COLL, int STORE, int KIND, bool RED, bool WX, typename R>
 __device__ __forceinline__ void finish_cell(const InstanceDev &I, R (&g)[Q], const Par<R> &P, const R *rates,
-                                            uint32_t cell, uint32_t x,
+                                            uint32_t cell, uint32_t xf,
                                             bool inner, const uint32_t *pull_off, const uint32_t *push_off,
                                             uint32_t wm, uint32_t off, const typename Store<STORE>::T *fs,
                                             typename Store<STORE>::T *fd, const R *linkc, const R *linkw,
@@ -432,7 +432,7 @@ __device__ __forceinline__ void finish_cell(const InstanceDev &I, R (&g)[Q], con
         packed[k] = sr ? S::pack_sr(g[k], P.sc, round_bits(h, k, float(g[k]))) : S::pack(g[k], P.sc);
     if constexpr (KIND == KIND_AA_PULL) {
         if (push_off) {  // interior cell: x + e_k is cell + e_k, except across the x faces
-            const uint32_t cxm = x == 0 ? P.nx : 0u, cxp = x == P.nx - 1 ? P.nx : 0u;
+            const uint32_t cxm = (xf & 1u) ? P.nx : 0u, cxp = (xf & 2u) ? P.nx : 0u;
 #pragma unroll
             for (int k = 0; k < Q; ++k) {
                 uint32_t idx = cell + push_off[k];
@@ -471,7 +471,7 @@ __device__ __forceinline__ void finish_cell(const InstanceDev &I, R (&g)[Q], con
         // the next step's pull of direction k reads (A-B: slot k of x - e_k in the other
         // buffer; AA: slot kbar of x - e_k)
         if (wm) {
-            const uint32_t cxm = x == 0 ? P.nx : 0u, cxp = x == P.nx - 1 ? P.nx : 0u;
+            const uint32_t cxm = (xf & 1u) ? P.nx : 0u, cxp = (xf & 2u) ? P.nx : 0u;
             Coord co;
             if (!inner) co = coord_of(P, cell);
 #pragma unroll
@@ -506,15 +506,16 @@ __device__ __forceinline__ void finish_cell(const InstanceDev &I, R (&g)[Q], con
 // One warp's work item: 32 fluid cells of the work list (w = its index), their raw pulled
 // values (see pull_item) and what the finish needs.
 struct WarpItem {
-    uint32_t cell, x;  // this lane's cell (0xFFFFFFFF: padding lane) and its x
+    uint32_t cell;     // this lane's cell (0xFFFFFFFF: padding lane)
+    uint32_t xf;       // bit 0: x = 0, bit 1: x = nx - 1 (pulls and pushes across the x faces)
     uint32_t wm, off;  // boundary cell: wall mask (bit k: x - e_k solid) and first link; else 0
-    uint2 wd;          // boundary bits of the 32 lanes, first boundary-table index
+    uint2 wd;          // tiles: the warp's entry (.y its first link); bricks: y and z of the cell
     bool inner;        // every lane away from the y and z faces
 };
 
-// Locate one work item: this lane's cell and coordinates, its wall mask and links, and
-// whether every lane is away from the y and z faces.  Reads only the work list (one entry
-// per warp and one per lane, no dependent load), which no step writes.
+// Locate one work item: this lane's cell, its x-face flags, wall mask and links, and
+// whether every lane is away from the y and z faces, all precomputed in the work list (one
+// entry per warp and one per lane, no dependent load and no division), which no step writes.
 template <typename R>
 __device__ __forceinline__ void locate_item(const InstanceDev &I, const Par<R> &P, uint32_t w, int lane, WarpItem &it)
 {
@@ -524,15 +525,10 @@ __device__ __forceinline__ void locate_item(const InstanceDev &I, const Par<R> &
     const uint2 e = w_ok ? ld_keep(I.flane + (w * 32u + (uint32_t)lane), keep) : make_uint2(0xFFFFFFFFu, 0u);
     it.cell = e.x;
     if (it.cell != 0xFFFFFFFFu && !checked(I, it.cell, I.n32)) it.cell = 0xFFFFFFFFu;
-    const bool live = it.cell != 0xFFFFFFFFu;
-    const uint32_t yz = fast_div(it.cell, P.dnx);
-    it.x = it.cell - yz * P.nx;
-    const uint32_t z = fast_div(yz, P.dny);
-    const uint32_t y = yz - z * P.ny;
-    const bool in_yz = !live || (y - 1u < P.ny - 2u && z - 1u < P.nz - 2u);
-    it.inner = __all_sync(0xffffffffu, in_yz);
+    it.xf = (e.y >> 29) & 3u;
+    it.inner = (e.y >> 31) != 0u;  // the same in all lanes of the warp
     it.wm = e.y & 0x7FFFFu;
-    it.off = it.wd.y + (e.y >> 19);
+    it.off = it.wd.y + ((e.y >> 19) & 0x3FFu);
     // every link of the cell within the link tables
     if (it.wm && !checked(I, it.off + __popc(it.wm), I.n_links + 1u)) it.wm = 0u;
 }
@@ -547,7 +543,7 @@ __device__ __forceinline__ void pull_item(const InstanceDev &I, const Par<R> &P,
 {
     if (it.cell == 0xFFFFFFFFu) return;
     if (KIND != KIND_AA_LOCAL && it.inner) {
-        const uint32_t cxm = it.x == 0 ? P.nx : 0u, cxp = it.x == P.nx - 1 ? P.nx : 0u;
+        const uint32_t cxm = (it.xf & 1u) ? P.nx : 0u, cxp = (it.xf & 2u) ? P.nx : 0u;
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             uint32_t idx = it.cell + I.pull_off[k];
@@ -593,19 +589,19 @@ __device__ __forceinline__ void finish_item(const InstanceDev &I, const Par<R> &
     // pressure shift of the pulls that crossed the x boundary (wall directions take their
     // value from the wall rule instead)
     const uint32_t wm = it.wm;
-    if (it.x == 0) {
+    if (it.xf & 1u) {
 #pragma unroll
         for (int k = 0; k < Q; ++k)
             if (ex(k) == 1 && !((wm >> k) & 1u)) g[k] += R(weight(k)) * P.dshift;
     }
-    if (it.x == P.nx - 1) {
+    if (it.xf & 2u) {
 #pragma unroll
         for (int k = 0; k < Q; ++k)
             if (ex(k) == -1 && !((wm >> k) & 1u)) g[k] -= R(weight(k)) * P.dshift;
     }
     R rd = R(0), rx = R(0), ry = R(0), rz = R(0);
     R fm[3] = {R(0), R(0), R(0)};
-    finish_cell<COLL, STORE, KIND, RED, WX, R>(I, g, P, rates, it.cell, it.x, it.inner, I.pull_off,
+    finish_cell<COLL, STORE, KIND, RED, WX, R>(I, g, P, rates, it.cell, it.xf, it.inner, I.pull_off,
                                                it.inner ? I.push_off : nullptr, wm, it.off, fs, fd,
                                                reinterpret_cast<const R *>(I.linkc),
                                                reinterpret_cast<const R *>(I.linkw), status, rd, rx, ry, rz, fm);

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kBrickCells, tma_min_blocks<STORE>())
         const uint4 sg = in_box ? I.seg[cell >> 5] : make_uint4(~0u, 0u, 0u, 0u);
         const bool live = !((sg.x >> cx) & 1u);
         m.cell = live ? cell : 0xFFFFFFFFu;
-        m.x = x;
+        m.xf = (x == 0 ? 1u : 0u) | (x == P.nx - 1 ? 2u : 0u);
         m.wm = 0u;
         m.off = 0u;
         m.inner = (y - 1u < P.ny - 2u) && (z - 1u < P.nz - 2u);
@@ -177,14 +177,14 @@ __global__ void __launch_bounds__(kBrickCells, tma_min_blocks<STORE>())
         const int s = it % kBrickStages;
         const uint32_t parity = (uint32_t)(it / kBrickStages) & 1u;
         const bool live = meta.cell != 0xFFFFFFFFu;
-        const uint32_t x = meta.x, y = meta.wd.x, z = meta.wd.y;
+        const uint32_t xf = meta.xf, y = meta.wd.x, z = meta.wd.y;
         // pulls whose source lies across a face: outside the box, read directly
         T raw[Q];
         uint32_t wrap = 0u;
-        if (live && (x == 0 || x == P.nx - 1 || y == 0 || y == P.ny - 1 || z == 0 || z == P.nz - 1)) {
+        if (live && (xf != 0u || y == 0 || y == P.ny - 1 || z == 0 || z == P.nz - 1)) {
 #pragma unroll
             for (int k = 0; k < Q; ++k) {
-                const bool w = (ex(k) == 1 && x == 0) || (ex(k) == -1 && x == P.nx - 1) || (ey(k) == 1 && y == 0) ||
+                const bool w = (ex(k) == 1 && (xf & 1u)) || (ex(k) == -1 && (xf & 2u)) || (ey(k) == 1 && y == 0) ||
                                (ey(k) == -1 && y == P.ny - 1) || (ez(k) == 1 && z == 0) ||
                                (ez(k) == -1 && z == P.nz - 1);
                 wrap |= (w ? 1u : 0u) << k;

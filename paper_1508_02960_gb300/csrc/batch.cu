@@ -499,15 +499,17 @@ lbm_status Batch::rebuild()
         if (nt > in.partial_capacity || ns > in.partial_capacity) return fail(LBM_ERR_STATE, "partials too small");
         if (ns * kTileSegs > in.geo.n_fwarps_padded) return fail(LBM_ERR_STATE, "fluid work list too short");
         tc[i] = (int)nt;
-        for (long long t = 0; t < nt; ++t) tiles.push_back(TileDev{i, (int)t, t * CS});
+        for (long long t = 0; t < nt; ++t) tiles.push_back(TileDev{i, (int)t, t * CS, nullptr, nullptr});
         sc[i] = (int)ns;
-        for (long long t = 0; t < ns; ++t) stiles.push_back(TileDev{i, (int)t, t * kTileSegs});
+        for (long long t = 0; t < ns; ++t)
+            stiles.push_back(TileDev{i, (int)t, t * kTileSegs, in.geo.flane, in.geo.fwarp});
         // tiles of the other block shapes of the non-reducing step (no partial sums)
         for (int w = 0; w < kShapeWarpsN; ++w) {
             const int W = kShapeWarps[w];
             const long long nw = (in.geo.n_fwarps + W - 1) / W;
             if (nw * W > in.geo.n_fwarps_padded) return fail(LBM_ERR_STATE, "fluid work list too short");
-            for (long long t = 0; t < nw; ++t) wtiles[w].push_back(TileDev{i, (int)t, t * W});
+            for (long long t = 0; t < nw; ++t)
+                wtiles[w].push_back(TileDev{i, (int)t, t * W, in.geo.flane, in.geo.fwarp});
         }
     }
     if (tiles.size() > (size_t)INT32_MAX || stiles.size() > (size_t)INT32_MAX)

@@ -309,11 +309,15 @@ enum { LW_EPS = 0, LW_GAMMA, LW_ALPHA, LW_BETA, LW_DELTA, LW_X, LW_THETA, LW_ZET
 
 // A tile: consecutive entries of one instance's work list, processed by one thread block:
 // for the step kernels kTileSegs fluid warps (seg0 = the first), for the other kernels
-// blockDim/32 entries of the active-segment list (the segments holding fluid).
+// blockDim/32 entries of the active-segment list (the segments holding fluid).  A batch's
+// step tiles also carry the instance's fluid work list, so that a block's work-list loads
+// do not wait for its instance's table entry (they are issued together with the table's).
 struct TileDev {
     int inst;
-    int local;       // tile index within its instance (partials slot)
-    long long seg0;  // first entry of the active-segment list
+    int local;           // tile index within its instance (partials slot)
+    long long seg0;      // first entry of the work list
+    const uint2 *flane;  // step tiles: the instance's flane and fwarp; else NULL
+    const uint2 *fwarp;
 };
 
 enum { KIND_AB = 0, KIND_AA_PULL = 1, KIND_AA_LOCAL = 2 };

@@ -165,12 +165,15 @@ __device__ __forceinline__ uint2 ld_keep(const uint2 *a, uint64_t pol)
 #ifndef LBM_STEP_WARPS_PER_SM
 #define LBM_STEP_WARPS_PER_SM 36
 #endif
-template <int STORE, int COLL, bool RED, bool WX, int WARPS = kStepWarps, int KIND = KIND_AB>
+template <int STORE, int COLL, bool RED, bool WX, int WARPS = kStepWarps, int KIND = KIND_AB, bool BATCH = false>
 constexpr int step_min_blocks()
 {
     // the in-place steps of the 16-bit formats (stochastic rounding, scaling) spill at 56
-    // registers: 32 warps, measured 0.3-3 % faster than 36
-    constexpr bool wide = RED || WX || COLL == COLL_MRT || ((STORE == ST_F16 || STORE == ST_BF16) && KIND != KIND_AB);
+    // registers: 32 warps, measured 0.3-3 % faster than 36; so does a batch's local step,
+    // whose parameters come from the instance table instead of the constant bank (60 bytes
+    // at 56 registers; 32 warps measured 3-6 % faster on batches of 2-4 cells)
+    constexpr bool wide = RED || WX || COLL == COLL_MRT || ((STORE == ST_F16 || STORE == ST_BF16) && KIND != KIND_AB) ||
+                          (BATCH && KIND == KIND_AA_LOCAL);
     return (STORE == ST_F64 ? 8 : wide ? 32 : LBM_STEP_WARPS_PER_SM) / WARPS;
 }
 
@@ -517,12 +520,13 @@ struct WarpItem {
 // whether every lane is away from the y and z faces, all precomputed in the work list (one
 // entry per warp and one per lane, no dependent load and no division), which no step writes.
 template <typename R>
-__device__ __forceinline__ void locate_item(const InstanceDev &I, const Par<R> &P, uint32_t w, int lane, WarpItem &it)
+__device__ __forceinline__ void locate_item(const InstanceDev &I, const Par<R> &P, const uint2 *flane,
+                                            const uint2 *fwarp, uint32_t w, int lane, WarpItem &it)
 {
     const uint64_t keep = l2_keep_policy();
     const bool w_ok = checked(I, w, I.n_fwarps_padded);
-    it.wd = w_ok ? ld_keep(I.fwarp + w, keep) : make_uint2(0u, 0u);
-    const uint2 e = w_ok ? ld_keep(I.flane + (w * 32u + (uint32_t)lane), keep) : make_uint2(0xFFFFFFFFu, 0u);
+    it.wd = w_ok ? ld_keep(fwarp + w, keep) : make_uint2(0u, 0u);
+    const uint2 e = w_ok ? ld_keep(flane + (w * 32u + (uint32_t)lane), keep) : make_uint2(0xFFFFFFFFu, 0u);
     it.cell = e.x;
     if (it.cell != 0xFFFFFFFFu && !checked(I, it.cell, I.n32)) it.cell = 0xFFFFFFFFu;
     it.xf = (e.y >> 29) & 3u;
@@ -705,7 +709,7 @@ __device__ __forceinline__ const InstanceDev &instance_of(const InstanceDev *tab
 // flags diverged cells in status[instance]; the other steps carry none of that code.  The WX
 // variant (A-B only) also runs the interpolated wall rules LIBB, QIBB, IEBB and MR.
 template <int COLL, int STORE, int KIND, bool BATCH, bool RED, bool WX, int WARPS = kStepWarps>
-__global__ void __launch_bounds__(WARPS * 32, step_min_blocks<STORE, COLL, RED, WX, WARPS, KIND>())
+__global__ void __launch_bounds__(WARPS * 32, step_min_blocks<STORE, COLL, RED, WX, WARPS, KIND, BATCH>())
     step_kernel(const InstanceDev *__restrict__ table, const __grid_constant__ InstanceDev one,
                 const TileDev *__restrict__ tiles, int ntiles, int flip, unsigned *__restrict__ status)
 {
@@ -721,7 +725,7 @@ __global__ void __launch_bounds__(WARPS * 32, step_min_blocks<STORE, COLL, RED, 
     // table entry holds the same, so that no load precedes the work list's)
     TileDev tile;
     if constexpr (BATCH) tile = tiles[t];
-    else tile = TileDev{0, t, (long long)t * WARPS};
+    else tile = TileDev{0, t, (long long)t * WARPS, nullptr, nullptr};
     const InstanceDev &I = instance_of<BATCH>(table, one, tile.inst);
     const Par<R> P = load_par<R>(I);
     R rates[Q];
@@ -737,7 +741,8 @@ __global__ void __launch_bounds__(WARPS * 32, step_min_blocks<STORE, COLL, RED, 
         fs = fd;
     }
     WarpItem it;
-    locate_item<R>(I, P, (uint32_t)tile.seg0 + (uint32_t)warp, lane, it);
+    locate_item<R>(I, P, BATCH ? tile.flane : I.flane, BATCH ? tile.fwarp : I.fwarp,
+                   (uint32_t)tile.seg0 + (uint32_t)warp, lane, it);
     wait_previous_step();
     T raw[Q];
     pull_item<STORE, KIND, R>(I, P, fs, it, raw);

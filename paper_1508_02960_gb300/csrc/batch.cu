@@ -193,8 +193,10 @@ lbm_status Batch::make_instance(const lbm_desc &d0, cudaStream_t s, std::unique_
         if ((e = dev_alloc(&in->f1, pop)) != cudaSuccess) return cleanup(e, "dev_alloc(populations)");
         if ((e = clear(in->f1)) != cudaSuccess) return cleanup(e, "cudaMemset");
     }
-    // partial sums: one row of kRedSlots doubles per work chunk at the smallest chunk size
-    in->partial_capacity = std::max(1ll, (in->geo.n_active + kMinChunkSegs - 1) / kMinChunkSegs);
+    // partial sums: one row of kRedSlots doubles per tile at the smallest tile size, of the
+    // active-segment chunks (state kernels) and of the step work items alike
+    in->partial_capacity =
+        std::max(1ll, (std::max(in->geo.n_active, in->geo.n_fwarps) + kMinChunkSegs - 1) / kMinChunkSegs);
     if ((e = dev_alloc(&in->partials, sizeof(double) * kRedSlots * in->partial_capacity)) != cudaSuccess)
         return cleanup(e, "dev_alloc(partials)");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cleanup(e, "cudaStreamSynchronize");

@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <string>
+#include <vector>
 
 #include "lbm_internal.h"
 
@@ -148,70 +149,90 @@ __global__ void fluid_scatter_kernel(long long n, const uint4 *__restrict__ seg,
     }
 }
 
-// One warp per fluid warp w (fluid cells 32w .. 32w+31 in cell order): the boundary bits of
-// its lanes and the boundary-table index of its first boundary cell.  The boundary table
-// lists boundary cells in cell order, so the warp's boundary cells are consecutive there,
-// starting at the number of boundary cells before its first cell.
-__global__ void fwarp_kernel(long long nw, const uint32_t *__restrict__ fcell, const uint4 *__restrict__ seg,
-                             uint2 *__restrict__ fwarp)
+// The step kernels' per-lane work-list entries, one warp per work item w (its cells
+// icell[32w .. 32w+31] in cell order, padding lanes 0xFFFFFFFF), so that a step finds what
+// it needs of a cell without a dependent load or a division: flane[32w + l] = {x, y},
+//   x: the cell (bits 0-27; cells < 2^28 since 19 direction strides fit 32 bits), bit 28
+//      x = 0, bit 29 x = nx - 1 (the pulls and pushes that cross the x faces), bit 30 every
+//      cell of the item away from the y and z faces (the same in all its lanes);
+//      0xFFFFFFFF for a padding lane;
+//   y: bits 0-18 the wall mask (bit k: x - e_k solid), bits 19-31 the cell's first link
+//      minus the item's first link;
+// and fwarp[w] = {boundary bits of the lanes, the item's first link (0 when it has no
+// boundary cell)}.  Links are numbered in cell order, and an item's cells lie within
+// kItemSpan + 1 consecutive cells of at most 18 links each, so the offset fits 13 bits.
+static_assert(18 * (kItemSpan + 1) < (1 << 13), "link offset field of the work-list entries");
+__global__ void flane_kernel(long long nw, int nx, int ny, int nz, const uint32_t *__restrict__ icell,
+                             const uint4 *__restrict__ seg, const uint32_t *__restrict__ bmask,
+                             const uint32_t *__restrict__ boff, uint2 *__restrict__ fwarp, uint2 *__restrict__ flane)
 {
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nw; w += warps) {
-        const uint32_t c = fcell[w * 32 + lane];
+        const uint32_t c = icell[w * 32 + lane];
         const bool live = c != 0xFFFFFFFFu;
-        const bool bnd = live && ((seg[c >> 5].y >> (c & 31u)) & 1u);
-        const unsigned bb = __ballot_sync(0xffffffffu, bnd);
-        if (lane == 0) {
-            uint32_t base = 0u;
-            if (live) {
-                const uint4 m = seg[c >> 5];
-                base = m.z + __popc(m.y & ((1u << (c & 31u)) - 1u));
-            }
-            fwarp[w] = make_uint2(bb, base);
-        }
-    }
-}
-
-// The step kernels' per-lane work-list entries, so that a step finds what it needs of a
-// cell without a dependent load or a division: flane[32w + l] = {cell, bits}, bits holding
-//   0-18   the wall mask (bit k: x - e_k solid),
-//   19-28  the cell's first link minus the warp's first link,
-//   29, 30 x = 0, x = nx - 1 (the pulls and pushes that cross the x faces),
-//   31     every cell of the warp is away from the y and z faces (the same in all 32 lanes),
-// and fwarp[w].y becomes the warp's first link (0 when it has no boundary cell).  A warp's
-// links are consecutive (boundary cells in cell order, each with at most 18 of them), so
-// the offset is below 31 * 18 < 2^10.  Padding lanes hold cell 0xFFFFFFFF and no flags.
-static_assert(31 * 18 < (1 << 10), "link offset field of the work-list entries");
-__global__ void flane_kernel(long long nw, int nx, int ny, int nz, const uint32_t *__restrict__ fcell,
-                             const uint32_t *__restrict__ bmask, const uint32_t *__restrict__ boff,
-                             uint2 *__restrict__ fwarp, uint2 *__restrict__ flane)
-{
-    const int lane = threadIdx.x & 31;
-    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nw; w += warps) {
-        const uint2 wd = fwarp[w];
-        const uint32_t c = fcell[w * 32 + lane];
+        const uint4 m = live ? seg[c >> 5] : make_uint4(0u, 0u, 0u, 0u);
+        const bool bnd = live && ((m.y >> (c & 31u)) & 1u);
         uint32_t wm = 0u, off = 0u;
-        if ((wd.x >> lane) & 1u) {
-            const uint32_t b = wd.y + __popc(wd.x & ((1u << lane) - 1u));
+        if (bnd) {  // the boundary table lists boundary cells in cell order
+            const uint32_t b = m.z + __popc(m.y & ((1u << (c & 31u)) - 1u));
             wm = bmask[b];
             off = boff[b];
         }
-        const uint32_t base = wd.x ? __shfl_sync(0xffffffffu, off, __ffs(wd.x) - 1) : 0u;
-        uint32_t flags = 0u;
+        const unsigned bb = __ballot_sync(0xffffffffu, bnd);
+        const uint32_t base = bb ? __shfl_sync(0xffffffffu, off, __ffs(bb) - 1) : 0u;
+        uint32_t ex = 0xFFFFFFFFu;
         bool in_yz = true;
-        if (c != 0xFFFFFFFFu) {
+        if (live) {
             const uint32_t x = c % (uint32_t)nx, yz = c / (uint32_t)nx;
             const uint32_t y = yz % (uint32_t)ny, z = yz / (uint32_t)ny;
-            flags = (x == 0 ? 1u << 29 : 0u) | (x == (uint32_t)nx - 1u ? 1u << 30 : 0u);
+            ex = c | (x == 0 ? 1u << 28 : 0u) | (x == (uint32_t)nx - 1u ? 1u << 29 : 0u);
             in_yz = y >= 1 && y + 2 <= (uint32_t)ny && z >= 1 && z + 2 <= (uint32_t)nz;
         }
-        if (__all_sync(0xffffffffu, in_yz)) flags |= 1u << 31;
-        flane[w * 32 + lane] = make_uint2(c, wm | ((wm ? off - base : 0u) << 19) | flags);
-        __syncwarp();
-        if (lane == 0) fwarp[w].y = base;
+        if (__all_sync(0xffffffffu, in_yz) && live) ex |= 1u << 30;
+        flane[w * 32 + lane] = make_uint2(ex, wm | ((bnd ? off - base : 0u) << 19));
+        if (lane == 0) fwarp[w] = make_uint2(bb, base);
     }
+}
+
+// The step kernels' work items (one warp each) from the fluid cells in cell order.  A
+// box segment of 32 cells that are all fluid is an item of its own: aligned to 128-byte
+// lines, each of its loads and stores touches one line (two for the directions with
+// e_kx != 0).  The fluid cells of the other segments are packed 32 to an item in cell
+// order, an item spanning at most kItemSpan + 1 cells (the link-offset field above).  On
+// the r = 60 sphere cell this cuts the cache lines a step touches by a fifth at the same
+// number of items, where 32 consecutive fluid cells to an item straddle two lines almost
+// always.
+static std::vector<uint32_t> pack_items(const std::vector<uint32_t> &cells, long long *n_items)
+{
+    std::vector<uint32_t> out, pend;
+    out.reserve(cells.size() + cells.size() / 8 + 64);
+    pend.reserve(32);
+    auto flush = [&]() {
+        if (pend.empty()) return;
+        out.insert(out.end(), pend.begin(), pend.end());
+        out.insert(out.end(), 32 - pend.size(), 0xFFFFFFFFu);
+        pend.clear();
+    };
+    size_t j = 0;
+    while (j < cells.size()) {
+        const uint32_t sg = cells[j] >> 5;
+        size_t k = j + 1;
+        while (k < cells.size() && (cells[k] >> 5) == sg) ++k;
+        if (k - j == 32) {
+            out.insert(out.end(), cells.begin() + (long)j, cells.begin() + (long)k);
+        } else {
+            for (size_t i = j; i < k; ++i) {
+                if (pend.size() == 32 || (!pend.empty() && (long long)cells[i] - (long long)pend[0] > kItemSpan))
+                    flush();
+                pend.push_back(cells[i]);
+            }
+        }
+        j = k;
+    }
+    flush();
+    *n_items = (long long)(out.size() / 32);
+    return out;
 }
 
 __global__ void seg_base_kernel(long long nseg, uint4 *__restrict__ seg, const unsigned long long *__restrict__ base)
@@ -518,9 +539,13 @@ cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_
 {
     cudaError_t e = cudaSuccess;
     const long long n = (long long)nx * ny * nz;
+    if (n >= (1ll << 28)) {  // the work-list entries keep a cell in 28 bits
+        *err = "geometry: box of 2^28 cells or more";
+        return cudaErrorInvalidValue;
+    }
     double4 *d_sph = nullptr;
     double *d_q = nullptr;
-    uint32_t *d_wm = nullptr;
+    uint32_t *d_wm = nullptr, *d_icell = nullptr;  // d_icell: the work items' cells, [32 n_fwarps_padded]
     unsigned long long *d_cnt = nullptr, *d_base = nullptr, *d_nl = nullptr, *d_lbase = nullptr, *d_ctr = nullptr;
     unsigned long long h_ctr[2] = {0ull, 0ull};
     unsigned long long h_last[2];
@@ -578,27 +603,36 @@ cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_
                                                                          d_cnt, d_base, g->aseg, g->n_active);
     GEO_CHECK(cudaGetLastError());
 
-    // the step kernels' work list: fluid cells in cell order, 32 per warp (padding lanes
-    // hold 0xFFFFFFFF), and per warp its boundary bits and first boundary-table index
+    // the fluid cells in cell order (fcell, the state kernels' list), then the step kernels'
+    // work items packed from it on the host (pack_items)
     fluid_count_kernel<<<grid_for(g->nseg_padded, 256), 256, 0, s>>>(g->nseg_padded, g->seg, d_cnt);
     GEO_CHECK(cudaGetLastError());
     GEO_CHECK(exclusive_scan(d_cnt, d_base, g->nseg_padded, s));
     GEO_CHECK(cudaMemcpy(&h_last[0], d_base + g->nseg_padded - 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
     GEO_CHECK(cudaMemcpy(&h_last[1], d_cnt + g->nseg_padded - 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
-    {
-        const long long nf = (long long)(h_last[0] + h_last[1]);
-        g->n_fwarps = (nf + 31) / 32;
-        g->n_fwarps_padded = std::max<long long>(kMaxWarpsPerBlock,
-            (g->n_fwarps + kMaxWarpsPerBlock - 1) / kMaxWarpsPerBlock * kMaxWarpsPerBlock);
-    }
-    GEO_CHECK(dev_alloc(&g->fcell, sizeof(uint32_t) * 32 * g->n_fwarps_padded));
-    GEO_CHECK(dev_alloc(&g->fwarp, sizeof(uint2) * g->n_fwarps_padded));
-    GEO_CHECK(cudaMemsetAsync(g->fcell, 0xFF, sizeof(uint32_t) * 32 * g->n_fwarps_padded, s));
+    g->n_fcell = (long long)(h_last[0] + h_last[1]);
+    g->n_fcell_padded = std::max<long long>(32, (g->n_fcell + 31) / 32 * 32);
+    GEO_CHECK(dev_alloc(&g->fcell, sizeof(uint32_t) * g->n_fcell_padded));
+    GEO_CHECK(cudaMemsetAsync(g->fcell, 0xFF, sizeof(uint32_t) * g->n_fcell_padded, s));
     fluid_scatter_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, g->seg, d_base, g->fcell);
     GEO_CHECK(cudaGetLastError());
-    fwarp_kernel<<<grid_for(g->n_fwarps_padded * 32, 256), 256, 0, s>>>(g->n_fwarps_padded, g->fcell, g->seg,
-                                                                          g->fwarp);
-    GEO_CHECK(cudaGetLastError());
+    {
+        std::vector<uint32_t> cells((size_t)g->n_fcell);
+        if (g->n_fcell > 0)
+            GEO_CHECK(cudaMemcpyAsync(cells.data(), g->fcell, sizeof(uint32_t) * cells.size(), cudaMemcpyDeviceToHost,
+                                      s));
+        GEO_CHECK(cudaStreamSynchronize(s));
+        const std::vector<uint32_t> items = pack_items(cells, &g->n_fwarps);
+        g->n_fwarps_padded = std::max<long long>(kMaxWarpsPerBlock,
+            (g->n_fwarps + kMaxWarpsPerBlock - 1) / kMaxWarpsPerBlock * kMaxWarpsPerBlock);
+        GEO_CHECK(dev_alloc(&d_icell, sizeof(uint32_t) * 32 * g->n_fwarps_padded));
+        GEO_CHECK(cudaMemsetAsync(d_icell, 0xFF, sizeof(uint32_t) * 32 * g->n_fwarps_padded, s));
+        if (!items.empty())
+            GEO_CHECK(cudaMemcpyAsync(d_icell, items.data(), sizeof(uint32_t) * items.size(), cudaMemcpyHostToDevice,
+                                      s));
+        GEO_CHECK(cudaStreamSynchronize(s));  // before items goes out of scope
+    }
+    GEO_CHECK(dev_alloc(&g->fwarp, sizeof(uint2) * g->n_fwarps_padded));
 
     if (g->n_boundary > 0) {
         const long long nb = g->n_boundary;
@@ -644,15 +678,16 @@ cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_
     }
     // per-lane entries of the step kernels' work list (needs the boundary table's links)
     GEO_CHECK(dev_alloc(&g->flane, sizeof(uint2) * 32 * g->n_fwarps_padded));
-    flane_kernel<<<grid_for(g->n_fwarps_padded * 32, 256), 256, 0, s>>>(g->n_fwarps_padded, nx, ny, nz, g->fcell,
-                                                                          g->bmask, g->boff, g->fwarp, g->flane);
+    flane_kernel<<<grid_for(g->n_fwarps_padded * 32, 256), 256, 0, s>>>(g->n_fwarps_padded, nx, ny, nz, d_icell,
+                                                                          g->seg, g->bmask, g->boff, g->fwarp,
+                                                                          g->flane);
     GEO_CHECK(cudaGetLastError());
     GEO_CHECK(cudaMemcpyAsync(h_ctr, d_ctr, sizeof(h_ctr), cudaMemcpyDeviceToHost, s));
     GEO_CHECK(cudaStreamSynchronize(s));
     g->n_fluid = (long long)h_ctr[0];
     g->n_links_cli = (long long)h_ctr[1];
-    g->bytes = n + sizeof(uint4) * (g->nseg_padded + g->n_active_padded) +
-               ((sizeof(uint32_t) + sizeof(uint2)) * 32 + sizeof(uint2)) * g->n_fwarps_padded +
+    g->bytes = n + sizeof(uint4) * (g->nseg_padded + g->n_active_padded) + sizeof(uint32_t) * g->n_fcell_padded +
+               (sizeof(uint2) * 32 + sizeof(uint2)) * g->n_fwarps_padded +
                (sizeof(uint32_t) * 2 + sizeof(long long)) * g->n_boundary +
                (sizeof(double) + (c_double ? 8 : 4) * (wall >= 2 ? 1 + kLinkW : 1)) * g->n_links;
 
@@ -664,6 +699,7 @@ cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_
     cudaFree(d_nl);
     cudaFree(d_lbase);
     cudaFree(d_ctr);
+    cudaFree(d_icell);
     return cudaSuccess;
 fail:
     cudaStreamSynchronize(s);
@@ -675,6 +711,7 @@ fail:
     cudaFree(d_nl);
     cudaFree(d_lbase);
     cudaFree(d_ctr);
+    cudaFree(d_icell);
     free_geometry(g);
     return e == cudaSuccess ? cudaErrorUnknown : e;
 }

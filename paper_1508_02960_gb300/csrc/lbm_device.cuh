@@ -220,13 +220,16 @@ enum { STATUS_DIVERGED = 1u, STATUS_TIMEOUT = 2u, STATUS_BOUNDS = 4u };
 //   seg[s].x  bit l set: cell 32s+l is solid or beyond the box (no work)
 //   seg[s].y  bit l set: cell 32s+l is fluid with at least one solid pull source
 //   seg[s].z  index of the first such boundary cell of the segment in the boundary table
-// The step kernels take the fluid cells themselves, in cell order, 32 per warp: fcell[32w +
-// l] is the cell of lane l of fluid warp w (0xFFFFFFFF past the last fluid cell), fwarp[w].x
-// bit l set when that cell is a boundary cell, fwarp[w].y the index of the warp's first
-// link; flane[32w + l] = {fcell[32w + l], bits}: bits 0-18 the wall mask (as bmask below, 0
-// for other cells), 19-28 the first link - fwarp[w].y, 29 and 30 x = 0 and x = nx - 1, 31
-// all 32 cells of the warp away from the y and z faces, so that a step needs no dependent
-// load and no division to find a cell's walls and its periodic fix-ups.
+// fcell[j] is the j-th fluid cell in cell order (the state kernels' list).  The step kernels
+// take work items of one warp each (geometry.cu, pack_items): a box segment whose 32 cells
+// are all fluid, or up to 32 fluid cells of partly solid segments in cell order, the lanes
+// after an item's last cell padding.  For item w: fwarp[w].x bit l set when lane l's cell is
+// a boundary cell, fwarp[w].y the index of the item's first link; flane[32w + l] = {x, y}:
+// x the cell (bits 0-27) with bit 28 x = 0, bit 29 x = nx - 1, bit 30 all the item's cells
+// away from the y and z faces (0xFFFFFFFF: padding lane); y the wall mask (bits 0-18, as
+// bmask below, 0 for other cells) and the cell's first link - fwarp[w].y (bits 19-31), so
+// that a step needs no dependent load and no division to find a cell's walls and its
+// periodic fix-ups.
 // Boundary cell b: bmask[b] bit k set when x - e_k is solid (the pull of direction k hits
 // the wall), boff[b] the index of its first link; its links are ordered by k.  Link l:
 // linkc[l] = CLI coefficient (1-2q)/(1+2q) (0 where CLI falls back to SBB).
@@ -235,7 +238,7 @@ struct InstanceDev {
     void *f0, *f1;           // populations [19][ks] (direction k at k * ks); AA uses f0 only
     const uint4 *seg;        // [nseg]
     const uint4 *aseg;       // [n_active_padded]: seg entries of segments holding fluid, .w = segment
-    const uint32_t *fcell;   // [32 n_fwarps_padded]
+    const uint32_t *fcell;   // [n_fluid] (padded)
     const uint2 *flane;      // [32 n_fwarps_padded]
     const uint2 *fwarp;      // [n_fwarps_padded]
     const uint32_t *bmask;   // [n_boundary]
@@ -247,7 +250,7 @@ struct InstanceDev {
     uint32_t n32;            // ncells
     uint32_t ks;             // elements between consecutive direction arrays (>= ncells; 19 ks < 2^32)
     uint32_t n_active;       // entries of aseg
-    uint32_t n_fwarps;       // fluid warps (entries of fwarp before the padding)
+    uint32_t n_fwarps;       // step work items (entries of fwarp before the padding)
     // interior cells (no periodic wrap): element offset of the pulled population of
     // direction k relative to the cell, and (AA) of the pushed one (mod 2^32)
     uint32_t pull_off[Q];

@@ -93,10 +93,11 @@ struct GeometryDev {
     uint4 *seg = nullptr;          // [nseg_padded]
     uint4 *aseg = nullptr;         // [n_active_padded] segments holding fluid: {x, y, z, segment}
     long long n_active = 0, n_active_padded = 0;
-    uint32_t *fcell = nullptr;     // [32 n_fwarps_padded] fluid cells in cell order (pad 0xFFFFFFFF)
-    uint2 *flane = nullptr;        // [32 n_fwarps_padded] the same cells with their wall masks,
-                                   // link offsets and face flags (lbm_device.cuh)
-    uint2 *fwarp = nullptr;        // [n_fwarps_padded] per 32 fluid cells: boundary bits, first link
+    uint32_t *fcell = nullptr;     // [n_fcell_padded] fluid cells in cell order (pad 0xFFFFFFFF)
+    long long n_fcell = 0, n_fcell_padded = 0;
+    uint2 *flane = nullptr;        // [32 n_fwarps_padded] the step work items' cells with their
+                                   // wall masks, link offsets and face flags (lbm_device.cuh)
+    uint2 *fwarp = nullptr;        // [n_fwarps_padded] per work item: boundary bits, first link
     long long n_fwarps = 0, n_fwarps_padded = 0;
     uint32_t *bmask = nullptr;     // [n_boundary]
     uint32_t *boff = nullptr;      // [n_boundary]
@@ -131,6 +132,9 @@ cudaError_t launch_final_reduce(const InstanceDev *table, const int *tile_count,
 void set_error(const std::string &msg);
 
 constexpr int kMaxWarpsPerBlock = 32;
+// A step work item packed from partly solid box segments spans at most kItemSpan + 1
+// consecutive cells (pack_items in geometry.cu).
+constexpr long long kItemSpan = 448;
 constexpr int kMinChunkSegs = kStepWarps;  // smallest tile (work items) of any kernel: sizes the partial sums
 constexpr long long kDirPad = 0;       // extra elements between direction arrays
 // Sphere centres may lie at most this many box lengths from the origin along each axis

@@ -527,12 +527,13 @@ __device__ __forceinline__ void locate_item(const InstanceDev &I, const Par<R> &
     const bool w_ok = checked(I, w, I.n_fwarps_padded);
     it.wd = w_ok ? ld_keep(fwarp + w, keep) : make_uint2(0u, 0u);
     const uint2 e = w_ok ? ld_keep(flane + (w * 32u + (uint32_t)lane), keep) : make_uint2(0xFFFFFFFFu, 0u);
-    it.cell = e.x;
-    if (it.cell != 0xFFFFFFFFu && !checked(I, it.cell, I.n32)) it.cell = 0xFFFFFFFFu;
-    it.xf = (e.y >> 29) & 3u;
-    it.inner = (e.y >> 31) != 0u;  // the same in all lanes of the warp
+    const bool live = e.x != 0xFFFFFFFFu;
+    it.cell = live ? (e.x & 0x0FFFFFFFu) : 0xFFFFFFFFu;
+    if (live && !checked(I, it.cell, I.n32)) it.cell = 0xFFFFFFFFu;
+    it.xf = (e.x >> 28) & 3u;
+    it.inner = ((e.x >> 30) & 1u) != 0u;  // the same in all live lanes of the item
     it.wm = e.y & 0x7FFFFu;
-    it.off = it.wd.y + ((e.y >> 19) & 0x3FFu);
+    it.off = it.wd.y + (e.y >> 19);
     // every link of the cell within the link tables
     if (it.wm && !checked(I, it.off + __popc(it.wm), I.n_links + 1u)) it.wm = 0u;
 }

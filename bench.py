@@ -368,6 +368,60 @@ def study_drag(args):
                       "wall_s": time.perf_counter() - t0}), flush=True)
 
 
+def study_geometry(args):
+    """The same step kernel (FP32, AA, TRT, SBB walls, tau = 0.6) on 128^3 cells whose solid
+    is shaped to separate what the geometry costs: the r = 60 and r = 20 spheres, a slab of
+    55 solid planes (z), of 55 solid rows in every plane (y), of 55 solid cells in every row
+    (x; porosity 0.57, as the r = 60 sphere), and no solid at all.  Per geometry: MLUPS and
+    the fraction of the copy bandwidth (best of 10 windows of 100 steps)."""
+    import numpy as np
+    import torch
+
+    from paper_1508_02960_gb300 import capi
+    from paper_1508_02960_gb300 import inputs as I
+
+    L = 128
+    stream = torch.cuda.current_stream()
+    peak, _ = load_peaks()
+
+    def slab(axis):
+        f = np.zeros((L, L, L), np.uint8)  # [z][y][x]
+        sl = [slice(None)] * 3
+        sl[axis] = slice(36, 91)
+        f[tuple(sl)] = 1
+        return f
+
+    cases = [("sphere_r60", dict(spheres=I.centred_sphere(L, 60.0).spheres)),
+             ("sphere_r20", dict(spheres=I.centred_sphere(L, 20.0).spheres)),
+             ("slab_z", dict(flags=slab(0))), ("slab_y", dict(flags=slab(1))), ("slab_x", dict(flags=slab(2))),
+             ("empty", dict(flags=np.zeros((L, L, L), np.uint8)))]
+    rows = []
+    for name, geo in cases:
+        with capi.Context(shape=(L, L, L), tau=0.6, delta_rho=2e-5, magic_lambda=3 / 16, collision=capi.TRT,
+                          wall=capi.SBB, storage=capi.F32, layout=capi.LAYOUT_AA, stream=stream, **geo) as ctx:
+            nf = ctx.info()["n_fluid"]
+            ctx.init_equilibrium()
+            for _ in range(3):
+                ctx.step(100)
+                ctx.observables()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            best = None
+            for _ in range(10):
+                e0.record(stream)
+                ctx.step(100)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / 100
+                best = ms if best is None else min(best, ms)
+            rec = {"study": "geometry_point", "geometry": name, "n_fluid": nf, "us_per_step": best * 1e3,
+                   "mlups": nf / (best * 1e3), "roofline_frac": 38 * 4 * nf / (best * 1e-3) / 1e9 / peak}
+            rows.append(rec)
+            print(json.dumps(rec), flush=True)
+    print(json.dumps({"study": "geometry", "storage": "F32", "layout": "AA", "collision": "TRT", "wall": "SBB",
+                      "rows": rows}), flush=True)
+
+
 def study_kstar(args):
     """Apparent permeability and Forchheimer coefficient over Re_p (Sec. 4) on the simple
     cubic array (one sphere of r = 0.3 L, reading O12), TRT-CLI, FP32 storage, Lambda of
@@ -738,7 +792,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only build the workload and run this many steps (for ncu), no timing")
-    ap.add_argument("--study", choices=["precision", "sweep", "drag", "kstar"], default=None,
+    ap.add_argument("--study", choices=["precision", "sweep", "drag", "kstar", "geometry"], default=None,
                     help="run a study instead of the benchmark (JSON lines)")
     ap.add_argument("--study-size", type=int, default=64)
     ap.add_argument("--study-max-steps", type=int, default=60000)
@@ -760,6 +814,9 @@ def main():
         return
     if args.study == "kstar":
         study_kstar(args)
+        return
+    if args.study == "geometry":
+        study_geometry(args)
         return
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", 0))

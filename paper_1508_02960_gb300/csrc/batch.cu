@@ -509,6 +509,11 @@ lbm_status Batch::rebuild()
         for (int w = 0; w < kShapeWarpsN; ++w) {
             const int W = kShapeWarps[w];
             const long long nw = (in.geo.n_fwarps + W - 1) / W;
+            if (i < kBatchMapMax) {
+                maps_[w].tile_start[i] = (int)wtiles[w].size();
+                maps_[w].flane[i] = in.geo.flane;
+                maps_[w].fwarp[i] = in.geo.fwarp;
+            }
             if (nw * W > in.geo.n_fwarps_padded) return fail(LBM_ERR_STATE, "fluid work list too short");
             for (long long t = 0; t < nw; ++t)
                 wtiles[w].push_back(TileDev{i, (int)t, t * W, in.geo.flane, in.geo.fwarp});
@@ -516,6 +521,10 @@ lbm_status Batch::rebuild()
     }
     if (tiles.size() > (size_t)INT32_MAX || stiles.size() > (size_t)INT32_MAX)
         return fail(LBM_ERR_ARG, "too many tiles");
+    for (int w = 0; w < kShapeWarpsN; ++w) {  // maps for batches of 2 .. kBatchMapMax instances
+        maps_[w].n = (n >= 2 && n <= kBatchMapMax) ? n : 0;
+        if (maps_[w].n) maps_[w].tile_start[n] = (int)wtiles[w].size();
+    }
     ntiles_ = (int)tiles.size();
     nstiles_ = (int)stiles.size();
     cudaFree(d_table_);
@@ -691,7 +700,7 @@ Launch Batch::shaped_launch(const StepShape &sh, int kind) const
     while (w < kShapeWarpsN && kShapeWarps[w] != sh.warps) ++w;
     (void)kind;
     const int nt = nwtiles_[w];
-    return Launch{d_table_, d_wtiles_[w], nt, sh.warps, std::max(1, nt), sh.warps * 32, stream_};
+    return Launch{d_table_, d_wtiles_[w], nt, sh.warps, std::max(1, nt), sh.warps * 32, stream_, &maps_[w]};
 }
 
 // The graph of m steps (+ the reduction when red) from (flip_, aa_phase_) in shape sh,
@@ -713,7 +722,7 @@ lbm_status Batch::graph_for(long long m, bool red, const StepShape &sh, int wx, 
         graphs_.erase(lru);
     }
     StepQueue q{&ops(),
-                Launch{d_table_, d_stiles_, nstiles_, kTileSegs, grid_, kStepWarps * 32, stream_},
+                Launch{d_table_, d_stiles_, nstiles_, kTileSegs, grid_, kStepWarps * 32, stream_, &maps_[0]},
                 {shaped_launch(sh, layout_ == LBM_LAYOUT_AB ? KIND_AB : KIND_AA_PULL),
                  shaped_launch(sh, KIND_AA_LOCAL)},
                 sh.warps,

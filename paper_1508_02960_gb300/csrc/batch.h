@@ -46,6 +46,7 @@ struct StepShape {
     int warps = kStepWarps;
 };
 constexpr int kShapeWarps[] = {4, 2, 8};  // the candidates, in the order they are timed
+static_assert(kShapeWarps[0] == kStepWarps, "shape 0 is the reducing step's (its tile map serves both)");
 constexpr int kShapeWarpsN = 3;
 
 class Batch {
@@ -158,6 +159,8 @@ private:
     // tiles of every block shape of the non-reducing step
     TileDev *d_wtiles_[kShapeWarpsN] = {nullptr, nullptr, nullptr};
     int nwtiles_[kShapeWarpsN] = {0, 0, 0};
+    // the same tiles as kernel-parameter maps (batches of 2 .. kBatchMapMax instances)
+    BatchMap maps_[kShapeWarpsN] = {};
     StepShape shape_;
     int shape_src_ = 0;                // 0 default, 1 measured by this batch, 2 from the cache
     double shape_ms_[kShapeWarpsN] = {0, 0, 0};

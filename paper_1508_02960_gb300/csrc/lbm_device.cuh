@@ -325,6 +325,23 @@ struct TileDev {
 
 enum { KIND_AB = 0, KIND_AA_PULL = 1, KIND_AA_LOCAL = 2 };
 
+// The tiles of a batched step launch, as a kernel parameter (constant bank) for batches of up
+// to kBatchMapMax instances: instance i owns tiles tile_start[i] .. tile_start[i + 1] - 1 of
+// the launch, and its work list is flane[i], fwarp[i].  A block finds its instance by a
+// binary search there instead of loading its tile record first, which the work-list loads
+// would wait for.  n = 0: the launch reads its tile records (larger batches).
+constexpr int kBatchMapMax = 64;
+struct BatchMap {
+    int n;
+    int tile_start[kBatchMapMax + 1];
+    const uint2 *flane[kBatchMapMax];
+    const uint2 *fwarp[kBatchMapMax];
+};
+struct NoBatchMap {};
+template <bool BATCH> struct MapArgT { using type = NoBatchMap; };
+template <> struct MapArgT<true> { using type = BatchMap; };
+template <bool BATCH> using MapArg = typename MapArgT<BATCH>::type;
+
 // TMA brick kernel (lbm_tma.cuh): bricks of kBrickX x kBrickY x kBrickZ cells, one thread
 // per cell, kBrickStages shared-memory stages per block.
 constexpr int kBrickX = 32, kBrickY = 2, kBrickZ = 4;

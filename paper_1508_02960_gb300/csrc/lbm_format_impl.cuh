@@ -37,12 +37,13 @@ cudaError_t step_red(const Launch &L, int flip, unsigned *status, const Instance
 {
     cudaError_t e;
     if (one) {  // a single instance: parameters travel in the constant bank
-        e = launch_step(step_kernel<COLL, STORE, KIND, false, RED, WX, WARPS>, L, L.table, *one, L.tiles, L.ntiles,
-                        flip, status);
-    } else {  // a batch: parameters from the device table
+        e = launch_step(step_kernel<COLL, STORE, KIND, false, RED, WX, WARPS>, L, L.table, *one, NoBatchMap{}, L.tiles,
+                        L.ntiles, flip, status);
+    } else {  // a batch: parameters from the device table, the tiles' instances from the map
         static const InstanceDev unused{};
-        e = launch_step(step_kernel<COLL, STORE, KIND, true, RED, WX, WARPS>, L, L.table, unused, L.tiles, L.ntiles,
-                        flip, status);
+        static const BatchMap no_map{};  // n = 0: tile records
+        e = launch_step(step_kernel<COLL, STORE, KIND, true, RED, WX, WARPS>, L, L.table, unused,
+                        L.map ? *L.map : no_map, L.tiles, L.ntiles, flip, status);
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

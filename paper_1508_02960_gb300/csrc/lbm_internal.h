@@ -36,6 +36,7 @@ struct Launch {
     int chunk_segs;
     int grid, block;
     cudaStream_t stream;
+    const BatchMap *map = nullptr;  // a batched step launch: its tiles' instances (n = 0: none)
 };
 
 // Arguments of one launch of the TMA brick kernel (single instance, A-B layout): tensor

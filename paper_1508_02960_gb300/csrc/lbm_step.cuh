@@ -712,7 +712,8 @@ __device__ __forceinline__ const InstanceDev &instance_of(const InstanceDev *tab
 template <int COLL, int STORE, int KIND, bool BATCH, bool RED, bool WX, int WARPS = kStepWarps>
 __global__ void __launch_bounds__(WARPS * 32, step_min_blocks<STORE, COLL, RED, WX, WARPS, KIND, BATCH>())
     step_kernel(const InstanceDev *__restrict__ table, const __grid_constant__ InstanceDev one,
-                const TileDev *__restrict__ tiles, int ntiles, int flip, unsigned *__restrict__ status)
+                const __grid_constant__ MapArg<BATCH> map, const TileDev *__restrict__ tiles, int ntiles, int flip,
+                unsigned *__restrict__ status)
 {
     static_assert(!RED || WARPS == kStepWarps, "the reducing step runs kStepWarps-warp tiles");
     using S = Store<STORE>;
@@ -725,8 +726,22 @@ __global__ void __launch_bounds__(WARPS * 32, step_min_blocks<STORE, COLL, RED, 
     // a single instance's tiles are consecutive: tile t holds work items WARPS t ... (its
     // table entry holds the same, so that no load precedes the work list's)
     TileDev tile;
-    if constexpr (BATCH) tile = tiles[t];
-    else tile = TileDev{0, t, (long long)t * WARPS, nullptr, nullptr};
+    if constexpr (BATCH) {
+        if (map.n > 0) {  // the instance whose tiles hold t: the last i with tile_start[i] <= t
+            int lo = 0, hi = map.n - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (map.tile_start[mid] <= t) lo = mid;
+                else hi = mid - 1;
+            }
+            const int local = t - map.tile_start[lo];
+            tile = TileDev{lo, local, (long long)local * WARPS, map.flane[lo], map.fwarp[lo]};
+        } else {
+            tile = tiles[t];
+        }
+    } else {
+        tile = TileDev{0, t, (long long)t * WARPS, nullptr, nullptr};
+    }
     const InstanceDev &I = instance_of<BATCH>(table, one, tile.inst);
     const Par<R> P = load_par<R>(I);
     R rates[Q];

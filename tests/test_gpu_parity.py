@@ -320,6 +320,30 @@ def test_batch_alone_vs_mix_bitwise(capi, layout):
             assert ctx.observables()["U_sup"] == mix[i][1]["U_sup"]
 
 
+@pytest.mark.parametrize("n_inst", [64, 66])
+def test_batch_tile_map_and_tile_records_bitwise(capi, n_inst):
+    """Batches of up to 64 instances find each block's instance through the launch's tile map,
+    larger ones through tile records: both give every instance the state it reaches alone,
+    bit for bit (small cells of three shapes, in both layouts' kernels over 50 steps)."""
+    shapes = [I.centred_sphere(8, 2.5), I.Geometry(12, 8, 8, np.array([[5.5, 4.0, 4.2, 2.7]])),
+              I.Geometry(9, 10, 7, np.array([[1.0, 8.5, 3.0, 3.1]]))]
+    for layout in ("AB", "AA"):
+        keep = [capi.make_desc(spheres=shapes[i % 3].spheres, shape=shapes[i % 3].shape, tau=0.6 + 0.003 * i,
+                               delta_rho=1e-4 * (1 + i % 5), collision=capi.TRT, wall=capi.CLI, storage=capi.F32,
+                               layout=getattr(capi, "LAYOUT_" + layout)) for i in range(n_inst)]
+        b = capi.Batch([d for d, _ in keep])
+        b.init_equilibrium()
+        b.step(50)
+        check = (0, 1, n_inst // 2, n_inst - 2, n_inst - 1)
+        mix = {i: b.get_populations(i) for i in check}
+        b.close()
+        for i in check:
+            with capi.Context(desc=keep[i][0]) as ctx:
+                ctx.init_equilibrium()
+                ctx.step(50)
+                assert np.array_equal(ctx.get_populations(), mix[i]), (layout, i)
+
+
 def test_aa_batch_sets_one_instance_only_in_step0_arrangement(capi, orc):
     """The instances of an in-place batch share one arrangement: one instance's state can be
     set after an even number of steps (and steps on alike), not after an odd one."""

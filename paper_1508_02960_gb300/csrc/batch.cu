@@ -508,7 +508,9 @@ lbm_status Batch::rebuild()
         // tiles of the other block shapes of the non-reducing step (no partial sums)
         for (int w = 0; w < kShapeWarpsN; ++w) {
             const int W = kShapeWarps[w];
-            const long long nw = (in.geo.n_fwarps + W - 1) / W;
+            // at least one tile, as for the reducing step, whose tiles the kShapeWarps[0]
+            // map also describes (an instance without fluid has one tile of padding)
+            const long long nw = std::max(1ll, (in.geo.n_fwarps + W - 1) / W);
             if (i < kBatchMapMax) {
                 maps_[w].tile_start[i] = (int)wtiles[w].size();
                 maps_[w].flane[i] = in.geo.flane;

@@ -344,6 +344,30 @@ def test_batch_tile_map_and_tile_records_bitwise(capi, n_inst):
                 assert np.array_equal(ctx.get_populations(), mix[i]), (layout, i)
 
 
+@pytest.mark.parametrize("layout", ["AB", "AA"])
+def test_batch_with_an_instance_without_fluid(capi, layout):
+    """An instance without a fluid cell keeps one tile of padding in every launch shape, so
+    the instances after it keep their tiles: each steps as it does alone, bit for bit."""
+    solid = np.ones((4, 5, 6), dtype=np.uint8)
+    lay = getattr(capi, "LAYOUT_" + layout)
+    keep = [capi.make_desc(flags=solid, shape=solid.shape, tau=0.7, delta_rho=1e-4, collision=capi.TRT,
+                           wall=capi.CLI, storage=capi.F32, layout=lay)]
+    for i, gg in enumerate([I.centred_sphere(8, 2.5), RAGGED]):
+        keep.append(capi.make_desc(spheres=gg.spheres, shape=gg.shape, tau=0.65 + 0.05 * i, delta_rho=1e-4,
+                                   collision=capi.TRT, wall=capi.CLI, storage=capi.F32, layout=lay))
+    b = capi.Batch([d for d, _ in keep])
+    b.init_equilibrium()
+    b.step(60)
+    assert np.all(b.get_populations(0) == 0.0)
+    mix = [b.get_populations(i) for i in (1, 2)]
+    b.close()
+    for j, i in enumerate((1, 2)):
+        with capi.Context(desc=keep[i][0]) as ctx:
+            ctx.init_equilibrium()
+            ctx.step(60)
+            assert np.array_equal(ctx.get_populations(), mix[j]), i
+
+
 def test_aa_batch_sets_one_instance_only_in_step0_arrangement(capi, orc):
     """The instances of an in-place batch share one arrangement: one instance's state can be
     set after an even number of steps (and steps on alike), not after an odd one."""

@@ -79,6 +79,26 @@ __host__ __device__ constexpr int mrt_m(int i, int k)
     default: return (x * x - y * y) * z;
     }
 }
+// Row i of M is even in e (M[i][kbar] = M[i][k] for every k) or odd (M[i][kbar] = -M[i][k],
+// M[i][0] = 0): its moment needs only the sums, or only the differences, of the opposite
+// pairs (k, k + 1).  mrt_even is written out (rows 0-2 and 9-15 even) so that the unrolled
+// loops of the collision fold it to a constant; the check below derives it from the rows.
+__host__ __device__ constexpr bool mrt_even(int i) { return i <= 2 || (i >= 9 && i <= 15); }
+__host__ __device__ constexpr bool mrt_row_parity_holds(int i)
+{
+    for (int k = 1; k < Q; k += 2) {
+        const int a = mrt_m(i, k), b = mrt_m(i, k + 1);
+        if (mrt_even(i) ? (b != a) : (b != -a)) return false;
+    }
+    return mrt_even(i) || mrt_m(i, 0) == 0;
+}
+__host__ __device__ constexpr bool mrt_parities_hold()
+{
+    for (int i = 0; i < Q; ++i)
+        if (!mrt_row_parity_holds(i)) return false;
+    return true;
+}
+static_assert(mrt_parities_hold(), "mrt_even matches the rows of M");
 __host__ __device__ constexpr int mrt_norm2(int i)
 {
     int s = 0;

@@ -230,30 +230,57 @@ __device__ __forceinline__ void collide(R (&g)[Q], const Par<R> &p, const R *rat
             g[kb] = g[kb] - dp + dm;
         }
     } else {  // MRT: g~ = g - M^-1 S M (g - g^eq), M^-1 = M^T diag(1/|M_i|^2)
-        R neq[Q];
+        // Every row of M is even or odd in e (mrt_even), so a moment takes the sums (even
+        // rows) or the differences (odd rows) of the opposite pairs of g - g^eq, and the
+        // relaxation goes back to a pair as its even part plus or minus its odd part: the
+        // same matrix in half the operations of the full 19 x 19 products.
+        R sp[Q / 2 + 1], dp[Q / 2 + 1];
+        sp[0] = g[0] - R(weight(0)) * (drho - R(1.5) * rho0 * uu);
+        dp[0] = R(0);
 #pragma unroll
-        for (int k = 0; k < Q; ++k) {
+        for (int k = 1; k < Q; k += 2) {
+            const R w = R(weight(k));
             const R eu = R(ex(k)) * ux + R(ey(k)) * uy + R(ez(k)) * uz;
-            neq[k] = g[k] - R(weight(k)) * (drho + rho0 * (R(3) * eu + R(4.5) * eu * eu - R(1.5) * uu));
+            const R eqs = w * (drho + rho0 * (R(4.5) * eu * eu - R(1.5) * uu));  // even part of f^eq
+            const R eqd = w * rho0 * R(3) * eu;                                  // odd part of f^eq
+            const R nk = g[k] - (eqs + eqd), nkb = g[k + 1] - (eqs - eqd);
+            sp[(k + 1) / 2] = nk + nkb;
+            dp[(k + 1) / 2] = nk - nkb;
         }
+        R dm[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
+            dm[i] = R(0);
             if (i == 0 || i == 3 || i == 5 || i == 7) continue;  // conserved: m^neq = 0
             R m = R(0);
 #pragma unroll
-            for (int k = 0; k < Q; ++k) {
-                const int c = mrt_m(i, k);
-                if (c == 1) m += neq[k];
-                else if (c == -1) m -= neq[k];
-                else if (c != 0) m += R(c) * neq[k];
+            for (int p = 0; p <= Q / 2; ++p) {
+                const int c = mrt_m(i, p == 0 ? 0 : 2 * p - 1);
+                const R v = mrt_even(i) ? sp[p] : dp[p];
+                if (c == 1) m += v;
+                else if (c == -1) m -= v;
+                else if (c != 0) m += R(c) * v;
             }
-            const R dm = rates[i] * m;  // rates[] already divided by |M_i|^2
+            dm[i] = rates[i] * m;  // rates[] already divided by |M_i|^2
+        }
 #pragma unroll
-            for (int k = 0; k < Q; ++k) {
+        for (int p = 0; p <= Q / 2; ++p) {
+            const int k = p == 0 ? 0 : 2 * p - 1;
+            R ev = R(0), od = R(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                if (i == 0 || i == 3 || i == 5 || i == 7) continue;
                 const int c = mrt_m(i, k);
-                if (c == 1) g[k] -= dm;
-                else if (c == -1) g[k] += dm;
-                else if (c != 0) g[k] -= R(c) * dm;
+                if (c == 0) continue;
+                const R t = c == 1 ? dm[i] : (c == -1 ? -dm[i] : R(c) * dm[i]);
+                if (mrt_even(i)) ev += t;
+                else od += t;
+            }
+            if (p == 0) {
+                g[0] -= ev;
+            } else {
+                g[k] -= ev + od;
+                g[k + 1] -= ev - od;
             }
         }
     }

@@ -284,6 +284,18 @@ LBM_API unsigned lbm_build_flags(void);
  * since its kernels would use such an index. */
 LBM_API lbm_status lbm_debug_corrupt_worklist(lbm_ctx *ctx);
 
+/* Host code (no GPU), for tests of the step kernels' work list: packs the fluid cells
+ * cells[0 .. n_cells) (strictly increasing linear indices below 2^28, as the library lists
+ * a geometry's fluid cells) into work items of 32 entries, one warp each, as a context
+ * does.  A 32-cell segment of the box (cells 32s .. 32s+31) that is all fluid is an item of
+ * its own; the fluid cells of the other segments are packed up to 32 to an item in cell
+ * order, an item spanning at most 449 consecutive cells.  A padding entry is 0xFFFFFFFF
+ * and follows the item's cells.  Writes *n_items always.  If out_cap >= 32 * *n_items it
+ * also writes the 32 * *n_items entries to out (caller-owned). Otherwise it returns
+ * LBM_ERR_ARG, as it does for NULL or unordered input. */
+LBM_API lbm_status lbm_debug_pack_work_items(const uint32_t *cells, int64_t n_cells, uint32_t *out, int64_t out_cap,
+                                             int64_t *n_items);
+
 /* FP64 sums over fluid cells of (rho - rho0, u_x, u_y, u_z), computed now from the
  * stored post-collision populations (synchronises).  sums: host array of 4. */
 LBM_API lbm_status lbm_moment_sums(lbm_ctx *ctx, double *sums);

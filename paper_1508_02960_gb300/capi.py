@@ -180,6 +180,9 @@ PROTOTYPES = {
     "lbm_debug_fail_alloc_after": (None, [ctypes.c_int64]),
     "lbm_build_flags": (ctypes.c_uint, []),
     "lbm_debug_corrupt_worklist": (ctypes.c_int, [ctypes.c_void_p]),
+    "lbm_debug_pack_work_items": (_st, [ctypes.POINTER(ctypes.c_uint32), ctypes.c_int64,
+                                        ctypes.POINTER(ctypes.c_uint32), ctypes.c_int64,
+                                        ctypes.POINTER(ctypes.c_int64)]),
     "lbm_server_destroy": (None, [_vp]),
 }
 
@@ -564,6 +567,24 @@ def moment_sums_f64_noalloc(f_dev_ptr: int, solid_dev_ptr: int | None, n_cells: 
     tensor.data_ptr()).  Queued on the stream; does not wait."""
     check(lib().lbm_moment_sums_f64_noalloc(f_dev_ptr, solid_dev_ptr, int(n_cells), float(rho0), sums_dev_ptr,
                                             _stream_handle(stream)), "lbm_moment_sums_f64_noalloc")
+
+
+def pack_work_items(cells) -> np.ndarray:
+    """The step kernels' work items for the fluid cells `cells` (increasing linear indices),
+    as lbm_debug_pack_work_items packs them: an int64 array [n_items, 32] of cell indices,
+    -1 for padding.  Host code."""
+    c = np.ascontiguousarray(cells, dtype=np.uint32)
+    n = ctypes.c_int64(0)
+    p = c.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+    st = lib().lbm_debug_pack_work_items(p, int(c.size), None, 0, ctypes.byref(n))
+    if st != ERR_ARG or n.value < 0:
+        check(st, "lbm_debug_pack_work_items")
+    out = np.empty(32 * n.value, dtype=np.uint32)
+    check(lib().lbm_debug_pack_work_items(p, int(c.size), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                          int(out.size), ctypes.byref(n)), "lbm_debug_pack_work_items")
+    items = out.reshape(-1, 32).astype(np.int64)
+    items[items == 0xFFFFFFFF] = -1
+    return items
 
 
 def debug_fail_alloc_after(n: int):

@@ -114,6 +114,23 @@ const char *lbm_version(void) { return "lbm_gb300 0.1 (sm_103a)"; }
 
 unsigned lbm_build_flags(void) { return kChecked ? LBM_BUILD_CHECKED : 0u; }
 
+lbm_status lbm_debug_pack_work_items(const uint32_t *cells, int64_t n_cells, uint32_t *out, int64_t out_cap,
+                                     int64_t *n_items)
+{
+    if (!n_items || n_cells < 0 || (n_cells > 0 && !cells)) return fail(LBM_ERR_ARG, "NULL or negative argument");
+    std::vector<uint32_t> c(cells, cells + n_cells);
+    for (int64_t j = 1; j < n_cells; ++j)
+        if (c[(size_t)j] <= c[(size_t)j - 1]) return fail(LBM_ERR_ARG, "cells must be strictly increasing");
+    for (int64_t j = 0; j < n_cells; ++j)
+        if (c[(size_t)j] >= (1u << 28)) return fail(LBM_ERR_ARG, "cell index beyond 2^28");
+    long long ni = 0;
+    const std::vector<uint32_t> items = pack_work_items(c, &ni);
+    *n_items = (int64_t)ni;
+    if (!out || out_cap < (int64_t)items.size()) return fail(LBM_ERR_ARG, "out holds fewer than 32 n_items entries");
+    std::copy(items.begin(), items.end(), out);
+    return LBM_OK;
+}
+
 lbm_status lbm_debug_corrupt_worklist(lbm_ctx *ctx)
 {
     if (!ctx || ctx->b.size() != 1) return fail(LBM_ERR_ARG, "ctx is NULL");

@@ -533,6 +533,11 @@ void free_geometry(GeometryDev *g)
         }                                                                             \
     } while (0)
 
+std::vector<uint32_t> pack_work_items(const std::vector<uint32_t> &cells, long long *n_items)
+{
+    return pack_items(cells, n_items);
+}
+
 cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_spheres, const uint8_t *flags,
                            const double *q_host, bool c_double, int wall, double tau, cudaStream_t s, GeometryDev *g,
                            std::string *err)

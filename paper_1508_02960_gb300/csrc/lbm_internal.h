@@ -114,6 +114,9 @@ struct GeometryDev {
 // walls >= LBM_LIBB, linkw: the coefficients of the rule, see lbm_device.cuh) are written
 // as double when c_double, else float; tau enters IEBB's coefficients.  Returns a CUDA error or cudaSuccess;
 // *err receives a message on failure.
+// The step kernels' work items (32 entries each, padding 0xFFFFFFFF) from the fluid cells in
+// increasing cell order (geometry.cu).  Host code.
+std::vector<uint32_t> pack_work_items(const std::vector<uint32_t> &cells, long long *n_items);
 cudaError_t build_geometry(int nx, int ny, int nz, const double *spheres, int n_spheres,
                            const uint8_t *flags, const double *q_host, bool c_double, int wall, double tau,
                            cudaStream_t s, GeometryDev *g, std::string *err);
